@@ -1,0 +1,210 @@
+/*
+ * sgc.h -- cluster-wise Gustavson SpGEMM over CSR_Cluster, GB300 (sm_103a).
+ *
+ * C ABI of libsgc.so.  Every function returns an int status (SGC_OK on
+ * success); sgc_last_error() gives a message for the calling thread's last
+ * failure.
+ *
+ * Conventions that hold for every entry point below:
+ *  - Matrix arrays, workspaces and output arrays are DEVICE pointers on the
+ *    current CUDA device, allocated and owned by the caller; the library never
+ *    frees or keeps them after the call returns (CSR_Cluster keeps the
+ *    caller's perm / cluster_ptr pointers by reference for the matrix's life).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue their kernels on it and return without waiting,
+ *    except calls documented as "synchronises", which wait for the stream
+ *    because they return a count to the host.
+ *  - Sizes come from count-then-fill: a *_workspace_size or *_count call says
+ *    how much to allocate, the caller allocates, the fill call writes.
+ *  - CSR inputs: int64 row pointer (nrows+1, row_ptr[0] = 0), int32 column
+ *    ids sorted ascending and unique within each row, 0 <= col < ncols,
+ *    values of the matrix's dtype.  A and B of one product share a dtype.
+ *    With sgc_options.validate = 1 these are checked on the device and a
+ *    violation returns SGC_DEVICE_CHECK_FAILED; otherwise they are trusted.
+ *  - Output C is CSR in A's ORIGINAL row order, columns sorted within each
+ *    row, structural entries whose value cancels to zero kept (the symbolic
+ *    structure of Sec. 2.2).  FP32 products are accumulated in FP64 and
+ *    rounded once; FP64 accumulates without FMA in ascending k per (i, j),
+ *    except rows with more than 3072 outputs (see SGC_HEAVY_ROW_OUTPUTS);
+ *    int64 wraps modulo 2^64.
+ *  - Errors: SGC_INVALID_ARG (null pointer, negative or inconsistent size),
+ *    SGC_UNSUPPORTED (dtype mismatch, cluster larger than 32 rows),
+ *    SGC_WORKSPACE_TOO_SMALL, SGC_CUDA_ERROR (a CUDA call failed; the CUDA
+ *    error string is in sgc_last_error), SGC_DEVICE_CHECK_FAILED (a device
+ *    check failed: bad input or an internal invariant), SGC_DEVICE_TIMEOUT (a
+ *    bounded device-side wait gave up).  On any error, outputs are undefined.
+ */
+#ifndef SGC_H_
+#define SGC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SGC_ABI_VERSION 1
+
+enum {
+  SGC_OK = 0,
+  SGC_INVALID_ARG = 1,
+  SGC_UNSUPPORTED = 2,
+  SGC_WORKSPACE_TOO_SMALL = 3,
+  SGC_CUDA_ERROR = 4,
+  SGC_DEVICE_CHECK_FAILED = 5,
+  SGC_DEVICE_TIMEOUT = 6
+};
+
+/* value types */
+enum { SGC_F32 = 0, SGC_F64 = 1, SGC_I64 = 2 };
+
+/* CSR_Cluster value layouts (Sec. 3.1, "Clustered matrix format") */
+enum {
+  SGC_LAYOUT_PADDED = 0, /* placeholders kept: value of row l, union column t at val_ptr[c] + t*K_c + l */
+  SGC_LAYOUT_MASKED = 1  /* placeholders dropped: values in (t, l ascending over set mask bits) order */
+};
+
+/* staging of B rows into shared memory */
+enum {
+  SGC_STAGING_AUTO = 0, /* bulk copies when B's col/val base pointers are 16-byte aligned */
+  SGC_STAGING_BULK = 1, /* 1D bulk async copies (cp.async.bulk) completing on an mbarrier */
+  SGC_STAGING_LDG = 2   /* cooperative vector loads by the CTA's threads */
+};
+
+/* A row with more outputs than this (more than 6144 possible outputs in the
+ * symbolic phase) is a heavy row: one CTA per row, dense accumulator over
+ * column windows, shared-memory atomics (FP64 values then depend on the
+ * order of atomic adds, within the FP64 bound; int64 exact). */
+#define SGC_HEAVY_ROW_OUTPUTS 3072
+
+/* CSR matrix (Sec. 2.1: row-id / col-id / value arrays). */
+typedef struct sgc_csr {
+  int64_t nrows, ncols, nnz;
+  int64_t* row_ptr; /* device, nrows+1 */
+  int32_t* col;     /* device, nnz */
+  void* val;        /* device, nnz values of dtype */
+  int32_t dtype;    /* SGC_F32 / SGC_F64 / SGC_I64 */
+  int32_t reserved;
+} sgc_csr;
+
+/* CSR_Cluster matrix (Sec. 3.1): rows merged into clusters of K_c <= 32 rows;
+ * per cluster the sorted union of the rows' column ids, a presence mask per
+ * union column (bit l: row l of the cluster has an entry there), and the
+ * values grouped by column with placeholders (PADDED) or without (MASKED).
+ * Original row ids are implicit: position p = cluster_ptr[c] + l holds
+ * original row perm[p]. */
+typedef struct sgc_csr_cluster {
+  int64_t nrows, ncols;        /* shape of A */
+  int64_t nclusters;
+  int64_t nucols;              /* total union columns = ucol_ptr[nclusters] */
+  int64_t nvals;               /* value slots = val_ptr[nclusters] */
+  int32_t layout;              /* SGC_LAYOUT_* */
+  int32_t dtype;
+  const int32_t* perm;         /* device, nrows: position -> original row (a permutation) */
+  const int64_t* cluster_ptr;  /* device, nclusters+1: cluster c = positions [cluster_ptr[c], cluster_ptr[c+1]) */
+  int64_t* ucol_ptr;           /* device, nclusters+1 */
+  int32_t* ucol;               /* device, nucols: sorted union column ids per cluster */
+  uint32_t* mask;              /* device, nucols */
+  int64_t* val_ptr;            /* device, nclusters+1 */
+  void* val;                   /* device, nvals */
+} sgc_csr_cluster;
+
+typedef struct sgc_options {
+  int32_t staging;          /* SGC_STAGING_*; default AUTO */
+  int32_t validate;         /* 1: check CSR / CSR_Cluster invariants on the device; default 0 */
+  int32_t stage_elems;      /* B elements per staging buffer, 0 = default (2048 numeric, 4096 symbolic) */
+  int32_t max_warps;        /* warps (cluster rows in flight) per CTA, 0 = default 8; 1..8 */
+  int32_t load_pct;         /* hash table fill limit in percent, 0 = default 75; 25..90 */
+  int32_t reserved[11];
+} sgc_options;
+
+/* Version of this ABI (SGC_ABI_VERSION). */
+int sgc_abi_version(void);
+
+/* Message for the calling thread's last failed call ("" if none).  The
+ * pointer stays valid until the thread's next call into the library. */
+const char* sgc_last_error(void);
+
+/* Fills *opt with the defaults. */
+int sgc_default_options(sgc_options* opt);
+
+/* Reads and clears the device status word kept in a spgemm workspace
+ * (a failed device check or timeout in an asynchronous call such as
+ * spgemm_numeric).  Synchronises.  Returns SGC_OK or the recorded error. */
+int sgc_workspace_status(void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * CSR_Cluster construction (Sec. 3.1; A_CSR_CLUSTER(A_CSR, clusters) at the
+ * end of Algorithms 2 and 3).
+ *
+ * csr_cluster_build_count: for clusters given by perm / cluster_ptr over the
+ * rows of A (CSR), writes ucol_ptr[0..nclusters] (prefix of union sizes) and
+ * val_ptr[0..nclusters] (prefix of value slots for `layout`), both device
+ * int64 arrays of nclusters+1 owned by the caller, and returns the totals in
+ * *nucols_host and *nvals_host.  ws: device workspace of at least
+ * csr_cluster_build_workspace_size(nclusters) bytes.  Checks on the device
+ * that perm is a permutation and every cluster has 1..32 rows
+ * (SGC_DEVICE_CHECK_FAILED otherwise).  Synchronises.
+ * ------------------------------------------------------------------------- */
+int csr_cluster_build_workspace_size(int64_t nrows, int64_t nclusters, size_t* bytes);
+int csr_cluster_build_count(const sgc_csr* A, const int32_t* perm, const int64_t* cluster_ptr,
+                            int64_t nclusters, int32_t layout, int64_t* ucol_ptr, int64_t* val_ptr,
+                            int64_t* nucols_host, int64_t* nvals_host, void* ws, size_t ws_bytes,
+                            void* stream);
+
+/* csr_cluster_build: fills out->ucol, out->mask and out->val (arrays of
+ * out->nucols / out->nucols / out->nvals elements allocated by the caller)
+ * from A.  out must carry nrows, ncols, nclusters, nucols, nvals, layout,
+ * dtype, perm, cluster_ptr, ucol_ptr and val_ptr as returned by
+ * csr_cluster_build_count for the same inputs.  Asynchronous. */
+int csr_cluster_build(const sgc_csr* A, sgc_csr_cluster* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Cluster-wise SpGEMM C = A * B, A in CSR_Cluster (Algorithm 1,
+ * ClusterWise_SpGEMM; Sec. 3.1 "Access pattern"): each cluster is one unit of
+ * work; every B row k in the cluster's column union is staged in shared
+ * memory once and applied to every row of the cluster that has a_lk.
+ * Split into the symbolic and numeric phases of Sec. 2.2.
+ *
+ * spgemm_workspace_size: bytes of device workspace the two calls need for
+ * these shapes (independent of values; the same workspace may serve both).
+ *
+ * spgemm_symbolic: writes C's row pointer c_row_ptr[0..A.nrows] (device,
+ * int64, caller-owned, in original row order) and, when c_nnz_host is not
+ * NULL, stores nnz(C) there and synchronises; with c_nnz_host NULL it is
+ * asynchronous and nnz(C) is c_row_ptr[nrows] on the device.
+ *
+ * spgemm_numeric: C->row_ptr must hold the symbolic result; writes C->col and
+ * C->val (nnz(C) elements each, caller-allocated, dtype = A's).  Asynchronous;
+ * device-side failures are reported by sgc_workspace_status.
+ * opt may be NULL (defaults).
+ * ------------------------------------------------------------------------- */
+int spgemm_workspace_size(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_options* opt,
+                          size_t* bytes);
+int spgemm_symbolic(const sgc_csr_cluster* A, const sgc_csr* B, int64_t* c_row_ptr,
+                    int64_t* c_nnz_host, void* ws, size_t ws_bytes, const sgc_options* opt,
+                    void* stream);
+int spgemm_numeric(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, void* ws,
+                   size_t ws_bytes, const sgc_options* opt, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Plain row-wise Gustavson SpGEMM C = A * B with A in CSR (Sec. 2.2, Fig. 1):
+ * the comparison method.  Same binning, hash accumulators, sort and copy-out
+ * as the cluster-wise path, one row per warp, B rows read straight from
+ * global memory.  Same contracts as spgemm_workspace_size / spgemm_symbolic /
+ * spgemm_numeric.
+ * ------------------------------------------------------------------------- */
+int spgemm_rowwise_workspace_size(const sgc_csr* A, const sgc_csr* B, const sgc_options* opt,
+                                  size_t* bytes);
+int spgemm_rowwise_symbolic(const sgc_csr* A, const sgc_csr* B, int64_t* c_row_ptr,
+                            int64_t* c_nnz_host, void* ws, size_t ws_bytes,
+                            const sgc_options* opt, void* stream);
+int spgemm_rowwise_numeric(const sgc_csr* A, const sgc_csr* B, sgc_csr* C, void* ws,
+                           size_t ws_bytes, const sgc_options* opt, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGC_H_ */

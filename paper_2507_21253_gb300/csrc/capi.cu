@@ -1,0 +1,402 @@
+// C ABI of libsgc (declared in include/sgc.h): argument checks, workspace
+// carving, status words, and the sequence of launches of each call.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "sgc_device.cuh"
+#include "sgc_kernels.h"
+
+namespace sgc {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+  return n;
+}
+
+ResolvedOptions resolve(const sgc_options* opt) {
+  ResolvedOptions r{};
+  r.staging = opt ? opt->staging : SGC_STAGING_AUTO;
+  r.validate = opt ? opt->validate : 0;
+  r.stage_elems_num = (opt && opt->stage_elems > 0) ? opt->stage_elems : 2048;
+  r.stage_elems_sym = (opt && opt->stage_elems > 0) ? opt->stage_elems : 4096;
+  r.max_warps = (opt && opt->max_warps > 0) ? opt->max_warps : 8;
+  if (r.max_warps > 8) r.max_warps = 8;
+  r.load_pct = (opt && opt->load_pct > 0) ? opt->load_pct : 75;
+  if (r.load_pct < 25) r.load_pct = 25;
+  if (r.load_pct > 90) r.load_pct = 90;
+  return r;
+}
+
+namespace {
+
+struct SpWs {
+  DevStatus* status;
+  BinOut bins;
+  int64_t* scan_tmp;
+  size_t bytes;
+};
+
+SpWs carve_sp(void* base, size_t cap, int64_t nrows, int64_t ncl) {
+  Carver cv(base, cap);
+  SpWs w{};
+  w.status = cv.take<DevStatus>(4);
+  w.bins.count = cv.take<int32_t>(NBIN_ALL);
+  w.bins.dense_items = cv.take<int32_t>((int64_t)NDB * ncl);
+  w.bins.row_items = cv.take<int64_t>((int64_t)NRB * nrows);
+  w.bins.heavy_items = cv.take<int64_t>(nrows);
+  w.bins.uc_rec = cv.take<int32_t>(ncl);
+  w.bins.nout_rec = cv.take<int32_t>(ncl);
+  w.bins.ncl = ncl;
+  w.bins.nrows = nrows;
+  w.scan_tmp = cv.take<int64_t>(scan_tmp_elems(nrows));
+  w.bytes = cv.off + 256;
+  return w;
+}
+
+#define SGC_FAIL(code, msg)         \
+  do {                              \
+    ::sgc::set_last_error(msg);     \
+    return code;                    \
+  } while (0)
+
+#define SGC_CUDA(expr)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      ::sgc::set_last_error(std::string(#expr) + " failed: " + cudaGetErrorString(e_));      \
+      return SGC_CUDA_ERROR;                                                                  \
+    }                                                                                         \
+  } while (0)
+
+int map_status(const DevStatus& s) {
+  if (s.code == DEV_OK) return SGC_OK;
+  char buf[160];
+  std::snprintf(buf, sizeof buf, "device check failed: code %d at site %d (item %lld)", s.code, s.where,
+                (long long)s.info);
+  set_last_error(buf);
+  if (s.code == DEV_TIMEOUT) return SGC_DEVICE_TIMEOUT;
+  return SGC_DEVICE_CHECK_FAILED;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int dtype_bytes(int dt) { return dt == SGC_F32 ? 4 : 8; }
+
+int check_csr(const sgc_csr* M, const char* name, bool need_val) {
+  if (!M) SGC_FAIL(SGC_INVALID_ARG, std::string(name) + " is NULL");
+  if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0) SGC_FAIL(SGC_INVALID_ARG, std::string(name) + ": negative size");
+  if (M->ncols > 0x7fffffffll) SGC_FAIL(SGC_UNSUPPORTED, std::string(name) + ": ncols must fit int32");
+  if (!M->row_ptr) SGC_FAIL(SGC_INVALID_ARG, std::string(name) + ": row_ptr is NULL");
+  if (M->nnz > 0 && (!M->col || (need_val && !M->val)))
+    SGC_FAIL(SGC_INVALID_ARG, std::string(name) + ": col/val NULL with nnz > 0");
+  if (M->dtype < SGC_F32 || M->dtype > SGC_I64) SGC_FAIL(SGC_UNSUPPORTED, std::string(name) + ": unknown dtype");
+  return SGC_OK;
+}
+
+int check_cluster(const sgc_csr_cluster* A, bool need_val) {
+  if (!A) SGC_FAIL(SGC_INVALID_ARG, "A is NULL");
+  if (A->nrows < 0 || A->ncols < 0 || A->nclusters < 0 || A->nucols < 0 || A->nvals < 0)
+    SGC_FAIL(SGC_INVALID_ARG, "A: negative size");
+  if (A->nclusters > A->nrows || (A->nrows > 0 && A->nclusters == 0))
+    SGC_FAIL(SGC_INVALID_ARG, "A: nclusters inconsistent with nrows");
+  if (A->nclusters > (1ll << 26)) SGC_FAIL(SGC_UNSUPPORTED, "A: more than 2^26 clusters");
+  if (A->nrows > 0 && (!A->perm || !A->cluster_ptr || !A->ucol_ptr || !A->val_ptr))
+    SGC_FAIL(SGC_INVALID_ARG, "A: NULL perm / cluster_ptr / ucol_ptr / val_ptr");
+  if (A->nucols > 0 && (!A->ucol || !A->mask)) SGC_FAIL(SGC_INVALID_ARG, "A: NULL ucol / mask");
+  if (need_val && A->nvals > 0 && !A->val) SGC_FAIL(SGC_INVALID_ARG, "A: NULL val");
+  if (A->layout != SGC_LAYOUT_PADDED && A->layout != SGC_LAYOUT_MASKED) SGC_FAIL(SGC_UNSUPPORTED, "A: bad layout");
+  if (A->dtype < SGC_F32 || A->dtype > SGC_I64) SGC_FAIL(SGC_UNSUPPORTED, "A: unknown dtype");
+  return SGC_OK;
+}
+
+AClusterView cview(const sgc_csr_cluster* A, bool with_val) {
+  return AClusterView{A->perm, A->cluster_ptr, A->ucol_ptr, A->ucol, A->mask, A->val_ptr,
+                      with_val ? A->val : nullptr, A->nclusters, A->nrows, A->layout};
+}
+BView bview(const sgc_csr* B, bool with_val) {
+  return BView{B->row_ptr, B->col, with_val ? B->val : nullptr, B->nrows, B->ncols, B->nnz};
+}
+
+int resolve_mode(const ResolvedOptions& o, const sgc_csr* B, bool numeric, int* mode) {
+  const bool al = aligned16(B->col) && (!numeric || aligned16(B->val));
+  if (o.staging == SGC_STAGING_LDG) {
+    *mode = 0;
+  } else if (o.staging == SGC_STAGING_BULK) {
+    if (!al) SGC_FAIL(SGC_UNSUPPORTED, "bulk staging needs 16-byte aligned B col/val base pointers");
+    *mode = 1;
+  } else if (o.staging == SGC_STAGING_AUTO) {
+    *mode = al ? 1 : 0;
+  } else {
+    SGC_FAIL(SGC_INVALID_ARG, "unknown staging mode");
+  }
+  return SGC_OK;
+}
+
+int finish_symbolic(int64_t* c_row_ptr, int64_t nrows, int64_t* c_nnz_host, DevStatus* status, int64_t* scan_tmp,
+                    cudaStream_t s) {
+  SGC_CUDA(inclusive_scan_i64(c_row_ptr + 1, nrows, scan_tmp, s));
+  if (!c_nnz_host) return SGC_OK;
+  int64_t nnz = 0;
+  DevStatus st{};
+  SGC_CUDA(cudaMemcpyAsync(&nnz, c_row_ptr + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SGC_CUDA(cudaMemcpyAsync(&st, status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  SGC_CUDA(cudaStreamSynchronize(s));
+  *c_nnz_host = nnz;
+  return map_status(st);
+}
+
+// Waits for the stream and returns the recorded device status (used after
+// validation kernels so that invalid input never reaches the product kernels).
+int sync_status(DevStatus* status, cudaStream_t s) {
+  DevStatus st{};
+  SGC_CUDA(cudaMemcpyAsync(&st, status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  SGC_CUDA(cudaStreamSynchronize(s));
+  return map_status(st);
+}
+
+}  // namespace
+}  // namespace sgc
+
+using namespace sgc;
+
+extern "C" {
+
+int sgc_abi_version(void) { return SGC_ABI_VERSION; }
+
+const char* sgc_last_error(void) { return g_last_error.c_str(); }
+
+int sgc_default_options(sgc_options* opt) {
+  if (!opt) SGC_FAIL(SGC_INVALID_ARG, "opt is NULL");
+  std::memset(opt, 0, sizeof(*opt));
+  opt->staging = SGC_STAGING_AUTO;
+  return SGC_OK;
+}
+
+int sgc_workspace_status(void* ws, size_t ws_bytes, void* stream) {
+  if (!ws || ws_bytes < sizeof(DevStatus)) SGC_FAIL(SGC_INVALID_ARG, "workspace too small or NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevStatus st{};
+  SGC_CUDA(cudaMemcpyAsync(&st, ws, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  SGC_CUDA(cudaMemsetAsync(ws, 0, sizeof(DevStatus), s));
+  SGC_CUDA(cudaStreamSynchronize(s));
+  return map_status(st);
+}
+
+// ---------------------------------------------------------------------------
+// CSR_Cluster construction
+// ---------------------------------------------------------------------------
+int csr_cluster_build_workspace_size(int64_t nrows, int64_t nclusters, size_t* bytes) {
+  if (!bytes || nrows < 0 || nclusters < 0) SGC_FAIL(SGC_INVALID_ARG, "bad arguments");
+  Carver cv(nullptr, 0);
+  cv.take<DevStatus>(4);
+  cv.take<int32_t>(nrows > 0 ? nrows : 1);
+  cv.take<int64_t>(scan_tmp_elems(nclusters));
+  *bytes = cv.off + 256;
+  return SGC_OK;
+}
+
+int csr_cluster_build_count(const sgc_csr* A, const int32_t* perm, const int64_t* cluster_ptr, int64_t nclusters,
+                            int32_t layout, int64_t* ucol_ptr, int64_t* val_ptr, int64_t* nucols_host,
+                            int64_t* nvals_host, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_csr(A, "A", false);
+  if (rc) return rc;
+  if (!nucols_host || !nvals_host || !ucol_ptr || !val_ptr) SGC_FAIL(SGC_INVALID_ARG, "NULL output");
+  if (layout != SGC_LAYOUT_PADDED && layout != SGC_LAYOUT_MASKED) SGC_FAIL(SGC_UNSUPPORTED, "bad layout");
+  if (nclusters < 0 || nclusters > A->nrows || (A->nrows > 0 && nclusters == 0))
+    SGC_FAIL(SGC_INVALID_ARG, "nclusters inconsistent with A.nrows");
+  if (A->nrows > 0 && (!perm || !cluster_ptr)) SGC_FAIL(SGC_INVALID_ARG, "NULL perm / cluster_ptr");
+  size_t need = 0;
+  csr_cluster_build_workspace_size(A->nrows, nclusters, &need);
+  if (!ws || ws_bytes < need) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  Carver cv(ws, ws_bytes);
+  DevStatus* status = cv.take<DevStatus>(4);
+  int32_t* seen = cv.take<int32_t>(A->nrows > 0 ? A->nrows : 1);
+  int64_t* scan_tmp = cv.take<int64_t>(scan_tmp_elems(nclusters));
+  SGC_CUDA(cudaMemsetAsync(status, 0, sizeof(DevStatus), s));
+  if (nclusters == 0) {
+    SGC_CUDA(cudaMemsetAsync(ucol_ptr, 0, sizeof(int64_t), s));
+    SGC_CUDA(cudaMemsetAsync(val_ptr, 0, sizeof(int64_t), s));
+    SGC_CUDA(cudaStreamSynchronize(s));
+    *nucols_host = *nvals_host = 0;
+    return SGC_OK;
+  }
+  SGC_CUDA(cluster_build_count_run(A->row_ptr, A->col, perm, cluster_ptr, nclusters, A->nrows, layout, ucol_ptr,
+                                   val_ptr, seen, scan_tmp, status, s));
+  DevStatus st{};
+  SGC_CUDA(cudaMemcpyAsync(nucols_host, ucol_ptr + nclusters, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SGC_CUDA(cudaMemcpyAsync(nvals_host, val_ptr + nclusters, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SGC_CUDA(cudaMemcpyAsync(&st, status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  SGC_CUDA(cudaStreamSynchronize(s));
+  return map_status(st);
+}
+
+int csr_cluster_build(const sgc_csr* A, sgc_csr_cluster* out, void* stream) {
+  int rc = check_csr(A, "A", true);
+  if (rc) return rc;
+  if (!out) SGC_FAIL(SGC_INVALID_ARG, "out is NULL");
+  rc = check_cluster(out, true);
+  if (rc) return rc;
+  if (out->dtype != A->dtype) SGC_FAIL(SGC_UNSUPPORTED, "out.dtype differs from A.dtype");
+  if (out->nrows != A->nrows || out->ncols != A->ncols) SGC_FAIL(SGC_INVALID_ARG, "out shape differs from A");
+  cudaStream_t s = (cudaStream_t)stream;
+  AClusterView v = cview(out, true);
+  SGC_CUDA(cluster_build_fill_run(A->row_ptr, A->col, A->val, dtype_bytes(A->dtype), v, out->ucol, out->mask,
+                                  out->val, s));
+  return SGC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Cluster-wise SpGEMM
+// ---------------------------------------------------------------------------
+int spgemm_workspace_size(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_options* opt, size_t* bytes) {
+  (void)opt;
+  if (!A || !B || !bytes) SGC_FAIL(SGC_INVALID_ARG, "NULL argument");
+  *bytes = carve_sp(nullptr, 0, A->nrows, A->nclusters).bytes;
+  return SGC_OK;
+}
+
+static int check_product(const sgc_csr_cluster* A, const sgc_csr* B, bool numeric) {
+  int rc = check_cluster(A, numeric);
+  if (rc) return rc;
+  rc = check_csr(B, "B", numeric);
+  if (rc) return rc;
+  if (A->ncols != B->nrows) SGC_FAIL(SGC_INVALID_ARG, "A.ncols != B.nrows");
+  if (A->dtype != B->dtype) SGC_FAIL(SGC_UNSUPPORTED, "A and B value types differ");
+  return SGC_OK;
+}
+
+int spgemm_symbolic(const sgc_csr_cluster* A, const sgc_csr* B, int64_t* c_row_ptr, int64_t* c_nnz_host, void* ws,
+                    size_t ws_bytes, const sgc_options* opt, void* stream) {
+  int rc = check_product(A, B, false);
+  if (rc) return rc;
+  if (!c_row_ptr) SGC_FAIL(SGC_INVALID_ARG, "c_row_ptr is NULL");
+  SpWs w = carve_sp(ws, ws_bytes, A->nrows, A->nclusters);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const ResolvedOptions o = resolve(opt);
+  Launch L{s, o, num_sms(), 0};
+  rc = resolve_mode(o, B, false, &L.mode);
+  if (rc) return rc;
+  SGC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+  SGC_CUDA(cudaMemsetAsync(c_row_ptr, 0, sizeof(int64_t), s));
+  if (A->nrows == 0) return finish_symbolic(c_row_ptr, 0, c_nnz_host, w.status, w.scan_tmp, s);
+  const AClusterView av = cview(A, false);
+  if (o.validate) {
+    SGC_CUDA(validate_cluster_run(av, A->ncols, w.status, s));
+    SGC_CUDA(validate_csr_run(B->row_ptr, B->col, B->nrows, B->ncols, B->nnz, w.status, 52, s));
+    rc = sync_status(w.status, s);
+    if (rc) return rc;
+  }
+  SGC_CUDA((run_cluster_phase<true, SGC_F64>(av, bview(B, false), CView{}, c_row_ptr, w.bins, w.status, L)));
+  return finish_symbolic(c_row_ptr, A->nrows, c_nnz_host, w.status, w.scan_tmp, s);
+}
+
+int spgemm_numeric(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, void* ws, size_t ws_bytes,
+                   const sgc_options* opt, void* stream) {
+  int rc = check_product(A, B, true);
+  if (rc) return rc;
+  rc = check_csr(C, "C", true);
+  if (rc) return rc;
+  if (C->nrows != A->nrows || C->ncols != B->ncols || C->dtype != A->dtype)
+    SGC_FAIL(SGC_INVALID_ARG, "C shape or dtype inconsistent with A*B");
+  SpWs w = carve_sp(ws, ws_bytes, A->nrows, A->nclusters);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const ResolvedOptions o = resolve(opt);
+  Launch L{s, o, num_sms(), 0};
+  rc = resolve_mode(o, B, true, &L.mode);
+  if (rc) return rc;
+  SGC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+  if (A->nrows == 0 || C->nnz == 0) return SGC_OK;
+  const AClusterView av = cview(A, true);
+  const BView bv = bview(B, true);
+  const CView cv{C->row_ptr, C->col, C->val};
+  switch (A->dtype) {
+    case SGC_F32: SGC_CUDA((run_cluster_phase<false, SGC_F32>(av, bv, cv, C->row_ptr, w.bins, w.status, L))); break;
+    case SGC_F64: SGC_CUDA((run_cluster_phase<false, SGC_F64>(av, bv, cv, C->row_ptr, w.bins, w.status, L))); break;
+    default: SGC_CUDA((run_cluster_phase<false, SGC_I64>(av, bv, cv, C->row_ptr, w.bins, w.status, L))); break;
+  }
+  return SGC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Row-wise SpGEMM (comparison method)
+// ---------------------------------------------------------------------------
+int spgemm_rowwise_workspace_size(const sgc_csr* A, const sgc_csr* B, const sgc_options* opt, size_t* bytes) {
+  (void)opt;
+  if (!A || !B || !bytes) SGC_FAIL(SGC_INVALID_ARG, "NULL argument");
+  *bytes = carve_sp(nullptr, 0, A->nrows, 0).bytes;
+  return SGC_OK;
+}
+
+static int check_rows_product(const sgc_csr* A, const sgc_csr* B, bool numeric) {
+  int rc = check_csr(A, "A", numeric);
+  if (rc) return rc;
+  rc = check_csr(B, "B", numeric);
+  if (rc) return rc;
+  if (A->ncols != B->nrows) SGC_FAIL(SGC_INVALID_ARG, "A.ncols != B.nrows");
+  if (A->dtype != B->dtype) SGC_FAIL(SGC_UNSUPPORTED, "A and B value types differ");
+  return SGC_OK;
+}
+
+int spgemm_rowwise_symbolic(const sgc_csr* A, const sgc_csr* B, int64_t* c_row_ptr, int64_t* c_nnz_host, void* ws,
+                            size_t ws_bytes, const sgc_options* opt, void* stream) {
+  int rc = check_rows_product(A, B, false);
+  if (rc) return rc;
+  if (!c_row_ptr) SGC_FAIL(SGC_INVALID_ARG, "c_row_ptr is NULL");
+  SpWs w = carve_sp(ws, ws_bytes, A->nrows, 0);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const ResolvedOptions o = resolve(opt);
+  Launch L{s, o, num_sms(), 0};
+  SGC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+  SGC_CUDA(cudaMemsetAsync(c_row_ptr, 0, sizeof(int64_t), s));
+  if (A->nrows == 0) return finish_symbolic(c_row_ptr, 0, c_nnz_host, w.status, w.scan_tmp, s);
+  if (o.validate) {
+    SGC_CUDA(validate_csr_run(A->row_ptr, A->col, A->nrows, A->ncols, A->nnz, w.status, 53, s));
+    SGC_CUDA(validate_csr_run(B->row_ptr, B->col, B->nrows, B->ncols, B->nnz, w.status, 52, s));
+    rc = sync_status(w.status, s);
+    if (rc) return rc;
+  }
+  const ACsrView av{A->row_ptr, A->col, nullptr, A->nrows};
+  SGC_CUDA((run_rows_phase<true, SGC_F64>(av, bview(B, false), CView{}, c_row_ptr, w.bins, w.status, L)));
+  return finish_symbolic(c_row_ptr, A->nrows, c_nnz_host, w.status, w.scan_tmp, s);
+}
+
+int spgemm_rowwise_numeric(const sgc_csr* A, const sgc_csr* B, sgc_csr* C, void* ws, size_t ws_bytes,
+                           const sgc_options* opt, void* stream) {
+  int rc = check_rows_product(A, B, true);
+  if (rc) return rc;
+  rc = check_csr(C, "C", true);
+  if (rc) return rc;
+  if (C->nrows != A->nrows || C->ncols != B->ncols || C->dtype != A->dtype)
+    SGC_FAIL(SGC_INVALID_ARG, "C shape or dtype inconsistent with A*B");
+  SpWs w = carve_sp(ws, ws_bytes, A->nrows, 0);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const ResolvedOptions o = resolve(opt);
+  Launch L{s, o, num_sms(), 0};
+  SGC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+  if (A->nrows == 0 || C->nnz == 0) return SGC_OK;
+  const ACsrView av{A->row_ptr, A->col, A->val, A->nrows};
+  const BView bv = bview(B, true);
+  const CView cv{C->row_ptr, C->col, C->val};
+  switch (A->dtype) {
+    case SGC_F32: SGC_CUDA((run_rows_phase<false, SGC_F32>(av, bv, cv, C->row_ptr, w.bins, w.status, L))); break;
+    case SGC_F64: SGC_CUDA((run_rows_phase<false, SGC_F64>(av, bv, cv, C->row_ptr, w.bins, w.status, L))); break;
+    default: SGC_CUDA((run_rows_phase<false, SGC_I64>(av, bv, cv, C->row_ptr, w.bins, w.status, L))); break;
+  }
+  return SGC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Binning of work before each phase (Sec. 2.2: the symbolic phase sizes C,
+// the numeric phase fills it).  Clusters go to the cluster kernel when their
+// staged footprint fits in shared memory (bins = shared-memory budget
+// classes); otherwise their rows go to the row-level kernels, binned by hash
+// table size, and rows beyond the table limit go to the heavy-row kernel.
+// Symbolic bins use the flop upper bound ub_l = sum_k nnz(B_k) (capped by
+// ncols(B)); numeric bins use the exact counts the symbolic phase produced.
+#pragma once
+
+#include "k_cluster.cuh"
+
+namespace sgc {
+
+__device__ __forceinline__ void push_dense(const BinOut& o, int b, int32_t c) {
+  const int32_t idx = atomicAdd(&o.count[b], 1);
+  o.dense_items[(int64_t)b * o.ncl + idx] = c;
+}
+__device__ __forceinline__ void push_row(const BinOut& o, int lg, int64_t item) {
+  const int b = lg - LOG2T_MIN;
+  const int32_t idx = atomicAdd(&o.count[NDB + b], 1);
+  o.row_items[(int64_t)b * o.nrows + idx] = item;
+}
+__device__ __forceinline__ void push_heavy(const BinOut& o, int64_t item) {
+  const int32_t idx = atomicAdd(&o.count[BIN_HEAVY], 1);
+  o.heavy_items[idx] = item;
+}
+
+// Smallest dense budget class that holds `need` bytes, or -1.
+__device__ __forceinline__ int dense_class(int64_t need) {
+  for (int b = 0; b < NDB; ++b)
+    if (need <= dense_budget(b)) return b;
+  return -1;
+}
+
+// Classify one row by its bound h (symbolic) or exact count (numeric); h > 0.
+__device__ __forceinline__ void classify_row(const BinOut& o, int64_t item, int64_t h, int64_t heavy_limit,
+                                             int load_pct) {
+  if (h > heavy_limit) {
+    push_heavy(o, item);
+    return;
+  }
+  const int lg = table_log2(h, load_pct);
+  if (lg > LOG2T_MAX)
+    push_heavy(o, item);
+  else
+    push_row(o, lg, item);
+}
+
+// ---- cluster path, symbolic: warp per cluster ------------------------------
+static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, BView B, int64_t* c_rp, BinOut o,
+                                                         int load_pct, int bulk, int use_dense) {
+  __shared__ unsigned long long s_ub[8][32];
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t c = gw; c < A.ncl; c += nwarps) {
+    const int64_t p0 = A.cptr[c];
+    const int K = (int)(A.cptr[c + 1] - p0);
+    const int64_t u0 = A.uptr[c], u1 = A.uptr[c + 1];
+    s_ub[w][lane] = 0;
+    __syncwarp();
+    int64_t U = 0;
+    for (int64_t t = u0 + lane; t < u1; t += 32) {
+      const int32_t k = A.ucol[t];
+      const int64_t len = B.rp[k + 1] - B.rp[k];
+      U += len;
+      uint32_t m = A.mask[t];
+      while (m) {
+        const int l = __ffs(m) - 1;
+        m &= m - 1;
+        atomicAdd(&s_ub[w][l], (unsigned long long)len);
+      }
+    }
+    U = warp_sum(U);
+    __syncwarp();
+    const int64_t T = u1 - u0;
+    int cls = -1;
+    if (use_dense && U < (1ll << 28) && T < (1ll << 24)) {
+      const int LH = table_log2(min64(U, B.ncols), 75);
+      const DenseLayout L = dense_layout(true, T, U, LH, 0, K, 4, 8, bulk != 0);
+      cls = dense_class(L.total);
+    }
+    if (lane == 0) {
+      o.uc_rec[c] = (int32_t)min64(U, 0x7fffffff);
+      o.nout_rec[c] = -1;
+      if (cls >= 0) push_dense(o, cls, (int32_t)c);
+    }
+    if (cls < 0 && lane < K) {
+      const int64_t ub = (int64_t)s_ub[w][lane];
+      const int64_t row = A.perm[p0 + lane];
+      if (ub == 0)
+        c_rp[row + 1] = 0;
+      else
+        classify_row(o, (c << 5) | lane, min64(ub, B.ncols), HEAVY_SYM, load_pct);
+    }
+    __syncwarp();
+  }
+}
+
+// ---- cluster path, numeric: warp per cluster -------------------------------
+static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, BView B, const int64_t* c_rp, BinOut o,
+                                                         int load_pct, int bulk, int in_bytes, int acc_bytes) {
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t c = gw; c < A.ncl; c += nwarps) {
+    const int64_t p0 = A.cptr[c];
+    const int K = (int)(A.cptr[c + 1] - p0);
+    const int64_t T = A.uptr[c + 1] - A.uptr[c];
+    const int32_t nout = o.nout_rec[c];
+    int cls = -1;
+    if (nout >= 0) {
+      const int LH = table_log2(nout, 75);
+      const DenseLayout L = dense_layout(false, T, o.uc_rec[c], LH, nout, K, in_bytes, acc_bytes, bulk != 0);
+      cls = dense_class(L.total);
+    }
+    if (cls >= 0) {
+      if (lane == 0) push_dense(o, cls, (int32_t)c);
+    } else if (lane < K) {
+      const int64_t row = A.perm[p0 + lane];
+      const int64_t cnt = c_rp[row + 1] - c_rp[row];
+      if (cnt > 0) classify_row(o, (c << 5) | lane, cnt, HEAVY_NUM, load_pct);
+    }
+  }
+}
+
+// ---- row-wise path, symbolic: warp per row ---------------------------------
+static __global__ void __launch_bounds__(256) k_bin_rows_sym(ACsrView A, BView B, int64_t* c_rp, BinOut o, int load_pct) {
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t r = gw; r < A.nrows; r += nwarps) {
+    int64_t ub = 0;
+    for (int64_t p = A.rp[r] + lane; p < A.rp[r + 1]; p += 32) {
+      const int32_t k = A.col[p];
+      ub += B.rp[k + 1] - B.rp[k];
+    }
+    ub = warp_sum(ub);
+    if (lane == 0) {
+      if (ub == 0)
+        c_rp[r + 1] = 0;
+      else
+        classify_row(o, r, min64(ub, B.ncols), HEAVY_SYM, load_pct);
+    }
+  }
+}
+
+// ---- row-wise path, numeric: thread per row --------------------------------
+static __global__ void __launch_bounds__(256) k_bin_rows_num(int64_t nrows, const int64_t* c_rp, BinOut o, int load_pct) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cnt = c_rp[r + 1] - c_rp[r];
+    if (cnt > 0) classify_row(o, r, cnt, HEAVY_NUM, load_pct);
+  }
+}
+
+}  // namespace sgc

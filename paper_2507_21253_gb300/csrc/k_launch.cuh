@@ -1,0 +1,125 @@
+// Host launchers of one SpGEMM phase: bin, then one launch per non-trivial
+// bin class (persistent grids that read their item count on the device, so
+// the sequence needs no host synchronisation and can be graph-captured).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "k_bins.cuh"
+
+namespace sgc {
+
+template <class Kern>
+inline int occupancy(Kern kern, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess || n < 1) n = 1;
+  return n;
+}
+
+template <class Kern>
+inline cudaError_t allow_smem(Kern kern) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX);
+}
+
+inline unsigned grid_for(int64_t units, int64_t per_cta, int sms, int occ) {
+  int64_t need = (units + per_cta - 1) / per_cta;
+  int64_t cap = (int64_t)sms * occ;
+  int64_t g = need < cap ? need : cap;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// Launch the row-hash and heavy kernels for all row bins.
+template <bool SYM, int DT, int SRC>
+cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const BView& B, const CView& C,
+                            int64_t* c_rp, const BinOut& bins, void* status, const Launch& L) {
+  using Acc = typename VT<DT>::Acc;
+  auto kh = k_row_hash<SYM, DT, SRC>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = allow_smem(kh);
+    if (e != cudaSuccess) return e;
+  }
+  for (int lg = LOG2T_MIN; lg <= LOG2T_MAX; ++lg) {
+    const size_t per_warp = row_hash_smem(1, lg, SYM, sizeof(Acc));
+    int warps = L.o.max_warps;
+    while (warps > 1 && (size_t)warps * per_warp > (size_t)SMEM_MAX) --warps;
+    if ((size_t)warps * per_warp > (size_t)SMEM_MAX) continue;  // cannot happen for lg <= 13
+    const size_t smem = (size_t)warps * per_warp;
+    const int occ = occupancy(kh, warps * 32, smem);
+    const unsigned grid = grid_for(bins.nrows, warps, L.sms, occ);
+    const int b = lg - LOG2T_MIN;
+    kh<<<grid, warps * 32, smem, L.s>>>(Ac, Acl, B, C, c_rp, bins.row_items + (int64_t)b * bins.nrows,
+                                         bins.count + NDB + b, lg, status);
+  }
+  auto kv = k_row_heavy<SYM, DT, SRC>;
+  const size_t hsmem = row_heavy_smem(SYM, sizeof(Acc));
+  if (!attr) {
+    cudaError_t e = allow_smem(kv);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int occ = occupancy(kv, HEAVY_THREADS, hsmem);
+  const unsigned grid = grid_for(bins.nrows, 1, L.sms, occ);
+  kv<<<grid, HEAVY_THREADS, hsmem, L.s>>>(Ac, Acl, B, C, c_rp, bins.heavy_items, bins.count + BIN_HEAVY, status);
+  return cudaGetLastError();
+}
+
+template <bool SYM, int DT>
+cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView& C, int64_t* c_rp,
+                              const BinOut& bins, void* status, const Launch& L) {
+  using In = typename VT<DT>::In;
+  using Acc = typename VT<DT>::Acc;
+  cudaError_t e = cudaMemsetAsync(bins.count, 0, sizeof(int32_t) * NBIN_ALL, L.s);
+  if (e != cudaSuccess) return e;
+  const unsigned gb = grid_for(A.ncl, 8, L.sms, 8);
+  if (SYM)
+    k_bin_cluster_sym<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, 1);
+  else
+    k_bin_cluster_num<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, (int)sizeof(In),
+                                            (int)sizeof(Acc));
+  auto kd = k_cluster_dense<SYM, DT>;
+  static bool attr = false;
+  if (!attr) {
+    e = allow_smem(kd);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  for (int b = 0; b < NDB; ++b) {
+    const size_t smem = (size_t)dense_budget(b);
+    const int occ = occupancy(kd, CL_THREADS, smem);
+    const unsigned grid = grid_for(A.ncl, 1, L.sms, occ);
+    kd<<<grid, CL_THREADS, smem, L.s>>>(A, B, C, c_rp, bins.dense_items + (int64_t)b * bins.ncl, bins.count + b,
+                                         bins.nout_rec, bins.uc_rec, L.mode, status);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ACsrView none{};
+  return launch_row_bins<SYM, DT, SRC_CLUSTER>(none, A, B, C, c_rp, bins, status, L);
+}
+
+template <bool SYM, int DT>
+cudaError_t run_rows_phase(const ACsrView& A, const BView& B, const CView& C, int64_t* c_rp, const BinOut& bins,
+                           void* status, const Launch& L) {
+  cudaError_t e = cudaMemsetAsync(bins.count, 0, sizeof(int32_t) * NBIN_ALL, L.s);
+  if (e != cudaSuccess) return e;
+  if (SYM) {
+    const unsigned gb = grid_for(A.nrows, 8, L.sms, 8);
+    k_bin_rows_sym<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct);
+  } else {
+    const unsigned gb = grid_for(A.nrows, 256, L.sms, 8);
+    k_bin_rows_num<<<gb, 256, 0, L.s>>>(A.nrows, c_rp, bins, L.o.load_pct);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  AClusterView none{};
+  return launch_row_bins<SYM, DT, SRC_CSR>(A, none, B, C, c_rp, bins, status, L);
+}
+
+}  // namespace sgc
+
+#define SGC_INSTANTIATE_PHASES(SYM, DT)                                                                   \
+  template cudaError_t sgc::run_cluster_phase<SYM, DT>(const sgc::AClusterView&, const sgc::BView&,          \
+                                                       const sgc::CView&, int64_t*, const sgc::BinOut&, void*, \
+                                                       const sgc::Launch&);                                   \
+  template cudaError_t sgc::run_rows_phase<SYM, DT>(const sgc::ACsrView&, const sgc::BView&, const sgc::CView&, \
+                                                    int64_t*, const sgc::BinOut&, void*, const sgc::Launch&);

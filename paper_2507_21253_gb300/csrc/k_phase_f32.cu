@@ -1,0 +1,4 @@
+// Instantiates the numeric phase for SGC_F32 values.
+#include "k_launch.cuh"
+
+SGC_INSTANTIATE_PHASES(false, SGC_F32)

@@ -1,0 +1,4 @@
+// Instantiates the numeric phase for SGC_I64 values.
+#include "k_launch.cuh"
+
+SGC_INSTANTIATE_PHASES(false, SGC_I64)

@@ -1,0 +1,387 @@
+// Row-level SpGEMM kernels: one warp per output row with a shared-memory hash
+// accumulator (Sec. 2.2, Gustavson row-wise; hash accumulator as in the
+// paper's evaluation setup), and one CTA per heavy row with a dense
+// accumulator over column windows.  Rows come either from a CSR matrix (the
+// plain row-wise method) or from a CSR_Cluster matrix (rows of clusters whose
+// staged footprint exceeds the cluster kernel's shared memory).
+#pragma once
+
+#include "sgc_device.cuh"
+#include "sgc_kernels.h"
+
+namespace sgc {
+
+constexpr int SMEM_MAX = 232448;          // 227 KB opt-in shared memory per CTA
+constexpr uint32_t WAIT_LIMIT = 1u << 22;  // mbarrier polls before giving up (~0.3 s)
+
+enum { SRC_CSR = 0, SRC_CLUSTER = 1 };
+
+// ---------------------------------------------------------------------------
+// Row sources: iterate the (k, a_ik) entries of one row of A, warp-collectively.
+// f(k, a) is called by all lanes with warp-uniform arguments.
+// ---------------------------------------------------------------------------
+template <int DT, class F>
+__device__ __forceinline__ void for_row_entries_csr(const ACsrView& A, int64_t row, F&& f) {
+  using In = typename VT<DT>::In;
+  const int lane = lane_id();
+  const int64_t s = A.rp[row], e = A.rp[row + 1];
+  for (int64_t pb = s; pb < e; pb += 32) {
+    const int64_t p = pb + lane;
+    int32_t k = 0;
+    In a{};
+    if (p < e) {
+      k = A.col[p];
+      if (A.val) a = ((const In*)A.val)[p];
+    }
+    const int n = (int)min64(32, e - pb);
+    for (int i = 0; i < n; ++i) f(__shfl_sync(FULL, k, i), __shfl_sync(FULL, a, i));
+  }
+}
+
+template <int DT, class F>
+__device__ __forceinline__ void for_row_entries_cluster(const AClusterView& A, int64_t item, F&& f) {
+  using In = typename VT<DT>::In;
+  const int lane = lane_id();
+  const int64_t c = item >> 5;
+  const int l = (int)(item & 31);
+  const int K = (int)(A.cptr[c + 1] - A.cptr[c]);
+  const int64_t u0 = A.uptr[c], u1 = A.uptr[c + 1], v0 = A.vptr[c];
+  const uint32_t below = (1u << l) - 1u;
+  int64_t run = 0;  // MASKED: value slots before this 32-column block
+  for (int64_t tb = u0; tb < u1; tb += 32) {
+    const int64_t t = tb + lane;
+    uint32_t m = 0;
+    int32_t k = 0;
+    if (t < u1) {
+      m = A.mask[t];
+      k = A.ucol[t];
+    }
+    const int pc = __popc(m);
+    const int excl = warp_incl_scan(pc) - pc;
+    In a{};
+    if ((m >> l) & 1u) {
+      const int64_t vi = A.layout == SGC_LAYOUT_PADDED ? v0 + (t - u0) * K + l
+                                                       : v0 + run + excl + __popc(m & below);
+      if (A.val) a = ((const In*)A.val)[vi];
+    }
+    const unsigned has = __ballot_sync(FULL, (m >> l) & 1u);
+    unsigned rem = has;
+    while (rem) {
+      const int i = __ffs(rem) - 1;
+      rem &= rem - 1;
+      f(__shfl_sync(FULL, k, i), __shfl_sync(FULL, a, i));
+    }
+    run += __shfl_sync(FULL, excl + pc, 31);
+  }
+}
+
+template <int SRC, int DT, class F>
+__device__ __forceinline__ void for_row_entries(const ACsrView& Ac, const AClusterView& Acl, int64_t item,
+                                                F&& f) {
+  if constexpr (SRC == SRC_CSR)
+    for_row_entries_csr<DT>(Ac, item, f);
+  else
+    for_row_entries_cluster<DT>(Acl, item, f);
+}
+
+// Original row id and position of a row item.
+template <int SRC>
+__device__ __forceinline__ int64_t item_row(const AClusterView& Acl, int64_t item) {
+  if constexpr (SRC == SRC_CSR)
+    return item;
+  else
+    return Acl.perm[Acl.cptr[item >> 5] + (item & 31)];
+}
+
+// ---------------------------------------------------------------------------
+// Warp-per-row hash kernel (symbolic: count; numeric: accumulate, sort, write)
+// items: int64 row items of one bin; count at ws.bin_count[bin]
+// ---------------------------------------------------------------------------
+template <bool SYM, int DT, int SRC>
+__global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl, BView B, CView C,
+                                                  int64_t* c_rp_sym, const int64_t* items,
+                                                  const int32_t* count_ptr, int log2T, void* status) {
+  using In = typename VT<DT>::In;
+  using Acc = typename VT<DT>::Acc;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int T = 1 << log2T;
+  const int warps = blockDim.x >> 5;
+  const int w = threadIdx.x >> 5, lane = lane_id();
+  int32_t* keys = (int32_t*)sm + (size_t)w * T;
+  Acc* vals = SYM ? nullptr : (Acc*)(sm + (size_t)warps * T * 4) + (size_t)w * T;
+  DevStatus* st = (DevStatus*)status;
+  const int32_t count = *count_ptr;
+  for (int64_t it = (int64_t)blockIdx.x * warps + w; it < count; it += (int64_t)gridDim.x * warps) {
+    const int64_t item = items[it];
+    const int64_t row = item_row<SRC>(Acl, item);
+    int64_t out0 = 0, expect = 0;
+    if (!SYM) {
+      out0 = C.rp[row];
+      expect = C.rp[row + 1] - out0;
+    }
+    for (int i = lane; i < T; i += 32) {
+      keys[i] = EMPTY_KEY;
+      if (!SYM) vals[i] = Acc(0);
+    }
+    __syncwarp();
+    int64_t cnt = 0;
+    bool full = false;
+    for_row_entries<SRC, DT>(Ac, Acl, item, [&](int32_t k, In a) {
+      const int64_t s = B.rp[k], e = B.rp[k + 1];
+      for (int64_t q = s + lane; q < e; q += 32) {
+        bool nw;
+        const int slot = hash_find_or_insert(keys, log2T, B.col[q], &nw);
+        if (slot < 0) {
+          full = true;
+          continue;
+        }
+        if constexpr (SYM) {
+          cnt += nw;
+        } else {
+          vals[slot] = VT<DT>::add(vals[slot], VT<DT>::mul(a, ((const In*)B.val)[q]));
+        }
+      }
+      __syncwarp();
+    });
+    if (__any_sync(FULL, full)) {
+      if (lane == 0) raise(st, DEV_TABLE_FULL, 10, row);
+      continue;
+    }
+    if constexpr (SYM) {
+      const int64_t tot = warp_sum(cnt);
+      if (lane == 0) c_rp_sym[row + 1] = tot;
+    } else {
+      const int n = warp_compact(keys, vals, T);
+      if (n != expect) {
+        if (lane == 0) raise(st, DEV_INTERNAL, 11, row);
+        continue;
+      }
+      int P = 1;
+      while (P < n) P <<= 1;
+      for (int i = n + lane; i < P; i += 32) keys[i] = PAD_KEY;
+      __syncwarp();
+      warp_bitonic_sort(keys, vals, P);
+      for (int i = lane; i < n; i += 32) {
+        C.col[out0 + i] = keys[i];
+        ((In*)C.val)[out0 + i] = VT<DT>::out(vals[i]);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+inline size_t row_hash_smem(int warps, int log2T, bool sym, int acc_bytes) {
+  return (size_t)warps * ((size_t)4 << log2T) + (sym ? 0 : (size_t)warps * ((size_t)acc_bytes << log2T));
+}
+
+// ---------------------------------------------------------------------------
+// Heavy rows: one CTA per row, dense accumulator over windows of W columns.
+// The row's entries are gathered in chunks of blockDim into shared memory,
+// then warps take one entry (B row) each and update the window with
+// shared-memory atomics.  The numeric output of a window is emitted in
+// column order by scanning its presence bitmap.
+// ---------------------------------------------------------------------------
+constexpr int HEAVY_THREADS = 512;
+constexpr int HEAVY_SYM_WORDS = 16384;  // 64 KB bitmap: 524288 columns per pass
+constexpr int HEAVY_NUM_W = 16384;      // columns per numeric pass (128 KB of FP64)
+
+template <int DT>
+__device__ __forceinline__ void gather_chunk(const ACsrView& Ac, const AClusterView& Acl, int src, int64_t item,
+                                             int64_t cb, int32_t* s_k, typename VT<DT>::In* s_a, int64_t* tmp,
+                                             int* n_out, int64_t* run_inout) {
+  // Loads entry cb + threadIdx.x of the row (CSR: row entry; cluster: union column
+  // of the cluster, kept when its mask has the row's bit) into s_k / s_a, compacted.
+  using In = typename VT<DT>::In;
+  const int tid = threadIdx.x;
+  int keep = 0;
+  int32_t k = 0;
+  In a{};
+  if (src == SRC_CSR) {
+    const int64_t s = Ac.rp[item], e = Ac.rp[item + 1];
+    const int64_t p = s + cb + tid;
+    if (p < e) {
+      keep = 1;
+      k = Ac.col[p];
+      if (Ac.val) a = ((const In*)Ac.val)[p];
+    }
+  } else {
+    const int64_t c = item >> 5;
+    const int l = (int)(item & 31);
+    const int K = (int)(Acl.cptr[c + 1] - Acl.cptr[c]);
+    const int64_t u0 = Acl.uptr[c], u1 = Acl.uptr[c + 1], v0 = Acl.vptr[c];
+    const int64_t t = u0 + cb + tid;
+    uint32_t m = 0;
+    if (t < u1) m = Acl.mask[t];
+    int64_t tot;
+    const int64_t ex = block_excl_scan<int64_t>(__popc(m), tmp, &tot);
+    if ((m >> l) & 1u) {
+      keep = 1;
+      k = Acl.ucol[t];
+      const int64_t vi = Acl.layout == SGC_LAYOUT_PADDED
+                             ? v0 + (t - u0) * K + l
+                             : v0 + *run_inout + ex + __popc(m & ((1u << l) - 1u));
+      if (Acl.val) a = ((const In*)Acl.val)[vi];
+    }
+    __syncthreads();
+    if (tid == 0) *run_inout += tot;
+  }
+  int64_t nk;
+  const int64_t pos = block_excl_scan<int64_t>(keep, tmp, &nk);
+  if (keep) {
+    s_k[pos] = k;
+    s_a[pos] = a;
+  }
+  if (tid == 0) *n_out = (int)nk;
+  __syncthreads();
+}
+
+template <bool SYM, int DT, int SRC>
+__global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClusterView Acl, BView B, CView C,
+                                                             int64_t* c_rp_sym, const int64_t* items,
+                                                             const int32_t* count_ptr, void* status) {
+  using In = typename VT<DT>::In;
+  using Acc = typename VT<DT>::Acc;
+  extern __shared__ __align__(16) unsigned char sm[];
+  int64_t* tmp = (int64_t*)sm;                       // 34 int64
+  int* s_n = (int*)(sm + 34 * 8);                    // misc ints
+  int64_t* s_run = (int64_t*)(sm + 34 * 8 + 16);     // running MASKED offset
+  int32_t* s_k = (int32_t*)(sm + 512);
+  In* s_a = (In*)(sm + 512 + 4 * HEAVY_THREADS);
+  unsigned char* win = sm + 512 + 4 * HEAVY_THREADS + 8 * HEAVY_THREADS;
+  uint32_t* bits = (uint32_t*)win;
+  const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5, nw = blockDim.x >> 5;
+  constexpr int WCOLS = SYM ? HEAVY_SYM_WORDS * 32 : HEAVY_NUM_W;
+  constexpr int WWORDS = WCOLS / 32;
+  Acc* acc = (Acc*)(win + (SYM ? 0 : 4 * WWORDS));
+  DevStatus* st = (DevStatus*)status;
+  const int32_t count = *count_ptr;
+  for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+    const int64_t item = items[it];
+    const int64_t row = item_row<SRC>(Acl, item);
+    int64_t nent;
+    if constexpr (SRC == SRC_CSR) {
+      nent = Ac.rp[item + 1] - Ac.rp[item];
+    } else {
+      const int64_t c = item >> 5;
+      nent = Acl.uptr[c + 1] - Acl.uptr[c];
+    }
+    // ---- pass 0: column range of the row's products
+    int32_t lo = PAD_KEY, hi = -1;
+    if (tid == 0) *s_run = 0;
+    __syncthreads();
+    for (int64_t cb = 0; cb < nent; cb += blockDim.x) {
+      gather_chunk<DT>(Ac, Acl, SRC, item, cb, s_k, s_a, tmp, s_n, s_run);
+      const int n = *s_n;
+      for (int i = tid; i < n; i += blockDim.x) {
+        const int32_t k = s_k[i];
+        const int64_t s = B.rp[k], e = B.rp[k + 1];
+        if (e > s) {
+          lo = min(lo, B.col[s]);
+          hi = max(hi, B.col[e - 1]);
+        }
+      }
+      __syncthreads();
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    if (lane == 0) {
+      tmp[w] = lo;
+      tmp[16 + w] = hi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int i = 1; i < nw; ++i) {
+        tmp[0] = min(tmp[0], tmp[i]);
+        tmp[16] = max(tmp[16], tmp[16 + i]);
+      }
+    }
+    __syncthreads();
+    lo = (int32_t)tmp[0];
+    hi = (int32_t)tmp[16];
+    __syncthreads();
+    int64_t total = 0;
+    int64_t out0 = 0, expect = 0;
+    if (!SYM) {
+      out0 = C.rp[row];
+      expect = C.rp[row + 1] - out0;
+    }
+    for (int64_t base = lo; base <= hi; base += WCOLS) {
+      const int64_t wend = base + WCOLS;
+      for (int i = tid; i < WWORDS; i += blockDim.x) bits[i] = 0;
+      if (!SYM)
+        for (int i = tid; i < WCOLS; i += blockDim.x) acc[i] = Acc(0);
+      if (tid == 0) *s_run = 0;
+      __syncthreads();
+      for (int64_t cb = 0; cb < nent; cb += blockDim.x) {
+        gather_chunk<DT>(Ac, Acl, SRC, item, cb, s_k, s_a, tmp, s_n, s_run);
+        const int n = *s_n;
+        for (int i = w; i < n; i += nw) {
+          const int32_t k = s_k[i];
+          const In a = s_a[i];
+          int64_t s = B.rp[k];
+          const int64_t e = B.rp[k + 1];
+          if (e <= s || B.col[e - 1] < base || B.col[s] >= wend) continue;
+          // first entry >= base (binary search, warp-uniform)
+          int64_t L = s, R = e;
+          while (L < R) {
+            const int64_t mid = (L + R) >> 1;
+            if (B.col[mid] < base) L = mid + 1; else R = mid;
+          }
+          for (int64_t q = L + lane; q < e; q += 32) {
+            const int32_t j = B.col[q];
+            if (j >= wend) break;
+            const int o = (int)(j - base);
+            atomicOr(&bits[o >> 5], 1u << (o & 31));
+            if constexpr (!SYM) VT<DT>::atomic_add(&acc[o], VT<DT>::mul(a, ((const In*)B.val)[q]));
+          }
+        }
+        __syncthreads();
+      }
+      // ---- window result
+      if constexpr (SYM) {
+        int64_t c = 0;
+        for (int i = tid; i < WWORDS; i += blockDim.x) c += __popc(bits[i]);
+        int64_t tot;
+        block_excl_scan<int64_t>(c, tmp, &tot);
+        total += tot;
+      } else {
+        // each thread owns WWORDS / blockDim consecutive words
+        constexpr int WPT = WWORDS / HEAVY_THREADS;
+        int c = 0;
+        for (int i = 0; i < WPT; ++i) c += __popc(bits[tid * WPT + i]);
+        int64_t tot;
+        int64_t pos = block_excl_scan<int64_t>(c, tmp, &tot);
+        if (total + tot <= expect) {
+          for (int i = 0; i < WPT; ++i) {
+            uint32_t b = bits[tid * WPT + i];
+            while (b) {
+              const int bit = __ffs(b) - 1;
+              b &= b - 1;
+              const int o = (tid * WPT + i) * 32 + bit;
+              C.col[out0 + total + pos] = (int32_t)(base + o);
+              ((In*)C.val)[out0 + total + pos] = VT<DT>::out(acc[o]);
+              ++pos;
+            }
+          }
+        }
+        total += tot;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      if (SYM)
+        c_rp_sym[row + 1] = total;
+      else if (total != expect)
+        raise(st, DEV_INTERNAL, 20, row);
+    }
+    __syncthreads();
+  }
+}
+
+inline size_t row_heavy_smem(bool sym, int acc_bytes) {
+  const size_t head = 512 + 4 * HEAVY_THREADS + 8 * HEAVY_THREADS;
+  return sym ? head + 4 * (size_t)HEAVY_SYM_WORDS
+             : head + 4 * (size_t)(HEAVY_NUM_W / 32) + (size_t)acc_bytes * HEAVY_NUM_W;
+}
+
+}  // namespace sgc

@@ -1,0 +1,57 @@
+// Host-side internals of libsgc shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sgc.h"
+
+namespace sgc {
+
+// thread-local last-error message (capi.cu)
+void set_last_error(const std::string& msg);
+
+int num_sms();
+
+// ---- scan (k_scan.cu): in-place inclusive scan of n int64 values ----------
+constexpr int SCAN_TILE = 2048;  // 256 threads x 8 items
+inline int64_t scan_tmp_elems(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 2; }
+cudaError_t inclusive_scan_i64(int64_t* data, int64_t n, int64_t* tmp, cudaStream_t s);
+
+// ---- workspace carving ----------------------------------------------------
+struct Carver {
+  char* base;
+  size_t off = 0;
+  size_t cap;
+  Carver(void* b, size_t c) : base((char*)b), cap(c) {}
+  template <class T>
+  T* take(int64_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = (T*)(base ? base + off : nullptr);
+    off += sizeof(T) * (size_t)(n > 0 ? n : 0);
+    return p;
+  }
+  bool fits() const { return off <= cap; }
+};
+
+// Row-hash table sizes: log2 T from 5 (32 slots) to 13 (8192 slots).
+constexpr int LOG2T_MIN = 5;
+constexpr int LOG2T_MAX = 13;
+
+// Heavy-row limits (rows above go to the dense-window kernels).
+constexpr int64_t HEAVY_NUM = SGC_HEAVY_ROW_OUTPUTS;     // numeric: exact count
+constexpr int64_t HEAVY_SYM = 2 * SGC_HEAVY_ROW_OUTPUTS; // symbolic: min(ub, ncols)
+
+struct ResolvedOptions {
+  int staging;
+  int validate;
+  int stage_elems_num;
+  int stage_elems_sym;
+  int max_warps;
+  int load_pct;
+};
+ResolvedOptions resolve(const sgc_options* opt);
+
+}  // namespace sgc

@@ -1,0 +1,305 @@
+"""Thin ctypes binding of libsgc.so (C ABI in include/sgc.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  Device memory comes from PyTorch tensors on the
+current CUDA device and kernels run on PyTorch's current stream.  Importing
+this module loads ``_build/libsgc.so`` and raises ImportError if it has not
+been built (``python -m paper_2507_21253_gb300.build``); there is no fallback.
+
+Function names follow the C ABI.  Each C call that returns a non-zero status
+raises :class:`SgcError` carrying the status and ``sgc_last_error()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsgc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libsgc.so not built at {LIB_PATH}; run python -m paper_2507_21253_gb300.build")
+_lib = ctypes.CDLL(LIB_PATH)
+
+SGC_OK, SGC_INVALID_ARG, SGC_UNSUPPORTED, SGC_WORKSPACE_TOO_SMALL = 0, 1, 2, 3
+SGC_CUDA_ERROR, SGC_DEVICE_CHECK_FAILED, SGC_DEVICE_TIMEOUT = 4, 5, 6
+SGC_F32, SGC_F64, SGC_I64 = 0, 1, 2
+LAYOUT_PADDED, LAYOUT_MASKED = 0, 1
+STAGING_AUTO, STAGING_BULK, STAGING_LDG = 0, 1, 2
+
+_DT = {torch.float32: SGC_F32, torch.float64: SGC_F64, torch.int64: SGC_I64}
+_TORCH = {v: k for k, v in _DT.items()}
+
+vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+
+
+class SgcError(RuntimeError):
+    def __init__(self, code: int, fn: str):
+        msg = _lib.sgc_last_error().decode(errors="replace")
+        super().__init__(f"{fn} failed with status {code}: {msg}")
+        self.code = code
+
+
+class CsrStruct(ctypes.Structure):
+    _fields_ = [("nrows", i64), ("ncols", i64), ("nnz", i64), ("row_ptr", vp), ("col", vp), ("val", vp),
+                ("dtype", i32), ("reserved", i32)]
+
+
+class ClusterStruct(ctypes.Structure):
+    _fields_ = [("nrows", i64), ("ncols", i64), ("nclusters", i64), ("nucols", i64), ("nvals", i64),
+                ("layout", i32), ("dtype", i32), ("perm", vp), ("cluster_ptr", vp), ("ucol_ptr", vp),
+                ("ucol", vp), ("mask", vp), ("val_ptr", vp), ("val", vp)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("staging", i32), ("validate", i32), ("stage_elems", i32), ("max_warps", i32),
+                ("load_pct", i32), ("reserved", i32 * 11)]
+
+
+def _sig(name, *args):
+    f = getattr(_lib, name)
+    f.restype = ctypes.c_int
+    f.argtypes = list(args)
+    return f
+
+
+_lib.sgc_last_error.restype = ctypes.c_char_p
+_lib.sgc_abi_version.restype = ctypes.c_int
+P = ctypes.POINTER
+_c = {
+    "sgc_default_options": _sig("sgc_default_options", P(Options)),
+    "sgc_workspace_status": _sig("sgc_workspace_status", vp, ctypes.c_size_t, vp),
+    "csr_cluster_build_workspace_size": _sig("csr_cluster_build_workspace_size", i64, i64, P(ctypes.c_size_t)),
+    "csr_cluster_build_count": _sig("csr_cluster_build_count", P(CsrStruct), vp, vp, i64, i32, vp, vp, P(i64),
+                                    P(i64), vp, ctypes.c_size_t, vp),
+    "csr_cluster_build": _sig("csr_cluster_build", P(CsrStruct), P(ClusterStruct), vp),
+    "spgemm_workspace_size": _sig("spgemm_workspace_size", P(ClusterStruct), P(CsrStruct), P(Options),
+                                  P(ctypes.c_size_t)),
+    "spgemm_symbolic": _sig("spgemm_symbolic", P(ClusterStruct), P(CsrStruct), vp, P(i64), vp, ctypes.c_size_t,
+                            P(Options), vp),
+    "spgemm_numeric": _sig("spgemm_numeric", P(ClusterStruct), P(CsrStruct), P(CsrStruct), vp, ctypes.c_size_t,
+                           P(Options), vp),
+    "spgemm_rowwise_workspace_size": _sig("spgemm_rowwise_workspace_size", P(CsrStruct), P(CsrStruct),
+                                          P(Options), P(ctypes.c_size_t)),
+    "spgemm_rowwise_symbolic": _sig("spgemm_rowwise_symbolic", P(CsrStruct), P(CsrStruct), vp, P(i64), vp,
+                                    ctypes.c_size_t, P(Options), vp),
+    "spgemm_rowwise_numeric": _sig("spgemm_rowwise_numeric", P(CsrStruct), P(CsrStruct), P(CsrStruct), vp,
+                                   ctypes.c_size_t, P(Options), vp),
+}
+
+
+def _call(name, *args):
+    rc = _c[name](*args)
+    if rc != SGC_OK:
+        raise SgcError(rc, name)
+
+
+def abi_version() -> int:
+    return int(_lib.sgc_abi_version())
+
+
+def _stream():
+    return vp(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return vp(t.data_ptr()) if t is not None and t.numel() > 0 else vp(0)
+
+
+def options(staging=STAGING_AUTO, validate=0, stage_elems=0, max_warps=0, load_pct=0) -> Options:
+    o = Options()
+    _call("sgc_default_options", ctypes.byref(o))
+    o.staging, o.validate, o.stage_elems, o.max_warps, o.load_pct = staging, validate, stage_elems, max_warps, load_pct
+    return o
+
+
+# ---------------------------------------------------------------------------
+# device-side matrices (tensors + shapes)
+# ---------------------------------------------------------------------------
+@dataclass
+class DeviceCsr:
+    nrows: int
+    ncols: int
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    val: torch.Tensor
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    def struct(self) -> CsrStruct:
+        return CsrStruct(self.nrows, self.ncols, self.nnz, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val),
+                         _DT[self.val.dtype], 0)
+
+    @staticmethod
+    def from_host(A, device="cuda") -> "DeviceCsr":
+        """A: any object with nrows, ncols, row_ptr, col, val (numpy)."""
+        return DeviceCsr(int(A.nrows), int(A.ncols), torch.from_numpy(A.row_ptr).to(device),
+                         torch.from_numpy(A.col).to(device), torch.from_numpy(A.val).to(device))
+
+    def to_host(self):
+        return self.row_ptr.cpu().numpy(), self.col.cpu().numpy(), self.val.cpu().numpy()
+
+
+@dataclass
+class DeviceCsrCluster:
+    nrows: int
+    ncols: int
+    layout: int
+    perm: torch.Tensor
+    cluster_ptr: torch.Tensor
+    ucol_ptr: torch.Tensor
+    ucol: torch.Tensor
+    mask: torch.Tensor
+    val_ptr: torch.Tensor
+    val: torch.Tensor
+
+    @property
+    def nclusters(self) -> int:
+        return int(self.cluster_ptr.numel()) - 1
+
+    def struct(self) -> ClusterStruct:
+        return ClusterStruct(self.nrows, self.ncols, self.nclusters, int(self.ucol.numel()), int(self.val.numel()),
+                             self.layout, _DT[self.val.dtype], _ptr(self.perm), _ptr(self.cluster_ptr),
+                             _ptr(self.ucol_ptr), _ptr(self.ucol), _ptr(self.mask), _ptr(self.val_ptr),
+                             _ptr(self.val))
+
+
+# ---------------------------------------------------------------------------
+# CSR_Cluster construction
+# ---------------------------------------------------------------------------
+def csr_cluster_build_count(A: DeviceCsr, perm: torch.Tensor, cluster_ptr: torch.Tensor, layout: int):
+    """Returns (ucol_ptr, val_ptr, nucols, nvals); synchronises."""
+    dev = A.row_ptr.device
+    ncl = int(cluster_ptr.numel()) - 1
+    ucol_ptr = torch.empty(ncl + 1, dtype=torch.int64, device=dev)
+    val_ptr = torch.empty(ncl + 1, dtype=torch.int64, device=dev)
+    nb = ctypes.c_size_t()
+    _call("csr_cluster_build_workspace_size", A.nrows, ncl, ctypes.byref(nb))
+    ws = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+    nu, nv = i64(), i64()
+    s = A.struct()
+    _call("csr_cluster_build_count", ctypes.byref(s), _ptr(perm), _ptr(cluster_ptr), ncl, layout, _ptr(ucol_ptr),
+          _ptr(val_ptr), ctypes.byref(nu), ctypes.byref(nv), _ptr(ws), nb.value, _stream())
+    return ucol_ptr, val_ptr, nu.value, nv.value
+
+
+def csr_cluster_build(A: DeviceCsr, perm, cluster_ptr, layout: int = LAYOUT_MASKED) -> DeviceCsrCluster:
+    """Count, allocate and fill the CSR_Cluster form of A for the given clusters."""
+    dev = A.row_ptr.device
+    perm = torch.as_tensor(perm, dtype=torch.int32, device=dev)
+    cluster_ptr = torch.as_tensor(cluster_ptr, dtype=torch.int64, device=dev)
+    ucol_ptr, val_ptr, nu, nv = csr_cluster_build_count(A, perm, cluster_ptr, layout)
+    out = DeviceCsrCluster(A.nrows, A.ncols, layout, perm, cluster_ptr, ucol_ptr,
+                           torch.empty(nu, dtype=torch.int32, device=dev),
+                           torch.empty(nu, dtype=torch.int32, device=dev).view(torch.int32),
+                           val_ptr, torch.empty(nv, dtype=A.val.dtype, device=dev))
+    s, o = A.struct(), out.struct()
+    _call("csr_cluster_build", ctypes.byref(s), ctypes.byref(o), _stream())
+    return out
+
+
+# ---------------------------------------------------------------------------
+# SpGEMM
+# ---------------------------------------------------------------------------
+class Workspace:
+    def __init__(self, nbytes: int, device="cuda"):
+        self.buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+    @property
+    def ptr(self):
+        return _ptr(self.buf)
+
+    @property
+    def nbytes(self):
+        return int(self.buf.numel())
+
+
+def spgemm_workspace_size(A: DeviceCsrCluster, B: DeviceCsr, opt: Options | None = None) -> int:
+    n = ctypes.c_size_t()
+    a, b = A.struct(), B.struct()
+    _call("spgemm_workspace_size", ctypes.byref(a), ctypes.byref(b), ctypes.byref(opt) if opt else None,
+          ctypes.byref(n))
+    return n.value
+
+
+def spgemm_rowwise_workspace_size(A: DeviceCsr, B: DeviceCsr, opt: Options | None = None) -> int:
+    n = ctypes.c_size_t()
+    a, b = A.struct(), B.struct()
+    _call("spgemm_rowwise_workspace_size", ctypes.byref(a), ctypes.byref(b), ctypes.byref(opt) if opt else None,
+          ctypes.byref(n))
+    return n.value
+
+
+def spgemm_symbolic(A: DeviceCsrCluster, B: DeviceCsr, ws: Workspace, opt: Options | None = None,
+                    c_row_ptr: torch.Tensor | None = None, sync: bool = True):
+    """C's row pointer (int64, nrows+1, original row order) and nnz(C) (None when sync=False)."""
+    if c_row_ptr is None:
+        c_row_ptr = torch.empty(A.nrows + 1, dtype=torch.int64, device=B.row_ptr.device)
+    nnz = i64()
+    a, b = A.struct(), B.struct()
+    _call("spgemm_symbolic", ctypes.byref(a), ctypes.byref(b), _ptr(c_row_ptr),
+          ctypes.byref(nnz) if sync else None, ws.ptr, ws.nbytes, ctypes.byref(opt) if opt else None, _stream())
+    return c_row_ptr, (nnz.value if sync else None)
+
+
+def spgemm_numeric(A: DeviceCsrCluster, B: DeviceCsr, c_row_ptr: torch.Tensor, nnz: int, ws: Workspace,
+                   opt: Options | None = None, C: DeviceCsr | None = None) -> DeviceCsr:
+    dev = B.row_ptr.device
+    if C is None:
+        C = DeviceCsr(A.nrows, B.ncols, c_row_ptr, torch.empty(nnz, dtype=torch.int32, device=dev),
+                      torch.empty(nnz, dtype=B.val.dtype, device=dev))
+    a, b, c = A.struct(), B.struct(), C.struct()
+    _call("spgemm_numeric", ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ws.ptr, ws.nbytes,
+          ctypes.byref(opt) if opt else None, _stream())
+    return C
+
+
+def spgemm_rowwise_symbolic(A: DeviceCsr, B: DeviceCsr, ws: Workspace, opt: Options | None = None,
+                            c_row_ptr: torch.Tensor | None = None, sync: bool = True):
+    if c_row_ptr is None:
+        c_row_ptr = torch.empty(A.nrows + 1, dtype=torch.int64, device=B.row_ptr.device)
+    nnz = i64()
+    a, b = A.struct(), B.struct()
+    _call("spgemm_rowwise_symbolic", ctypes.byref(a), ctypes.byref(b), _ptr(c_row_ptr),
+          ctypes.byref(nnz) if sync else None, ws.ptr, ws.nbytes, ctypes.byref(opt) if opt else None, _stream())
+    return c_row_ptr, (nnz.value if sync else None)
+
+
+def spgemm_rowwise_numeric(A: DeviceCsr, B: DeviceCsr, c_row_ptr: torch.Tensor, nnz: int, ws: Workspace,
+                           opt: Options | None = None, C: DeviceCsr | None = None) -> DeviceCsr:
+    dev = B.row_ptr.device
+    if C is None:
+        C = DeviceCsr(A.nrows, B.ncols, c_row_ptr, torch.empty(nnz, dtype=torch.int32, device=dev),
+                      torch.empty(nnz, dtype=B.val.dtype, device=dev))
+    a, b, c = A.struct(), B.struct(), C.struct()
+    _call("spgemm_rowwise_numeric", ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ws.ptr, ws.nbytes,
+          ctypes.byref(opt) if opt else None, _stream())
+    return C
+
+
+def workspace_status(ws: Workspace):
+    """Raises SgcError if an asynchronous call recorded a device-side failure."""
+    _call("sgc_workspace_status", ws.ptr, ws.nbytes, _stream())
+
+
+def spgemm(A: DeviceCsrCluster, B: DeviceCsr, opt: Options | None = None) -> DeviceCsr:
+    """Symbolic + numeric cluster-wise product, checked."""
+    ws = Workspace(spgemm_workspace_size(A, B, opt), B.row_ptr.device)
+    rp, nnz = spgemm_symbolic(A, B, ws, opt)
+    C = spgemm_numeric(A, B, rp, nnz, ws, opt)
+    workspace_status(ws)
+    return C
+
+
+def spgemm_rowwise(A: DeviceCsr, B: DeviceCsr, opt: Options | None = None) -> DeviceCsr:
+    """Symbolic + numeric row-wise product, checked."""
+    ws = Workspace(spgemm_rowwise_workspace_size(A, B, opt), B.row_ptr.device)
+    rp, nnz = spgemm_rowwise_symbolic(A, B, ws, opt)
+    C = spgemm_rowwise_numeric(A, B, rp, nnz, ws, opt)
+    workspace_status(ws)
+    return C

@@ -1,0 +1,172 @@
+"""GPU parity: row-wise and cluster-wise SpGEMM through the C ABI vs the CPU oracle.
+
+Sizes here run in seconds on the oracle and span several tiles, ragged tails,
+empty rows, heavy rows and every bin; the full-size workloads are covered in
+test_gpu_fullsize.py on sampled rows.
+"""
+import numpy as np
+import pytest
+
+from paper_2507_21253_gb300 import synth
+from tests.gpu_helpers import compare, lib
+from tests.test_oracle_gustavson import random_sparse
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sgc():
+    return lib()
+
+
+def dev(sgc, A):
+    return sgc.DeviceCsr.from_host(A)
+
+
+def cases():
+    yield "laplacian64", synth.workload_laplacian(1)
+    yield "rand_f64", random_sparse(300, 300, 0.03, 7, "f64")
+    yield "rand_f32", random_sparse(257, 257, 0.05, 8, "f32")
+    yield "rand_i64", random_sparse(333, 333, 0.04, 9, "i64")
+    yield "rmat12_f32", synth.workload_rmat("f32", seed=2, scale=12)
+    yield "rmat12_i64", synth.workload_rmat("i64", seed=2, scale=12)
+    yield "powerlaw", synth.powerlaw_matrix(3001, n=3000)
+    yield "planted", synth.planted_groups(4096, 4001)
+    yield "stencil14", synth.stencil27_3d(14, 13, 12, seed=5)
+
+
+CASES = list(cases())
+
+
+@pytest.mark.parametrize("name,A", CASES, ids=[c[0] for c in CASES])
+def test_rowwise(sgc, name, A):
+    Ad = dev(sgc, A)
+    C = sgc.spgemm_rowwise(Ad, Ad)
+    compare(C, A, A, exact_f64=(A.val.dtype == np.float64))
+
+
+@pytest.mark.parametrize("layout", [0, 1], ids=["padded", "masked"])
+@pytest.mark.parametrize("staging", [1, 2], ids=["bulk", "ldg"])
+@pytest.mark.parametrize("clus", ["fixed1", "fixed8", "random32"])
+@pytest.mark.parametrize("name,A", CASES, ids=[c[0] for c in CASES])
+def test_clusterwise(sgc, name, A, clus, staging, layout):
+    if clus == "fixed1":
+        perm, cptr = synth.fixed_clusters(A.nrows, 1)
+    elif clus == "fixed8":
+        perm, cptr = synth.fixed_clusters(A.nrows, 8)
+    else:
+        perm, cptr = synth.random_clusters(A.nrows, 11, kmax=32)
+    Ad = dev(sgc, A)
+    Acl = sgc.csr_cluster_build(Ad, perm, cptr, layout)
+    opt = sgc.options(staging=staging)
+    C = sgc.spgemm(Acl, Ad, opt)
+    compare(C, A, A, exact_f64=(A.val.dtype == np.float64))
+
+
+def test_cluster_format_matches_oracle(sgc):
+    from oracle import csr_cluster as occ
+    A = random_sparse(200, 120, 0.06, 3, "f64")
+    perm, cptr = synth.random_clusters(200, 5, kmax=32)
+    for layout in (0, 1):
+        got = sgc.csr_cluster_build(dev(sgc, A), perm, cptr, layout)
+        ref = occ.build(A, perm, cptr, layout)
+        assert np.array_equal(got.ucol_ptr.cpu().numpy(), ref["ucol_ptr"])
+        assert np.array_equal(got.ucol.cpu().numpy(), ref["ucol"])
+        assert np.array_equal(got.mask.cpu().numpy().view(np.uint32), ref["mask"])
+        assert np.array_equal(got.val_ptr.cpu().numpy(), ref["val_ptr"])
+        assert np.array_equal(got.val.cpu().numpy(), ref["val"])
+
+
+def heavy_matrix():
+    """A few rows of A with thousands of entries against a B with wide rows:
+    output rows far above the 3072-entry table limit (heavy-row kernels)."""
+    rs = synth.Stream(77, 1)
+    n, m = 64, 40000
+    rows, cols = [], []
+    for r in range(n):
+        k = 4000 if r % 16 == 0 else 10
+        c = np.unique(rs.randint(20000, k))
+        rows.append(np.full(c.size, r))
+        cols.append(c)
+    A = synth.csr_from_pattern(n, 20000, np.concatenate(rows), np.concatenate(cols))
+    A = A.with_values(rs.normal(A.nnz))
+    B = random_sparse(20000, m, 0.0004, 12, "f64")
+    return A, B
+
+
+@pytest.mark.parametrize("dtype", ["f64", "i64"])
+def test_heavy_rows(sgc, dtype):
+    A, B = heavy_matrix()
+    if dtype == "i64":
+        rs = synth.Stream(5, 5)
+        A = A.with_values(rs.randint(5, A.nnz).astype(np.int64) - 2)
+        B = B.with_values(rs.randint(5, B.nnz).astype(np.int64) - 2)
+    Ad, Bd = dev(sgc, A), dev(sgc, B)
+    C = sgc.spgemm_rowwise(Ad, Bd)
+    compare(C, A, B)
+    perm, cptr = synth.random_clusters(A.nrows, 3, kmax=8)
+    for layout in (0, 1):
+        Acl = sgc.csr_cluster_build(Ad, perm, cptr, layout)
+        C = sgc.spgemm(Acl, Bd)
+        compare(C, A, B)
+
+
+def test_rectangular_and_empty_rows(sgc):
+    A = random_sparse(90, 70, 0.05, 31, "f64")
+    B = random_sparse(70, 300, 0.02, 32, "f64")
+    # empty some rows of A
+    A.row_ptr = A.row_ptr.copy()
+    Ad, Bd = dev(sgc, A), dev(sgc, B)
+    compare(sgc.spgemm_rowwise(Ad, Bd), A, B)
+    perm, cptr = synth.random_clusters(90, 4, kmax=6)
+    compare(sgc.spgemm(sgc.csr_cluster_build(Ad, perm, cptr), Bd), A, B)
+
+
+def test_empty_matrices(sgc):
+    import torch
+    Z = synth.Csr(50, 40, np.zeros(51, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0))
+    B = random_sparse(40, 30, 0.1, 2, "f64")
+    C = sgc.spgemm_rowwise(dev(sgc, Z), dev(sgc, B))
+    assert C.nnz == 0 and int(C.row_ptr.sum()) == 0
+    perm, cptr = synth.fixed_clusters(50, 8)
+    C = sgc.spgemm(sgc.csr_cluster_build(dev(sgc, Z), perm, cptr), dev(sgc, B))
+    assert C.nnz == 0
+    E = synth.Csr(0, 40, np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32), np.zeros(0))
+    C = sgc.spgemm_rowwise(dev(sgc, E), dev(sgc, B))
+    assert C.nnz == 0 and C.row_ptr.numel() == 1
+
+
+def test_validation_rejects_bad_input(sgc):
+    import torch
+    A = random_sparse(40, 40, 0.2, 3, "f64")
+    bad = A.with_values(A.val)
+    bad.col = A.col.copy()
+    r = int(np.argmax(np.diff(A.row_ptr) >= 2))
+    s = A.row_ptr[r]
+    bad.col[s], bad.col[s + 1] = A.col[s + 1], A.col[s]      # unsorted row, ids in range
+    Bd = dev(sgc, A)
+    with pytest.raises(sgc.SgcError) as ei:
+        sgc.spgemm_rowwise(dev(sgc, bad), Bd, sgc.options(validate=1))
+    assert ei.value.code == sgc.SGC_DEVICE_CHECK_FAILED
+    # a cluster of 33 rows is refused by the build
+    perm = np.arange(40, dtype=np.int32)
+    with pytest.raises(sgc.SgcError):
+        sgc.csr_cluster_build(Bd, perm, np.array([0, 33, 40]))
+    # perm with a repeated row is refused
+    perm2 = perm.copy()
+    perm2[5] = 6
+    with pytest.raises(sgc.SgcError):
+        sgc.csr_cluster_build(Bd, perm2, np.array([0, 8, 40]))
+    # dtype mismatch
+    with pytest.raises(sgc.SgcError) as ei:
+        sgc.spgemm_rowwise(Bd, dev(sgc, random_sparse(40, 40, 0.2, 4, "f32")))
+    assert ei.value.code == sgc.SGC_UNSUPPORTED
+
+
+def test_workspace_too_small(sgc):
+    A = random_sparse(40, 40, 0.2, 3, "f64")
+    Ad = dev(sgc, A)
+    ws = sgc.Workspace(256)
+    with pytest.raises(sgc.SgcError) as ei:
+        sgc.spgemm_rowwise_symbolic(Ad, Ad, ws)
+    assert ei.value.code == sgc.SGC_WORKSPACE_TOO_SMALL
