@@ -203,6 +203,40 @@ int spgemm_rowwise_symbolic(const sgc_csr* A, const sgc_csr* B, int64_t* c_row_p
 int spgemm_rowwise_numeric(const sgc_csr* A, const sgc_csr* B, sgc_csr* C, void* ws,
                            size_t ws_bytes, const sgc_options* opt, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Hierarchical clustering (Sec. 3.3, Algorithm 3, "Construct Hierarchical
+ * Cluster"): candidate row pairs from SpGEMM_TopK(A, A^T) -- the structural
+ * product A*A^T with all values 1 gives the overlap c_ij of rows i and j, the
+ * Jaccard score is c_ij / (nnz_i + nnz_j - c_ij) -- then a max-heap of pairs
+ * merged by union-find into clusters of at most max_cluster rows.
+ *
+ * hcluster_workspace_size: device workspace bytes for both calls below.
+ *
+ * hcluster_candidates: for every row i of A (any shape; only the pattern is
+ * read), its `topk` best partners j != i with score > jacc_th, best first
+ * (score compared exactly as integers; ties: smaller j first; the threshold
+ * test is c > jacc_th * u in FP64): cand_j[i*topk + r] (-1 past the last),
+ * cand_inter / cand_union the overlap and union sizes.  Device int32 arrays
+ * of nrows*topk, caller-owned.  1 <= topk <= 31.  Asynchronous.
+ *
+ * hcluster_reorder: the clusters of Algorithm 3 with topk = max_cluster - 1
+ * (1 <= max_cluster <= 32).  Readings where the paper is open: the merge loop
+ * runs until the heap is empty; two roots merge only if the result has at
+ * most max_cluster rows, the smaller row id becoming the root; when a popped
+ * row is not a root, the pair of roots is scored and pushed if above the
+ * threshold and never seen before; the heap orders by score, then smaller i,
+ * then smaller j.  Output: perm (device int32, nrows: position -> row) and
+ * cluster_ptr (device int64, capacity nrows+1): clusters ordered by their
+ * smallest row, rows ascending within a cluster; *nclusters_host receives the
+ * count.  The candidate search runs on the GPU; the heap and union-find run on
+ * the host (A's pattern is copied to the host).  Synchronises.
+ * ------------------------------------------------------------------------- */
+int hcluster_workspace_size(const sgc_csr* A, int32_t max_cluster, size_t* bytes);
+int hcluster_candidates(const sgc_csr* A, float jacc_th, int32_t topk, int32_t* cand_j, int32_t* cand_inter,
+                        int32_t* cand_union, void* ws, size_t ws_bytes, void* stream);
+int hcluster_reorder(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm, int64_t* cluster_ptr,
+                     int64_t* nclusters_host, void* ws, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,14 +55,14 @@ def jaccard_lt(inter: int, union: int, th: float) -> bool:
     return float(inter) < float(th) * float(union)
 
 
-def candidate_pairs(A, th: float, topk: int) -> dict:
-    """{(i, j): (inter, union)} with i < j (Algorithm 3, candidate generation)."""
+def candidate_lists(A, th: float, topk: int) -> list:
+    """Per row i, its topk best partners [(j, inter, union), ...] in rank order."""
     rows = _rows(A)
     cols_to_rows: dict = {}
     for i, r in enumerate(rows):
         for c in r:
             cols_to_rows.setdefault(c, []).append(i)
-    out = {}
+    out = []
     for i, r in enumerate(rows):
         counts: dict = {}
         for c in r:                      # row i of A times A^T with unit values
@@ -76,7 +76,15 @@ def candidate_pairs(A, th: float, topk: int) -> dict:
             if jaccard_gt(inter, union, th):
                 scored.append((-Fraction(inter, union), j, inter, union))
         scored.sort()
-        for _, j, inter, union in scored[:topk]:
+        out.append([(j, inter, union) for _, j, inter, union in scored[:topk]])
+    return out
+
+
+def candidate_pairs(A, th: float, topk: int) -> dict:
+    """{(i, j): (inter, union)} with i < j (Algorithm 3, candidate generation)."""
+    out = {}
+    for i, lst in enumerate(candidate_lists(A, th, topk)):
+        for j, inter, union in lst:
             out[(min(i, j), max(i, j))] = (inter, union)
     return out
 

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "sgc_device.cuh"
 #include "sgc_kernels.h"
@@ -396,6 +397,127 @@ int spgemm_rowwise_numeric(const sgc_csr* A, const sgc_csr* B, sgc_csr* C, void*
     case SGC_F64: SGC_CUDA((run_rows_phase<false, SGC_F64>(av, bv, cv, C->row_ptr, w.bins, w.status, L))); break;
     default: SGC_CUDA((run_rows_phase<false, SGC_I64>(av, bv, cv, C->row_ptr, w.bins, w.status, L))); break;
   }
+  return SGC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Hierarchical clustering
+// ---------------------------------------------------------------------------
+namespace {
+struct HcWs {
+  DevStatus* status;
+  int64_t* trp;
+  int32_t* tcol;
+  int32_t* cursor;
+  int64_t* dummy_rp;
+  BinOut bins;
+  int64_t* scan_tmp;
+  int32_t *cj, *cc, *cu;
+  size_t bytes;
+};
+HcWs carve_hc(void* base, size_t cap, const sgc_csr* A, int topk) {
+  Carver cv(base, cap);
+  HcWs w{};
+  const int64_t n = A->nrows, m = A->ncols;
+  w.status = cv.take<DevStatus>(4);
+  w.trp = cv.take<int64_t>(m + 1);
+  w.tcol = cv.take<int32_t>(A->nnz > 0 ? A->nnz : 1);
+  w.cursor = cv.take<int32_t>(m > 0 ? m : 1);
+  w.dummy_rp = cv.take<int64_t>(n + 1);
+  w.bins.count = cv.take<int32_t>(NBIN_ALL);
+  w.bins.dense_items = nullptr;
+  w.bins.row_items = cv.take<int64_t>((int64_t)NRB * n);
+  w.bins.heavy_items = cv.take<int64_t>(n);
+  w.bins.uc_rec = w.bins.nout_rec = nullptr;
+  w.bins.ncl = 0;
+  w.bins.nrows = n;
+  w.scan_tmp = cv.take<int64_t>(scan_tmp_elems(n > m ? n : m));
+  w.cj = cv.take<int32_t>(n * (topk > 0 ? topk : 1));
+  w.cc = cv.take<int32_t>(n * (topk > 0 ? topk : 1));
+  w.cu = cv.take<int32_t>(n * (topk > 0 ? topk : 1));
+  w.bytes = cv.off + 256;
+  return w;
+}
+}  // namespace
+
+int hcluster_workspace_size(const sgc_csr* A, int32_t max_cluster, size_t* bytes) {
+  int rc = check_csr(A, "A", false);
+  if (rc) return rc;
+  if (!bytes) SGC_FAIL(SGC_INVALID_ARG, "bytes is NULL");
+  (void)max_cluster;
+  *bytes = carve_hc(nullptr, 0, A, 31).bytes;
+  return SGC_OK;
+}
+
+int hcluster_candidates(const sgc_csr* A, float jacc_th, int32_t topk, int32_t* cand_j, int32_t* cand_inter,
+                        int32_t* cand_union, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_csr(A, "A", false);
+  if (rc) return rc;
+  if (topk < 1 || topk > 31) SGC_FAIL(SGC_INVALID_ARG, "topk must be in 1..31");
+  if (A->nrows > 0 && (!cand_j || !cand_inter || !cand_union)) SGC_FAIL(SGC_INVALID_ARG, "NULL output");
+  HcWs w = carve_hc(ws, ws_bytes, A, 31);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  SGC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+  if (A->nrows == 0) return SGC_OK;
+  SGC_CUDA(hc_candidates_run(A->row_ptr, A->col, A->nrows, A->ncols, A->nnz, (double)jacc_th, topk, w.trp, w.tcol,
+                             w.cursor, w.dummy_rp, w.bins, w.scan_tmp, cand_j, cand_inter, cand_union, w.status,
+                             num_sms(), s));
+  return SGC_OK;
+}
+
+int hcluster_reorder(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm, int64_t* cluster_ptr,
+                     int64_t* nclusters_host, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_csr(A, "A", false);
+  if (rc) return rc;
+  if (max_cluster < 1 || max_cluster > 32) SGC_FAIL(SGC_INVALID_ARG, "max_cluster must be in 1..32");
+  if (!nclusters_host || (A->nrows > 0 && (!perm || !cluster_ptr))) SGC_FAIL(SGC_INVALID_ARG, "NULL output");
+  HcWs w = carve_hc(ws, ws_bytes, A, 31);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->nrows;
+  const int topk = max_cluster - 1;
+  SGC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+  std::vector<int64_t> rp((size_t)n + 1);
+  std::vector<int32_t> col((size_t)(A->nnz > 0 ? A->nnz : 1));
+  std::vector<int32_t> cj, cc, cu;
+  if (topk > 0 && n > 0) {
+    SGC_CUDA(hc_candidates_run(A->row_ptr, A->col, n, A->ncols, A->nnz, (double)jacc_th, topk, w.trp, w.tcol,
+                               w.cursor, w.dummy_rp, w.bins, w.scan_tmp, w.cj, w.cc, w.cu, w.status, num_sms(), s));
+    cj.resize((size_t)(n * topk));
+    cc.resize(cj.size());
+    cu.resize(cj.size());
+    SGC_CUDA(cudaMemcpyAsync(cj.data(), w.cj, sizeof(int32_t) * cj.size(), cudaMemcpyDeviceToHost, s));
+    SGC_CUDA(cudaMemcpyAsync(cc.data(), w.cc, sizeof(int32_t) * cj.size(), cudaMemcpyDeviceToHost, s));
+    SGC_CUDA(cudaMemcpyAsync(cu.data(), w.cu, sizeof(int32_t) * cj.size(), cudaMemcpyDeviceToHost, s));
+  }
+  if (n > 0) {
+    SGC_CUDA(cudaMemcpyAsync(rp.data(), A->row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+    if (A->nnz > 0)
+      SGC_CUDA(cudaMemcpyAsync(col.data(), A->col, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost, s));
+  }
+  rc = sync_status(w.status, s);
+  if (rc) return rc;
+  std::vector<int32_t> hperm((size_t)(n > 0 ? n : 1));
+  std::vector<int64_t> hcp((size_t)n + 1);
+  int64_t ncl = 0;
+  if (topk > 0) {
+    ncl = hc_merge_host(n, rp.data(), col.data(), cj.data(), cc.data(), cu.data(), topk, (double)jacc_th,
+                        max_cluster, hperm.data(), hcp.data());
+  } else {
+    for (int64_t r = 0; r < n; ++r) {
+      hperm[(size_t)r] = (int32_t)r;
+      hcp[(size_t)r + 1] = r + 1;
+    }
+    hcp[0] = 0;
+    ncl = n;
+  }
+  if (n > 0) {
+    SGC_CUDA(cudaMemcpyAsync(perm, hperm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    SGC_CUDA(cudaMemcpyAsync(cluster_ptr, hcp.data(), sizeof(int64_t) * (ncl + 1), cudaMemcpyHostToDevice, s));
+    SGC_CUDA(cudaStreamSynchronize(s));
+  }
+  *nclusters_host = ncl;
   return SGC_OK;
 }
 

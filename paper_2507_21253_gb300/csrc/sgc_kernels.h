@@ -86,4 +86,12 @@ cudaError_t validate_csr_run(const int64_t* rp, const int32_t* col, int64_t nrow
 cudaError_t validate_cluster_run(const AClusterView& A, int64_t ncols, void* status,
                                  cudaStream_t s);
 
+// k_hc.cu / hc_merge.cpp
+cudaError_t hc_candidates_run(const int64_t* arp, const int32_t* acol, int64_t nrows, int64_t ncols, int64_t nnz,
+                              double th, int topk, int64_t* trp, int32_t* tcol, int32_t* cursor, int64_t* dummy_rp,
+                              const BinOut& bins, int64_t* scan_tmp, int32_t* cj, int32_t* cc, int32_t* cu,
+                              void* status, int sms, cudaStream_t s);
+int64_t hc_merge_host(int64_t n, const int64_t* rp, const int32_t* col, const int32_t* cj, const int32_t* cc,
+                      const int32_t* cu, int topk, double th, int max_cluster, int32_t* perm, int64_t* cluster_ptr);
+
 }  // namespace sgc

@@ -86,6 +86,11 @@ _c = {
                                           P(Options), P(ctypes.c_size_t)),
     "spgemm_rowwise_symbolic": _sig("spgemm_rowwise_symbolic", P(CsrStruct), P(CsrStruct), vp, P(i64), vp,
                                     ctypes.c_size_t, P(Options), vp),
+    "hcluster_workspace_size": _sig("hcluster_workspace_size", P(CsrStruct), i32, P(ctypes.c_size_t)),
+    "hcluster_candidates": _sig("hcluster_candidates", P(CsrStruct), ctypes.c_float, i32, vp, vp, vp, vp,
+                                ctypes.c_size_t, vp),
+    "hcluster_reorder": _sig("hcluster_reorder", P(CsrStruct), ctypes.c_float, i32, vp, vp, P(i64), vp,
+                             ctypes.c_size_t, vp),
     "spgemm_rowwise_numeric": _sig("spgemm_rowwise_numeric", P(CsrStruct), P(CsrStruct), P(CsrStruct), vp,
                                    ctypes.c_size_t, P(Options), vp),
 }
@@ -303,3 +308,44 @@ def spgemm_rowwise(A: DeviceCsr, B: DeviceCsr, opt: Options | None = None) -> De
     C = spgemm_rowwise_numeric(A, B, rp, nnz, ws, opt)
     workspace_status(ws)
     return C
+
+
+# ---------------------------------------------------------------------------
+# hierarchical clustering
+# ---------------------------------------------------------------------------
+JACC_TH = 0.3      # jacc_th of the paper's experiments (Sec. 3.2)
+MAX_CLUSTER = 8    # max_cluster_th of the paper's experiments (Sec. 3.2)
+
+
+def _hc_ws(A: DeviceCsr, max_cluster: int) -> Workspace:
+    n = ctypes.c_size_t()
+    a = A.struct()
+    _call("hcluster_workspace_size", ctypes.byref(a), max_cluster, ctypes.byref(n))
+    return Workspace(n.value, A.row_ptr.device)
+
+
+def hcluster_candidates(A: DeviceCsr, jacc_th: float = JACC_TH, topk: int = MAX_CLUSTER - 1):
+    """(j, inter, union): int32 device tensors of shape (nrows, topk); j = -1 past the last."""
+    dev = A.row_ptr.device
+    ws = _hc_ws(A, 32)
+    j = torch.empty((A.nrows, topk), dtype=torch.int32, device=dev)
+    c = torch.empty_like(j)
+    u = torch.empty_like(j)
+    a = A.struct()
+    _call("hcluster_candidates", ctypes.byref(a), float(jacc_th), topk, _ptr(j), _ptr(c), _ptr(u), ws.ptr,
+          ws.nbytes, _stream())
+    workspace_status(ws)
+    return j, c, u
+
+
+def hcluster_reorder(A: DeviceCsr, jacc_th: float = JACC_TH, max_cluster: int = MAX_CLUSTER):
+    """Algorithm 3 clusters: (perm int32 [nrows], cluster_ptr int64 [nclusters+1]) on the device."""
+    dev = A.row_ptr.device
+    ws = _hc_ws(A, max_cluster)
+    perm = torch.empty(max(A.nrows, 1), dtype=torch.int32, device=dev)
+    cptr = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
+    ncl = i64()
+    a = A.struct()
+    _call("hcluster_reorder", ctypes.byref(a), float(jacc_th), max_cluster, _ptr(perm), _ptr(cptr),
+          ctypes.byref(ncl), ws.ptr, ws.nbytes, _stream())
+    return perm[:A.nrows], cptr[:ncl.value + 1]

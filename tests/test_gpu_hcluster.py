@@ -1,0 +1,94 @@
+"""GPU hierarchical clustering (Algorithm 3) vs the oracle's reading of it.
+
+Candidate lists (SpGEMM_TopK) must match per row exactly, in rank order,
+including overlap and union sizes; the merged clusters (perm, cluster_ptr)
+must be identical to the oracle's.
+"""
+import numpy as np
+import pytest
+
+from oracle import hcluster as oh
+from paper_2507_21253_gb300 import synth
+from tests.gpu_helpers import compare, lib
+from tests.test_oracle_gustavson import random_sparse
+
+pytestmark = pytest.mark.gpu
+TH = float(np.float32(0.3))
+
+
+@pytest.fixture(scope="module")
+def sgc():
+    return lib()
+
+
+def hub_matrix():
+    """8000 rows; hub column m (m < 10) is in rows 700m..700m+699 and in rows 0..9;
+    rows 0..9 then have A*A^T flop bounds above the hash limit (heavy rows)."""
+    rs = synth.Stream(41, 1)
+    n, m = 8000, 4000
+    rows, cols = [], []
+    for r in range(n):
+        extra = rs.randint(m - 10, 2) + 10
+        for c in extra:
+            rows.append(r)
+            cols.append(int(c))
+        if r < 7000:
+            rows.append(r)
+            cols.append(r // 700)
+        if r < 10:
+            for h in range(10):
+                rows.append(r)
+                cols.append(h)
+    A = synth.csr_from_pattern(n, m, np.array(rows), np.array(cols))
+    return A.with_values(np.ones(A.nnz))
+
+
+def hc_cases():
+    yield "laplacian64", synth.workload_laplacian(1)
+    yield "rand", random_sparse(300, 200, 0.03, 5, "f64")
+    yield "stencil10", synth.stencil27_3d(10, 10, 10, seed=5)
+    yield "planted", synth.planted_groups(2048, 4002)
+    yield "rmat11", synth.workload_rmat("f32", seed=3, scale=11)
+
+
+CASES = list(hc_cases())
+
+
+@pytest.mark.parametrize("topk", [1, 7, 31])
+@pytest.mark.parametrize("name,A", CASES + [("hubs", hub_matrix())], ids=[c[0] for c in CASES] + ["hubs"])
+def test_candidates(sgc, name, A, topk):
+    if name == "hubs" and topk == 31:
+        pytest.skip("oracle time")
+    j, c, u = sgc.hcluster_candidates(sgc.DeviceCsr.from_host(A), TH, topk)
+    j, c, u = j.cpu().numpy(), c.cpu().numpy(), u.cpu().numpy()
+    ref = oh.candidate_lists(A, TH, topk)
+    for i in range(A.nrows):
+        got = [(int(j[i, r]), int(c[i, r]), int(u[i, r])) for r in range(topk) if j[i, r] >= 0]
+        assert got == ref[i], f"row {i}: {got} vs {ref[i]}"
+
+
+@pytest.mark.parametrize("mc", [2, 8, 32])
+@pytest.mark.parametrize("name,A", CASES, ids=[c[0] for c in CASES])
+def test_reorder_matches_oracle(sgc, name, A, mc):
+    perm, cptr = sgc.hcluster_reorder(sgc.DeviceCsr.from_host(A), TH, mc)
+    rperm, rcptr = oh.hierarchical(A, TH, mc)
+    assert np.array_equal(cptr.cpu().numpy(), rcptr)
+    assert np.array_equal(perm.cpu().numpy(), rperm)
+
+
+def test_hc_then_spgemm(sgc):
+    A = synth.workload_laplacian(1)
+    Ad = sgc.DeviceCsr.from_host(A)
+    perm, cptr = sgc.hcluster_reorder(Ad)
+    sizes = np.diff(cptr.cpu().numpy())
+    assert sizes.max() <= 8 and sizes.sum() == A.nrows
+    for layout in (0, 1):
+        C = sgc.spgemm(sgc.csr_cluster_build(Ad, perm, cptr, layout), Ad)
+        compare(C, A, A, exact_f64=True)
+
+
+def test_max_cluster_one(sgc):
+    A = synth.workload_laplacian(1, nx=16)
+    perm, cptr = sgc.hcluster_reorder(sgc.DeviceCsr.from_host(A), TH, 1)
+    assert np.array_equal(perm.cpu().numpy(), np.arange(256))
+    assert np.array_equal(cptr.cpu().numpy(), np.arange(257))
