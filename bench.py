@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark of cluster-wise SpGEMM (CSR_Cluster, hierarchical clustering) on GB300.
+
+One step = the whole per-product hot path on one input that is already
+resident in HBM: the symbolic phase (binning, cluster kernels, scan) and the
+numeric phase of C = A*A with A in CSR_Cluster form.  Preprocessing
+(hierarchical clustering + CSR_Cluster build) is timed separately and reported
+in units of one step.  The plain row-wise method runs on the same GPU in the
+same process and is reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  With N > 1 (torchrun, one rank per GPU) every
+rank computes the same product on its own GPU (replicas; the method has no
+exchange step at this size), and the value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2507_21253_gb300 import synth  # noqa: E402
+
+METRIC = "SpGEMM GFLOP/s & HBM GB/s, clustered+learned vs plain row-wise, same GB300"
+
+WORKLOADS = {
+    "stencil27_160": ("C = A*A, A = 27-point stencil on a 160^3 grid (n = 4,096,000, nnz = 109,215,352), "
+                      "FP64 N(0,1) values, seeded random symmetric permutation; hierarchical clustering "
+                      "(jacc_th 0.3, max 8) + CSR_Cluster (masked layout)",
+                      lambda: synth.workload_stencil(5, nx=160)),
+    "stencil27_80": ("C = A*A, A = 27-point stencil on an 80^3 grid, FP64 N(0,1), seeded symmetric permutation; "
+                     "hierarchical clustering + CSR_Cluster",
+                     lambda: synth.workload_stencil(5, nx=80)),
+    "laplacian64": ("C = A*A, A = 2-D 5-point Laplacian 64x64 (FP64 4/-1), seeded symmetric permutation; "
+                    "hierarchical clustering + CSR_Cluster", lambda: synth.workload_laplacian(1)),
+    "rmat16_f32": ("C = A*A, A = R-MAT scale 16, edge factor 16, (0.57,0.19,0.19,0.05), duplicates merged, "
+                   "FP32 U(0,1); hierarchical clustering + CSR_Cluster", lambda: synth.workload_rmat("f32", 2)),
+    "rmat16_i64": ("C = A*A, A = R-MAT scale 16 as above, int64 U{1..3}; hierarchical clustering + CSR_Cluster",
+                   lambda: synth.workload_rmat("i64", 2)),
+    "planted1m": ("C = A*A, A = planted groups of 8 rows (n = 1,000,000, 11 of 16 shared columns + 5 random), "
+                  "FP64, seeded symmetric permutation; hierarchical clustering + CSR_Cluster",
+                  lambda: synth.workload_planted(4000)),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="stencil27_160", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def flops_of(A, B) -> int:
+    return int(np.sum(np.diff(B.row_ptr)[A.col]))
+
+
+def csr_bytes(M) -> int:
+    return 8 * (M.nrows + 1) + M.nnz * (4 + M.val.itemsize)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample of rows)
+# ---------------------------------------------------------------------------
+def row_flops(A) -> np.ndarray:
+    """Multiply-adds of each row of A*A (sum over a_ik of nnz(A_k))."""
+    per = np.diff(A.row_ptr)[A.col].astype(np.int64)
+    cs = np.concatenate([[0], np.cumsum(per)])
+    return cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]
+
+
+def oracle_sample_rate(A, target_s: float, seed: int = 9, rf=None):
+    """GFLOP/s of the CPU oracle (all host cores, rows over OpenMP threads) on a
+    seeded random row sample sized to take about target_s seconds."""
+    from oracle import gustavson as og
+    og.build()
+    threads = os.cpu_count() or 1
+    rf = row_flops(A) if rf is None else rf
+    probe = np.sort(synth.Stream(seed, 1).randint(A.nrows, 512)).astype(np.int64)
+    t = time.perf_counter()
+    og.spgemm(A, A, rows=probe, want_mag=False, nthreads=threads)
+    dt = max(time.perf_counter() - t, 1e-4)
+    want = max(512, min(A.nrows, int(512 * target_s / dt)))
+    rows = np.sort(synth.Stream(seed, 2).randint(A.nrows, want)).astype(np.int64)
+    t = time.perf_counter()
+    og.spgemm(A, A, rows=rows, want_mag=False, nthreads=threads)
+    dt = time.perf_counter() - t
+    return 2.0 * float(rf[rows].sum()) / dt / 1e9, threads, int(rows.size), dt
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_from_profiles(kernel_key: str, workload: str):
+    """Per-launch DRAM bytes recorded by an ncu capture summarised under profiles/."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(workload, {}).get(kernel_key)
+    return e
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    desc, make = WORKLOADS[args.workload]
+    A = make()
+    flops = flops_of(A, A)
+    steps = []
+    per_step_s = 8.0
+    rf = row_flops(A)
+    cores = os.cpu_count() or 1
+    sample_rows = 0
+    for s in range(args.warmup + args.steps):
+        gf, cores, sample_rows, dt = oracle_sample_rate(A, per_step_s if s >= args.warmup else 1.0, seed=100 + s,
+                                                        rf=rf)
+        if s >= args.warmup:
+            steps.append(gf)
+    value = float(np.mean(steps))
+    ms_per_step = 2.0 * flops / (value * 1e9) * 1e3
+    out = {"metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": desc, "flops": flops},
+           "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{sample_rows} random rows of C per step (serial std::map Gustavson per row, "
+                                      f"rows spread over {cores} OpenMP threads); rate scaled to the whole product"},
+           "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+    import torch.distributed as dist
+    from paper_2507_21253_gb300 import build as sgc_build
+    sgc_build.build()
+    from paper_2507_21253_gb300 import sgc
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    desc, make = WORKLOADS[args.workload]
+    A = make()
+    flops = flops_of(A, A)
+    Ad = sgc.DeviceCsr.from_host(A, dev)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- preprocessing: hierarchical clustering + CSR_Cluster build ----------
+    t0 = time.perf_counter()
+    perm, cptr = sgc.hcluster_reorder(Ad, sgc.JACC_TH, sgc.MAX_CLUSTER)
+    torch.cuda.synchronize()
+    t_hc = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Acl = sgc.csr_cluster_build(Ad, perm, cptr, sgc.LAYOUT_MASKED)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+
+    opt = sgc.options()
+    ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad, opt), dev)
+    rp, nnz = sgc.spgemm_symbolic(Acl, Ad, ws, opt)
+    C = sgc.spgemm_numeric(Acl, Ad, rp, nnz, ws, opt)
+    sgc.workspace_status(ws)
+    stream = torch.cuda.current_stream()
+
+    def timed_loop(sym_fn, num_fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for e0, e1, e2 in ev:
+            e0.record(stream)
+            sym_fn()
+            e1.record(stream)
+            num_fn()
+            e2.record(stream)
+        torch.cuda.synchronize()
+        sym = [a.elapsed_time(b) for a, b, _ in ev]
+        num = [b.elapsed_time(c) for _, b, c in ev]
+        return sym, num
+
+    sym_c = lambda: sgc.spgemm_symbolic(Acl, Ad, ws, opt, c_row_ptr=rp, sync=False)  # noqa: E731
+    num_c = lambda: sgc.spgemm_numeric(Acl, Ad, rp, nnz, ws, opt, C=C)  # noqa: E731
+    timed_loop(sym_c, num_c, args.warmup)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = sgc.kernel_launches()
+    with ClockSampler(local_rank) as clk:
+        t_wall = time.perf_counter()
+        sym_ms, num_ms = timed_loop(sym_c, num_c, args.steps)
+        t_wall = time.perf_counter() - t_wall
+    barrier()
+    launches = sgc.kernel_launches() - l0
+    sgc.workspace_status(ws)
+    step_ms = float(np.mean([a + b for a, b in zip(sym_ms, num_ms)]))
+    if world > 1:
+        tt = torch.tensor([step_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        step_ms = float(tt.item())
+    value = world * 2.0 * flops / (step_ms * 1e-3) / 1e9
+
+    # ---- plain row-wise method, same GPU ---------------------------------------
+    wsr = sgc.Workspace(sgc.spgemm_rowwise_workspace_size(Ad, Ad, opt), dev)
+    rpr, nnzr = sgc.spgemm_rowwise_symbolic(Ad, Ad, wsr, opt)
+    del C
+    torch.cuda.empty_cache()
+    Cr = sgc.spgemm_rowwise_numeric(Ad, Ad, rpr, nnzr, wsr, opt)
+    sgc.workspace_status(wsr)
+    sym_r = lambda: sgc.spgemm_rowwise_symbolic(Ad, Ad, wsr, opt, c_row_ptr=rpr, sync=False)  # noqa: E731
+    num_r = lambda: sgc.spgemm_rowwise_numeric(Ad, Ad, rpr, nnzr, wsr, opt, C=Cr)  # noqa: E731
+    timed_loop(sym_r, num_r, args.warmup)
+    rsym, rnum = timed_loop(sym_r, num_r, args.steps)
+    sgc.workspace_status(wsr)
+    row_ms = float(np.mean([a + b for a, b in zip(rsym, rnum)]))
+    del Cr
+    torch.cuda.empty_cache()
+
+    # ---- algorithmic bytes ----------------------------------------------------
+    ucol = Acl.ucol.cpu().numpy()
+    staged = int(np.sum(np.diff(A.row_ptr)[ucol]))      # sum over clusters of the B elements staged
+    ncl = Acl.nclusters
+    a_cl_bytes = 8 * 3 * (ncl + 1) + 4 * A.nrows + 8 * ucol.size + A.val.itemsize * Acl.val.numel()
+    c_bytes = 8 * (A.nrows + 1) + nnz * (4 + A.val.itemsize)
+    num_bytes = a_cl_bytes + staged * (4 + A.val.itemsize) + 16 * ucol.size + c_bytes
+    sym_bytes = (8 * 3 * (ncl + 1) + 4 * A.nrows + 8 * ucol.size) + staged * 4 + 16 * ucol.size + 8 * (A.nrows + 1)
+    num_avg = float(np.mean(num_ms))
+    peak, peak_kind = measured_peaks()
+    achieved = num_bytes / (num_avg * 1e-3) / 1e9
+    traffic = traffic_from_profiles("cluster_numeric", args.workload)
+    compulsory = 2 * csr_bytes(A) + c_bytes
+
+    # ---- end to end through the public API, host buffers -----------------------
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda x: torch.from_numpy(x).pin_memory()  # noqa: E731
+        h_rp, h_col, h_val = pin(A.row_ptr), pin(A.col), pin(A.val)
+        e_steps = max(1, min(args.steps, 3))
+        h_out = None
+        times = []
+        for s in range(e_steps + 1):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            Ad.row_ptr.copy_(h_rp, non_blocking=True)
+            Ad.col.copy_(h_col, non_blocking=True)
+            Ad.val.copy_(h_val, non_blocking=True)
+            Acl2 = sgc.csr_cluster_build(Ad, perm, cptr, sgc.LAYOUT_MASKED)
+            C2 = sgc.spgemm(Acl2, Ad, opt)
+            if h_out is None:
+                h_out = (torch.empty(C2.row_ptr.shape, dtype=torch.int64, pin_memory=True),
+                         torch.empty(C2.col.shape, dtype=torch.int32, pin_memory=True),
+                         torch.empty(C2.val.shape, dtype=C2.val.dtype, pin_memory=True))
+            h_out[0].copy_(C2.row_ptr, non_blocking=True)
+            h_out[1].copy_(C2.col, non_blocking=True)
+            h_out[2].copy_(C2.val, non_blocking=True)
+            torch.cuda.synchronize()
+            if s > 0:
+                times.append(time.perf_counter() - t)
+            del C2, Acl2
+        e_s = float(np.mean(times))
+        h2d = int(h_rp.numel() * 8 + h_col.numel() * 4 + h_val.numel() * h_val.element_size())
+        d2h = int(h_out[0].numel() * 8 + h_out[1].numel() * 4 + h_out[2].numel() * h_out[2].element_size())
+        e2e = {"value": round(world * 2.0 * flops / e_s / 1e9, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "step": "H2D of A (CSR) from pinned host memory, csr_cluster_build, spgemm_symbolic + "
+                       "spgemm_numeric, D2H of C (CSR) to pinned host memory"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        gf, cores, nrows_s, dt = oracle_sample_rate(A, 12.0)
+        cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"{nrows_s} random rows of C ({dt:.1f} s; serial std::map Gustavson per row, rows "
+                         f"over {cores} OpenMP threads), rate scaled to GFLOP/s"}
+
+    if rank == 0:
+        clocks = clk.summary()
+        out = {
+            "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": A.val.dtype.name.replace("float", "f").replace("int", "i"),
+            "data": "synthetic",
+            "config": {"workload": desc, "n": A.nrows, "nnz_A": A.nnz, "flops": flops, "nnz_C": nnz,
+                       "nclusters": ncl, "l2": "inputs larger than L2 (A and B = 1.3 GB each); no flush",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "phases_ms": {"symbolic": round(float(np.mean(sym_ms)), 4), "numeric": round(num_avg, 4)},
+            "rowwise": {"value": round(world * 2.0 * flops / (row_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
+                        "ms_per_step": round(row_ms, 4),
+                        "phases_ms": {"symbolic": round(float(np.mean(rsym)), 4),
+                                      "numeric": round(float(np.mean(rnum)), 4)}},
+            "speedup_vs_rowwise": round(row_ms / step_ms, 4),
+            "hbm": {"step_GBs": round((num_bytes + sym_bytes) / (step_ms * 1e-3) / 1e9, 2),
+                    "compulsory_bytes": compulsory,
+                    "compulsory_frac": round(compulsory / (step_ms * 1e-3) / (peak * 1e9), 4),
+                    "staged_B_elements": staged, "reuse_R": round(flops / max(staged, 1), 4)},
+            "roofline": {"bound": "hbm", "kernel": "cluster-wise numeric phase (spgemm_numeric)",
+                         "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": num_bytes},
+            "preprocess": {"hcluster_s": round(t_hc, 3), "csr_cluster_build_s": round(t_build, 4),
+                           "in_spgemm_units": round((t_hc + t_build) / (step_ms * 1e-3), 1)},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+            "timed_wall_s": round(t_wall, 3),
+        }
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -122,6 +122,10 @@ typedef struct sgc_options {
 /* Version of this ABI (SGC_ABI_VERSION). */
 int sgc_abi_version(void);
 
+/* Number of CUDA kernels the library has launched in this process so far
+ * (all threads; a monotone counter for reporting launch counts). */
+long long sgc_kernel_launches(void);
+
 /* Message for the calling thread's last failed call ("" if none).  The
  * pointer stays valid until the thread's next call into the library. */
 const char* sgc_last_error(void);

@@ -2,6 +2,7 @@
 // carving, status words, and the sequence of launches of each call.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -13,6 +14,9 @@
 namespace sgc {
 
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
+
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
@@ -120,8 +124,8 @@ int check_cluster(const sgc_csr_cluster* A, bool need_val) {
 }
 
 AClusterView cview(const sgc_csr_cluster* A, bool with_val) {
-  return AClusterView{A->perm, A->cluster_ptr, A->ucol_ptr, A->ucol, A->mask, A->val_ptr,
-                      with_val ? A->val : nullptr, A->nclusters, A->nrows, A->layout};
+  return AClusterView{A->perm,   A->cluster_ptr, A->ucol_ptr, A->ucol,  A->mask, A->val_ptr,
+                      with_val ? A->val : nullptr, A->nclusters, A->nrows, A->nvals, A->layout};
 }
 BView bview(const sgc_csr* B, bool with_val) {
   return BView{B->row_ptr, B->col, with_val ? B->val : nullptr, B->nrows, B->ncols, B->nnz};
@@ -172,6 +176,8 @@ using namespace sgc;
 extern "C" {
 
 int sgc_abi_version(void) { return SGC_ABI_VERSION; }
+
+long long sgc_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char* sgc_last_error(void) { return g_last_error.c_str(); }
 

@@ -25,13 +25,6 @@ __device__ __forceinline__ void push_heavy(const BinOut& o, int64_t item) {
   o.heavy_items[idx] = item;
 }
 
-// Smallest dense budget class that holds `need` bytes, or -1.
-__device__ __forceinline__ int dense_class(int64_t need) {
-  for (int b = 0; b < NDB; ++b)
-    if (need <= dense_budget(b)) return b;
-  return -1;
-}
-
 // Classify one row by its bound h (symbolic) or exact count (numeric); h > 0.
 __device__ __forceinline__ void classify_row(const BinOut& o, int64_t item, int64_t h, int64_t heavy_limit,
                                              int load_pct) {
@@ -75,9 +68,9 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
     const int64_t T = u1 - u0;
     int cls = -1;
     if (use_dense && U < (1ll << 28) && T < (1ll << 24)) {
-      const int LH = table_log2(min64(U, B.ncols), 75);
-      const DenseLayout L = dense_layout(true, T, U, LH, 0, K, 4, 8, bulk != 0);
-      cls = dense_class(L.total);
+      const int64_t nb = min64(U, B.ncols);
+      const WarpLayout L = warp_layout(true, T, U, 0, table_log2(nb, 75), nb, K, 4, 8, bulk != 0);
+      cls = warp_class(L.total);
     }
     if (lane == 0) {
       o.uc_rec[c] = (int32_t)min64(U, 0x7fffffff);
@@ -108,9 +101,10 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, 
     const int32_t nout = o.nout_rec[c];
     int cls = -1;
     if (nout >= 0) {
-      const int LH = table_log2(nout, 75);
-      const DenseLayout L = dense_layout(false, T, o.uc_rec[c], LH, nout, K, in_bytes, acc_bytes, bulk != 0);
-      cls = dense_class(L.total);
+      const int64_t nva = A.vptr[c + 1] - A.vptr[c];
+      const WarpLayout L =
+          warp_layout(false, T, o.uc_rec[c], nva, table_log2(nout, 75), nout, K, in_bytes, acc_bytes, bulk != 0);
+      cls = warp_class(L.total);
     }
     if (cls >= 0) {
       if (lane == 0) push_dense(o, cls, (int32_t)c);

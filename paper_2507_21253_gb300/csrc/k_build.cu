@@ -164,9 +164,11 @@ cudaError_t cluster_build_count_run(const int64_t* arp, const int32_t* acol, con
   cudaError_t e = cudaMemsetAsync(seen, 0, sizeof(int32_t) * (size_t)(nrows > 0 ? nrows : 1), s);
   if (e != cudaSuccess) return e;
   k_check_cptr<<<1, 32, 0, s>>>(cptr, ncl, nrows, status);
+  note_launches(1);
   const int64_t blocks = (ncl + 7) / 8;
   k_build_count<<<(unsigned)(blocks < 1 ? 1 : (blocks > 65535 * 8 ? 65535 * 8 : blocks)), 256, 0, s>>>(
       arp, acol, perm, cptr, ncl, nrows, layout, uptr, vptr, seen, status);
+  note_launches(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = inclusive_scan_i64(uptr + 1, ncl, scan_tmp, s);
@@ -186,6 +188,7 @@ cudaError_t cluster_build_fill_run(const int64_t* arp, const int32_t* acol, cons
   else
     k_build_fill<uint64_t><<<g, 256, 0, s>>>(arp, acol, (const uint64_t*)aval, out, ucol_out, mask_out,
                                               (uint64_t*)val_out);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -194,6 +197,7 @@ cudaError_t validate_csr_run(const int64_t* rp, const int32_t* col, int64_t nrow
   const int64_t blocks = (nrows + 7) / 8;
   const unsigned g = (unsigned)(blocks < 1 ? 1 : (blocks > 65535 * 8 ? 65535 * 8 : blocks));
   k_validate_csr<<<g, 256, 0, s>>>(rp, col, nrows, ncols, nnz, status, where);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -201,6 +205,7 @@ cudaError_t validate_cluster_run(const AClusterView& A, int64_t ncols, void* sta
   const int64_t blocks = (A.ncl + 7) / 8;
   const unsigned g = (unsigned)(blocks < 1 ? 1 : (blocks > 65535 * 8 ? 65535 * 8 : blocks));
   k_validate_cluster<<<g, 256, 0, s>>>(A, ncols, status);
+  note_launches(1);
   return cudaGetLastError();
 }
 

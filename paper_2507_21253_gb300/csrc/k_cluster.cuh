@@ -1,61 +1,77 @@
 // Cluster-wise SpGEMM kernel (Algorithm 1, ClusterWise_SpGEMM; Sec. 3.1
-// "Access pattern"): one CTA per cluster of A in CSR_Cluster format.
+// "Access pattern"): one warp group (1, 2, 4 or 8 warps) per cluster of A in
+// CSR_Cluster format, several independent groups per CTA, each with its own
+// shared-memory region and mbarrier; warps of a group sync on a named barrier.
 //
-//  1. Stage: every B row k in the cluster's column union is copied into shared
-//     memory once (1D bulk async copies on an mbarrier, or cooperative loads),
-//     so each needed B row is read from memory once per cluster, not once per
-//     row (the reuse Algorithm 1 creates by looping over the cluster's rows
-//     inside the loop over b_kj).
-//  2. Map: the staged column ids are inserted once into a cluster-local hash
-//     table, giving the cluster's output-column union; the staged ids are
-//     rewritten in place as slots (symbolic) or as ranks in column order
-//     (numeric), so each product costs one hash-free indexed update.
-//  3. Accumulate: one warp per cluster row l walks the union columns t in
-//     ascending order and, where row l has a_lt, applies the staged B row to
-//     its dense accumulator (c_lj += a_lt * b_tj, Algorithm 1 inner loop).
+//  1. Stage: every B row k in the cluster's column union, and the cluster's
+//     own value slots, are copied into the warp's shared memory once (1D bulk
+//     async copies completing on the warp's mbarrier, or cooperative loads),
+//     so each needed B row is read from memory once per cluster rather than
+//     once per row of the cluster.
+//  2. Map: the staged column ids are inserted once into a warp-local hash
+//     table, giving the cluster's output-column union; each staged id is then
+//     rewritten in place as a local id (numeric: its rank in column order,
+//     from an interpolation bucket sort of the union).
+//  3. Accumulate in the loop order of Algorithm 1: for each union column t
+//     (ascending), the lanes hold the entries j of B row t, and for each row
+//     l of the cluster having a_lt (a bit of the presence mask) they update
+//     c_lj += a_lt * b_tj in a dense per-row accumulator indexed by local id.
 //     Within one B row the ids are distinct, so lanes never collide; each
-//     (l, j) is accumulated in ascending k, as in the row-wise definition.
-//  4. Emit: symbolic counts a per-row bitmap; numeric writes each row's
-//     entries in rank (= column) order, so no per-row sort is needed.
+//     (l, j) is accumulated in ascending k, the order of the row-wise
+//     definition, without FMA.
+//  4. Emit: symbolic counts a per-row bitmap over local ids; numeric writes
+//     each row's entries in rank (= column) order: no per-row sort.
 #pragma once
 
 #include "k_rows.cuh"
 
 namespace sgc {
 
-constexpr int CL_THREADS = 256;
-__host__ __device__ inline int dense_budget(int b) {
-  const int kb[NDB] = {24, 32, 48, 64, 96, 128, 160, 227};
+constexpr int CL_THREADS = 256;  // 8 independent warps per CTA at most
+
+// Per-warp shared-memory budget classes (bytes), NDB of them.
+__host__ __device__ inline int warp_class_bytes(int b) {
+  const int kb[NDB] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 160, 227};
   return kb[b] * 1024;
 }
 
-struct DenseLayout {
-  int desc, stage_c, stage_v, table, sorted, acc, flags, total;
+struct WarpLayout {
+  int desc, stage_c, stage_v, stage_a, table, sorted, scratch, acc, flags, total;
 };
 
-// Shared-memory layout of one cluster.  T = union columns, U = staged B
-// elements, LH = log2 hash slots, nout = output columns (numeric), K rows.
-__host__ __device__ inline DenseLayout dense_layout(bool sym, int64_t T, int64_t U, int LH, int64_t nout, int K,
-                                                    int in_bytes, int acc_bytes, bool bulk) {
-  DenseLayout L{};
-  int64_t o = 512;  // mbarrier, scan scratch, counters
+// Layout of one cluster in a warp's region.  T union columns, U staged B
+// elements, nva value slots of the cluster, LH log2 hash slots, nout output
+// columns (numeric) or their bound (symbolic), K rows.
+__host__ __device__ inline WarpLayout warp_layout(bool sym, int64_t T, int64_t U, int64_t nva, int LH, int64_t nout,
+                                                  int K, int in_bytes, int acc_bytes, bool bulk) {
+  WarpLayout L{};
+  const int64_t pad_c = bulk ? 6 : 0, pad_v = bulk ? (in_bytes == 8 ? 2 : 6) : 0;
+  int64_t o = 128;  // mbarrier, counters, scan partials
   L.desc = (int)o;
   o += 20 * T;
   o = (o + 15) & ~15ll;
   L.stage_c = (int)o;
-  o += 4 * (U + (bulk ? 6 * T : 0));
+  o += 4 * (U + pad_c * T);
   o = (o + 15) & ~15ll;
   L.stage_v = (int)o;
-  if (!sym) o += (int64_t)in_bytes * (U + (bulk ? (in_bytes == 8 ? 2 : 6) * T : 0));
-  o = (o + 15) & ~15ll;
+  L.stage_a = (int)o;
+  if (!sym) {
+    o += (int64_t)in_bytes * (U + pad_v * T);
+    o = (o + 15) & ~15ll;
+    L.stage_a = (int)o;
+    o += (int64_t)in_bytes * (nva + 2 * (16 / in_bytes));
+    o = (o + 15) & ~15ll;
+  }
   L.table = (int)o;
   o += 4ll << LH;
   if (sym) {
-    L.acc = (int)o;  // per-row bitmaps over hash slots
-    o += (int64_t)K * (((1ll << LH) + 31) / 32) * 4;
+    L.flags = (int)o;  // per-row bitmaps over local ids
+    o += 4ll * K * ((nout + 31) / 32);
   } else {
     L.sorted = (int)o;
     o += 4 * nout;
+    L.scratch = (int)o;  // bucket starts, cursors, compacted keys, their slots
+    o += 16 * nout + 16;
     o = (o + 15) & ~15ll;
     L.acc = (int)o;
     o += (int64_t)acc_bytes * K * nout;
@@ -67,133 +83,199 @@ __host__ __device__ inline DenseLayout dense_layout(bool sym, int64_t T, int64_t
   return L;
 }
 
-// descriptor of union column t (20 bytes, struct-of-arrays in shared memory)
-struct DescPtr {
-  int32_t* off_c;  // staged col offset (elements); bit 31 set: copy with loads (bulk mode)
-  int32_t* off_v;
+// Smallest class holding `need` bytes, or -1.
+__host__ __device__ inline int warp_class(int64_t need) {
+  for (int b = 0; b < NDB; ++b)
+    if (need <= warp_class_bytes(b)) return b;
+  return -1;
+}
+
+// Warps per cluster for a shared-memory class: small footprints are small
+// clusters (one warp each); larger ones get a warp group so that more warps
+// share each byte of shared memory.
+__host__ __device__ inline int group_warps(int cls) {
+  const int b = warp_class_bytes(cls);
+  return b <= 8 * 1024 ? 1 : (b <= 16 * 1024 ? 2 : (b <= 48 * 1024 ? 4 : 8));
+}
+__host__ __device__ inline int groups_per_cta(int cls) {
+  int g = 8 / group_warps(cls);
+  const int by_smem = SMEM_MAX / warp_class_bytes(cls);
+  return g < by_smem ? g : (by_smem < 1 ? 1 : by_smem);
+}
+
+struct WDesc {  // struct-of-arrays per union column, in the group's region
+  int32_t* off_c;  // staged col offset (elements); bit 31: copy with loads (bulk mode)
+  int32_t* off_v;  // staged val offset (elements)
   int32_t* len;
   uint32_t* mask;
-  int32_t* aoff;
+  int32_t* aoff;   // MASKED: staged value slot of (t, lowest row of the mask)
 };
-__device__ __forceinline__ DescPtr desc_ptrs(unsigned char* base, int64_t T) {
-  DescPtr d;
-  d.off_c = (int32_t*)base;
-  d.off_v = d.off_c + T;
-  d.len = d.off_v + T;
-  d.mask = (uint32_t*)(d.len + T);
-  d.aoff = (int32_t*)(d.mask + T);
-  return d;
+
+__device__ __forceinline__ int bucket_of(int32_t key, int32_t kmin, int n, uint64_t range) {
+  return (int)(((uint64_t)(uint32_t)(key - kmin) * (uint64_t)n) / range);
+}
+
+// Synchronises the threads of one group (one warp: __syncwarp).
+__device__ __forceinline__ void group_sync(int gw, int gid) {
+  if (gw == 1) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + gid), "r"(gw * 32) : "memory");
+  }
+}
+
+// Exclusive scan over the group's threads; red: >= 2*gw+1 ints in the group header.
+__device__ __forceinline__ int group_excl_scan(int v, int gw, int gid, int wg, int* red, int* total) {
+  const int lane = lane_id();
+  const int incl = warp_incl_scan(v);
+  if (gw == 1) {
+    *total = __shfl_sync(FULL, incl, 31);
+    return incl - v;
+  }
+  if (lane == 31) red[wg] = incl;
+  group_sync(gw, gid);
+  int base = 0, tot = 0;
+  for (int q = 0; q < gw; ++q) {
+    const int x = red[q];
+    if (q < wg) base += x;
+    tot += x;
+  }
+  group_sync(gw, gid);
+  *total = tot;
+  return base + incl - v;
 }
 
 template <bool SYM, int DT>
-__global__ void __launch_bounds__(CL_THREADS) k_cluster_dense(AClusterView A, BView B, CView C, int64_t* c_rp_sym,
+__global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BView B, CView C, int64_t* c_rp_sym,
                                                               const int32_t* items, const int32_t* count_ptr,
                                                               int32_t* nout_rec, const int32_t* uc_rec, int mode,
-                                                              void* status) {
+                                                              int region_bytes, int gw, void* status) {
   using In = typename VT<DT>::In;
   using Acc = typename VT<DT>::Acc;
   extern __shared__ __align__(16) unsigned char sm[];
-  uint64_t* bar = (uint64_t*)sm;
-  int64_t* tmp = (int64_t*)(sm + 16);   // 34 int64 (scan scratch)
-  int* cnt_s = (int*)(sm + 16 + 34 * 8);  // [0] = distinct outputs
-  const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5, nw = blockDim.x >> 5;
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  const int gid = warp / gw, wg = warp % gw, gt = wg * 32 + lane, GT = gw * 32;
+  const int ngroups = (blockDim.x >> 5) / gw;
+  unsigned char* my = sm + (size_t)gid * region_bytes;
+  uint64_t* bar = (uint64_t*)my;
+  int* hdr = (int*)(my + 8);  // [0] distinct count, [1..gw] copy flags, [2..gw+1] scan partials (phases apart)
   DevStatus* st = (DevStatus*)status;
   const bool bulk = mode == 1;
   if (bulk) {
-    if (tid == 0) {
+    if (gt == 0) {
       mbar_init(bar, 1);
       fence_barrier_init();
     }
-    __syncthreads();
   }
+  group_sync(gw, gid);
   uint32_t phase = 0;
+  const unsigned lt = lanemask_lt();
   const int32_t count = *count_ptr;
-  for (int32_t it = blockIdx.x; it < count; it += gridDim.x) {
+  for (int64_t it = (int64_t)blockIdx.x * ngroups + gid; it < count; it += (int64_t)gridDim.x * ngroups) {
     const int32_t c = items[it];
     const int64_t p0 = A.cptr[c];
     const int K = (int)(A.cptr[c + 1] - p0);
-    const int64_t u0 = A.uptr[c], u1 = A.uptr[c + 1], v0 = A.vptr[c];
-    const int64_t T = u1 - u0;
+    const int64_t u0 = A.uptr[c], T = A.uptr[c + 1] - u0;
+    const int64_t v0 = A.vptr[c], nva = A.vptr[c + 1] - v0;
     const int64_t U = uc_rec[c];
-    int LH;
-    int64_t nout = 0;
-    if (SYM) {
-      LH = table_log2(min64(U, B.ncols), 75);
-    } else {
-      nout = nout_rec[c];
-      LH = table_log2(nout, 75);
-    }
-    const DenseLayout Ly = dense_layout(SYM, T, U, LH, nout, K, sizeof(In), sizeof(Acc), bulk);
-    const DescPtr d = desc_ptrs(sm + Ly.desc, T);
-    int32_t* stage_c = (int32_t*)(sm + Ly.stage_c);
-    In* stage_v = (In*)(sm + Ly.stage_v);
-    int32_t* table = (int32_t*)(sm + Ly.table);
+    const int64_t nb = SYM ? min64(U, B.ncols) : (int64_t)nout_rec[c];  // bound / exact output columns
+    const int LH = table_log2(nb, 75);
+    const WarpLayout Ly = warp_layout(SYM, T, U, SYM ? 0 : nva, LH, nb, K, sizeof(In), sizeof(Acc), bulk);
+    WDesc d;
+    d.off_c = (int32_t*)(my + Ly.desc);
+    d.off_v = d.off_c + T;
+    d.len = d.off_v + T;
+    d.mask = (uint32_t*)(d.len + T);
+    d.aoff = (int32_t*)(d.mask + T);
+    int32_t* stage_c = (int32_t*)(my + Ly.stage_c);
+    In* stage_v = (In*)(my + Ly.stage_v);
+    In* stage_a = (In*)(my + Ly.stage_a);
+    int32_t* table = (int32_t*)(my + Ly.table);
     const int TH = 1 << LH;
-    if (tid == 0) *cnt_s = 0;
-    for (int i = tid; i < TH; i += blockDim.x) table[i] = EMPTY_KEY;
 
-    // ---- 1. descriptors and staging -------------------------------------
+    // ---- 1. descriptors and staging ---------------------------------------
     int64_t run_c = 0, run_v = 0, run_a = 0;
-    bool any_bulk = false;
-    for (int64_t tb = 0; tb < T; tb += blockDim.x) {
-      const int64_t i = tb + tid;
+    bool issued = false;
+    if (bulk) fence_proxy_async_smem();  // earlier generic accesses to the region precede async writes
+    for (int64_t tb = 0; tb < T; tb += GT) {
+      const int64_t i = tb + gt;
       int wc = 0, wv = 0, shc = 0, shv = 0, len = 0;
       uint32_t m = 0;
       int64_t s = 0;
       bool ldg = !bulk;
       if (i < T) {
         const int32_t k = A.ucol[u0 + i];
+        m = A.mask[u0 + i];
         s = B.rp[k];
         const int64_t e = B.rp[k + 1];
         len = (int)(e - s);
-        m = A.mask[u0 + i];
         if (bulk) {
-          constexpr int VA = 16 / (int)sizeof(In);
-          const int64_t cs = s & ~3ll, ce = (e + 3) & ~3ll;
-          const int64_t vs = s & ~(int64_t)(VA - 1), ve = (e + VA - 1) & ~(int64_t)(VA - 1);
-          wc = (int)(ce - cs);
-          wv = SYM ? 0 : (int)(ve - vs);
-          shc = (int)(s - cs);
-          shv = (int)(s - vs);
-          if (ce > B.nnz || (!SYM && ve > B.nnz)) ldg = true;  // window would pass the array end
-          if (len == 0) wc = wv = shc = shv = 0;
+          if (len > 0) {
+            constexpr int VA = 16 / (int)sizeof(In);
+            const int64_t cs = s & ~3ll, ce = (e + 3) & ~3ll;
+            const int64_t vs = s & ~(int64_t)(VA - 1), ve = (e + VA - 1) & ~(int64_t)(VA - 1);
+            wc = (int)(ce - cs);
+            wv = SYM ? 0 : (int)(ve - vs);
+            shc = (int)(s - cs);
+            shv = (int)(s - vs);
+            if (ce > B.nnz || (!SYM && ve > B.nnz)) ldg = true;  // window would pass the array end
+          }
         } else {
           wc = len;
           wv = SYM ? 0 : len;
         }
       }
-      int64_t tc, tv, ta;
-      const int64_t oc = block_excl_scan<int64_t>(wc, tmp, &tc);
-      const int64_t ov = SYM ? 0 : block_excl_scan<int64_t>(wv, tmp, &tv);
-      const int64_t oa = (SYM || A.layout != SGC_LAYOUT_MASKED) ? 0 : block_excl_scan<int64_t>(__popc(m), tmp, &ta);
+      int tc, tv = 0, ta;
+      const int oc = group_excl_scan(wc, gw, gid, wg, hdr + 2, &tc);
+      const int ov = SYM ? 0 : group_excl_scan(wv, gw, gid, wg, hdr + 2, &tv);
+      const int pa = __popc(m);
+      const int oa = group_excl_scan(pa, gw, gid, wg, hdr + 2, &ta);
       if (i < T) {
-        const int64_t dc = run_c + oc + shc, dv = run_v + ov + shv;
-        d.off_c[i] = (int32_t)dc | (ldg ? (int32_t)0x80000000 : 0);
-        d.off_v[i] = (int32_t)dv;
+        d.off_c[i] = (int32_t)(run_c + oc + shc) | (ldg ? (int32_t)0x80000000 : 0);
+        d.off_v[i] = (int32_t)(run_v + ov + shv);
         d.len[i] = len;
         d.mask[i] = m;
         d.aoff[i] = (int32_t)(run_a + oa);
-      }
-      if (bulk && i < T && !ldg && len > 0) {
-        const uint32_t bytes = (uint32_t)wc * 4u + (SYM ? 0u : (uint32_t)wv * (uint32_t)sizeof(In));
-        fence_proxy_async_smem();  // earlier generic accesses to this memory precede the async writes
-        mbar_expect_tx(bar, bytes);
-        bulk_g2s(stage_c + run_c + oc, B.col + (s - shc), (uint32_t)wc * 4u, bar);
-        if (!SYM) bulk_g2s(stage_v + run_v + ov, (const In*)B.val + (s - shv), (uint32_t)wv * sizeof(In), bar);
-        any_bulk = true;
+        if (bulk && !ldg && len > 0) {
+          mbar_expect_tx(bar, (uint32_t)wc * 4u + (uint32_t)wv * (uint32_t)sizeof(In));
+          bulk_g2s(stage_c + run_c + oc, B.col + (s - shc), (uint32_t)wc * 4u, bar);
+          if (!SYM) bulk_g2s(stage_v + run_v + ov, (const In*)B.val + (s - shv), (uint32_t)wv * sizeof(In), bar);
+          issued = true;
+        }
       }
       run_c += tc;
-      if (!SYM) run_v += tv;
-      if (!SYM && A.layout == SGC_LAYOUT_MASKED) run_a += ta;
+      run_v += tv;
+      run_a += ta;
     }
-    __syncthreads();
+    // the cluster's own value slots (numeric): one window covering [v0, v0 + nva)
+    int ashift = 0;
+    if (!SYM && nva > 0) {
+      constexpr int VA = 16 / (int)sizeof(In);
+      const int64_t as = v0 & ~(int64_t)(VA - 1), ae = (v0 + nva + VA - 1) & ~(int64_t)(VA - 1);
+      const bool win_ok = bulk && ae <= A.nvals && ((uintptr_t)A.val & 15u) == 0;
+      if (win_ok) {
+        ashift = (int)(v0 - as);
+        if (gt == 0) {
+          mbar_expect_tx(bar, (uint32_t)((ae - as) * (int64_t)sizeof(In)));
+          bulk_g2s(stage_a, (const In*)A.val + as, (uint32_t)((ae - as) * (int64_t)sizeof(In)), bar);
+          issued = true;
+        }
+      } else {
+        for (int64_t q = gt; q < nva; q += GT) stage_a[q] = ((const In*)A.val)[v0 + q];
+      }
+    }
+    // table init overlaps the copies in flight
+    for (int x = gt; x < TH; x += GT) table[x] = EMPTY_KEY;
+    if (gt == 0) hdr[0] = 0;
+    group_sync(gw, gid);  // descriptors visible to the group
     // rows copied with loads: all of them in LDG mode, window-overflow rows in bulk mode
-    for (int64_t i = w; i < T; i += nw) {
+    for (int64_t i = wg; i < T; i += gw) {
       const int32_t oc = d.off_c[i];
-      if (!(oc & 0x80000000) || d.len[i] == 0) continue;
+      if (!(oc & 0x80000000)) continue;
+      const int n = d.len[i];
+      if (n == 0) continue;
       const int32_t k = A.ucol[u0 + i];
       const int64_t s = B.rp[k];
-      const int n = d.len[i];
       const int dc = oc & 0x7fffffff, dv = d.off_v[i];
       for (int q = lane; q < n; q += 32) {
         stage_c[dc + q] = B.col[s + q];
@@ -201,153 +283,208 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_dense(AClusterView A, BV
       }
     }
     if (bulk) {
-      const int issued = __syncthreads_or(any_bulk);
-      if (issued) {
-        if (tid == 0) mbar_arrive(bar);
+      // one arrival per phase, after every expect_tx of the group
+      const int any = __any_sync(FULL, issued);
+      if (lane == 0) hdr[1 + wg] = any;
+      group_sync(gw, gid);
+      int grp_any = 0;
+      for (int q = 0; q < gw; ++q) grp_any |= hdr[1 + q];
+      if (grp_any) {
+        if (gt == 0) mbar_arrive(bar);
         const bool ok = mbar_wait_bounded(bar, phase, WAIT_LIMIT);
         phase ^= 1u;
-        if (!__syncthreads_and(ok)) {
-          if (tid == 0) raise(st, DEV_TIMEOUT, 30, c);
-          return;
+        if (!__all_sync(FULL, ok)) {
+          if (lane == 0) raise(st, DEV_TIMEOUT, 30, c);
+          return;  // timeouts are not expected; the group's other warps time out alike
         }
       }
     }
-    __syncthreads();
+    group_sync(gw, gid);
 
-    // ---- 2. map staged column ids to cluster-local ids ----------------------
-    int newc = 0;
-    for (int64_t i = w; i < T; i += nw) {
+    // ---- 2. map staged column ids to slots ---------------------------------
+    bool full = false;
+    int newk = 0;
+    for (int64_t i = wg; i < T; i += gw) {
       const int n = d.len[i];
       const int dc = d.off_c[i] & 0x7fffffff;
       for (int q = lane; q < n; q += 32) {
         bool nwk;
         const int slot = hash_find_or_insert(table, LH, stage_c[dc + q], &nwk);
         if (slot < 0) {
-          raise(st, DEV_TABLE_FULL, 31, c);
+          full = true;
           continue;
         }
-        newc += nwk;
+        newk += nwk;
         stage_c[dc + q] = slot;
       }
     }
-    newc = warp_sum(newc);
-    if (lane == 0 && newc) atomicAdd(cnt_s, newc);
-    __syncthreads();
-    const int n_out = *cnt_s;
-
+    newk = warp_sum(newk);
+    if (lane == 0 && newk) atomicAdd(&hdr[0], newk);
+    if (__any_sync(FULL, full) && lane == 0) raise(st, DEV_TABLE_FULL, 31, c);
+    group_sync(gw, gid);
+    const int n_out = hdr[0];
+    // ---- 2b. local ids: compaction order (symbolic) or rank in column order (numeric)
+    if (wg == 0) {
+      if constexpr (SYM) {
+        int base = 0;
+        for (int x0 = 0; x0 < TH; x0 += 32) {
+          const int x = x0 + lane;
+          const bool occ = table[x] != EMPTY_KEY;
+          const unsigned bal = __ballot_sync(FULL, occ);
+          if (occ) table[x] = base + __popc(bal & lt);
+          base += __popc(bal);
+        }
+      } else if (n_out == nb) {
+        int32_t* srt = (int32_t*)(my + Ly.sorted);
+        int32_t* bst = (int32_t*)(my + Ly.scratch);
+        int32_t* bcur = bst + nb;
+        int32_t* bkey = bcur + nb;
+        int32_t* kslot = bkey + nb;
+        int32_t kmin = PAD_KEY, kmax = -1;
+        int base = 0;
+        for (int x0 = 0; x0 < TH; x0 += 32) {
+          const int x = x0 + lane;
+          const int32_t key = table[x];
+          const bool occ = key != EMPTY_KEY;
+          const unsigned bal = __ballot_sync(FULL, occ);
+          if (occ) {
+            const int pos = base + __popc(bal & lt);
+            bkey[pos] = key;
+            kslot[pos] = x;
+            kmin = min(kmin, key);
+            kmax = max(kmax, key);
+          }
+          base += __popc(bal);
+        }
+        kmin = warp_min(kmin);
+        kmax = warp_max(kmax);
+        const uint64_t range = (uint64_t)((int64_t)kmax - (int64_t)kmin + 1);
+        for (int x = lane; x < n_out; x += 32) bst[x] = 0;
+        __syncwarp();
+        for (int x = lane; x < n_out; x += 32) atomicAdd(&bst[bucket_of(bkey[x], kmin, n_out, range)], 1);
+        __syncwarp();
+        int carry = 0;
+        for (int x0 = 0; x0 < n_out; x0 += 32) {
+          const int x = x0 + lane;
+          const int v = x < n_out ? bst[x] : 0;
+          const int ex = warp_incl_scan(v) - v;
+          if (x < n_out) {
+            bst[x] = carry + ex;  // bucket start
+            bcur[x] = carry + ex;
+          }
+          carry += __shfl_sync(FULL, ex + v, 31);
+        }
+        __syncwarp();
+        for (int x = lane; x < n_out; x += 32)
+          srt[atomicAdd(&bcur[bucket_of(bkey[x], kmin, n_out, range)], 1)] = bkey[x];
+        __syncwarp();
+        for (int x = lane; x < n_out; x += 32) {
+          const int32_t key = bkey[x];
+          const int b = bucket_of(key, kmin, n_out, range);
+          const int bs = bst[b], be = bcur[b];
+          int r = bs;
+          for (int y = bs; y < be; ++y) r += srt[y] < key;
+          table[kslot[x]] = r;  // slot -> rank
+        }
+        __syncwarp();
+        for (int x = lane; x < n_out; x += 32) srt[table[kslot[x]]] = bkey[x];  // sorted keys
+      }
+    }
+    group_sync(gw, gid);
+    if (!SYM && n_out != nb) {
+      if (gt == 0) raise(st, DEV_INTERNAL, 32, c);
+      group_sync(gw, gid);
+      continue;
+    }
+    // rewrite staged ids: slot -> local id
+    for (int64_t i = wg; i < T; i += gw) {
+      const int n = d.len[i];
+      const int dc = d.off_c[i] & 0x7fffffff;
+      for (int q = lane; q < n; q += 32) stage_c[dc + q] = table[stage_c[dc + q]];
+    }
     if constexpr (SYM) {
-      // ---- 3s/4s. per-row bitmaps over slots, counted ------------------------
-      const int WPR = (TH + 31) / 32;
-      uint32_t* rb = (uint32_t*)(sm + Ly.acc);
-      for (int i = tid; i < K * WPR; i += blockDim.x) rb[i] = 0;
-      __syncthreads();
-      for (int l = w; l < K; l += nw) {
+      const int WPR = (n_out + 31) / 32;
+      uint32_t* rb = (uint32_t*)(my + Ly.flags);
+      for (int x = gt; x < K * WPR; x += GT) rb[x] = 0;
+      group_sync(gw, gid);
+      // ---- 3s. per-row bitmaps over local ids: warp per row, own columns only
+      for (int l = wg; l < K; l += gw) {
         uint32_t* mine = rb + (size_t)l * WPR;
-        for (int64_t i = 0; i < T; ++i) {
-          if (!((d.mask[i] >> l) & 1u)) continue;
-          const int n = d.len[i];
-          const int dc = d.off_c[i] & 0x7fffffff;
-          for (int q = lane; q < n; q += 32) {
-            const int slot = stage_c[dc + q];
-            atomicOr(&mine[slot >> 5], 1u << (slot & 31));
+        for (int64_t tb = 0; tb < T; tb += 32) {
+          const uint32_t mm = tb + lane < T ? d.mask[tb + lane] : 0u;
+          unsigned bits = __ballot_sync(FULL, (mm >> l) & 1u);
+          while (bits) {
+            const int64_t i = tb + __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int n = d.len[i];
+            const int dc = d.off_c[i] & 0x7fffffff;
+            for (int q = lane; q < n; q += 32) {
+              const int lid = stage_c[dc + q];
+              atomicOr(&mine[lid >> 5], 1u << (lid & 31));
+            }
           }
         }
         __syncwarp();
-        int64_t cc = 0;
-        for (int i = lane; i < WPR; i += 32) cc += __popc(mine[i]);
+        int cc = 0;
+        for (int x = lane; x < WPR; x += 32) cc += __popc(mine[x]);
         cc = warp_sum(cc);
         if (lane == 0) c_rp_sym[A.perm[p0 + l] + 1] = cc;
       }
-      if (tid == 0) nout_rec[c] = n_out;
-      __syncthreads();
+      if (gt == 0) nout_rec[c] = n_out;
     } else {
-      if (n_out != nout) {
-        if (tid == 0) raise(st, DEV_INTERNAL, 32, c);
-        __syncthreads();
-        continue;
+      const int32_t* srt = (const int32_t*)(my + Ly.sorted);
+      Acc* acc = (Acc*)(my + Ly.acc);
+      uint8_t* flg = (uint8_t*)(my + Ly.flags);
+      for (int64_t x = gt; x < (int64_t)K * n_out; x += GT) {
+        acc[x] = Acc(0);
+        flg[x] = 0;
       }
-      // ---- 2b. ranks in column order: compact slots, count smaller keys ----
-      int32_t* sorted = (int32_t*)(sm + Ly.sorted);
-      int32_t* skey = (int32_t*)(sm + Ly.acc);       // aliases the accumulators until step 3
-      int32_t* sslot = skey + nout;
-      {
-        const int SPT = (TH + blockDim.x - 1) / blockDim.x;
-        int cnt = 0;
-        for (int q = 0; q < SPT; ++q) {
-          const int s = tid * SPT + q;
-          if (s < TH && table[s] != EMPTY_KEY) ++cnt;
-        }
-        int64_t tot;
-        int pos = (int)block_excl_scan<int64_t>(cnt, tmp, &tot);
-        for (int q = 0; q < SPT; ++q) {
-          const int s = tid * SPT + q;
-          if (s < TH && table[s] != EMPTY_KEY) {
-            skey[pos] = table[s];
-            sslot[pos] = s;
-            ++pos;
-          }
-        }
-      }
-      __syncthreads();
-      for (int i = tid; i < n_out; i += blockDim.x) {
-        const int32_t key = skey[i];
-        int r = 0;
-        for (int j = 0; j < n_out; ++j) r += skey[j] < key;
-        table[sslot[i]] = r;  // slot -> rank (the key array is no longer needed)
-        sorted[r] = key;
-      }
-      __syncthreads();
-      for (int64_t i = w; i < T; i += nw) {
-        const int n = d.len[i];
-        const int dc = d.off_c[i] & 0x7fffffff;
-        for (int q = lane; q < n; q += 32) stage_c[dc + q] = table[stage_c[dc + q]];
-      }
-      Acc* acc = (Acc*)(sm + Ly.acc);
-      uint8_t* flg = (uint8_t*)(sm + Ly.flags);
-      __syncthreads();
-      for (int64_t i = tid; i < (int64_t)K * n_out; i += blockDim.x) {
-        acc[i] = Acc(0);
-        flg[i] = 0;
-      }
-      __syncthreads();
-      // ---- 3. accumulate: warp per cluster row, ascending t ------------------
-      for (int l = w; l < K; l += nw) {
+      group_sync(gw, gid);
+      const In* av = stage_a + ashift;
+      const bool padded = A.layout == SGC_LAYOUT_PADDED;
+      // ---- 3. accumulate: warp per row, the row's union columns in ascending order
+      for (int l = wg; l < K; l += gw) {
         Acc* al = acc + (size_t)l * n_out;
         uint8_t* fl = flg + (size_t)l * n_out;
         const uint32_t below = (1u << l) - 1u;
-        for (int64_t i = 0; i < T; ++i) {
-          const uint32_t m = d.mask[i];
-          if (!((m >> l) & 1u)) continue;
-          const int64_t ai = A.layout == SGC_LAYOUT_PADDED ? v0 + i * K + l : v0 + d.aoff[i] + __popc(m & below);
-          const In a = ((const In*)A.val)[ai];
-          const int n = d.len[i];
-          const int dc = d.off_c[i] & 0x7fffffff, dv = d.off_v[i];
-          for (int q = lane; q < n; q += 32) {
-            const int lid = stage_c[dc + q];
-            al[lid] = VT<DT>::add(al[lid], VT<DT>::mul(a, stage_v[dv + q]));
-            fl[lid] = 1;
+        for (int64_t tb = 0; tb < T; tb += 32) {
+          const uint32_t mm = tb + lane < T ? d.mask[tb + lane] : 0u;
+          unsigned bits = __ballot_sync(FULL, (mm >> l) & 1u);
+          while (bits) {
+            const int src = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int64_t i = tb + src;
+            const uint32_t m = __shfl_sync(FULL, mm, src);
+            const int n = d.len[i];
+            const int dc = d.off_c[i] & 0x7fffffff, dv = d.off_v[i];
+            const In a = padded ? av[i * K + l] : av[d.aoff[i] + __popc(m & below)];
+            for (int q = lane; q < n; q += 32) {
+              const int lid = stage_c[dc + q];
+              al[lid] = VT<DT>::add(al[lid], VT<DT>::mul(a, stage_v[dv + q]));
+              fl[lid] = 1;
+            }
+            __syncwarp();
           }
-          __syncwarp();
         }
         // ---- 4. emit row l in column order ----------------------------------
         const int64_t orow = A.perm[p0 + l];
         const int64_t out0 = C.rp[orow], expect = C.rp[orow + 1] - out0;
-        int64_t n = 0;
-        for (int b = 0; b < n_out; b += 32) {
-          const int x = b + lane;
+        int64_t nn = 0;
+        for (int x0 = 0; x0 < n_out; x0 += 32) {
+          const int x = x0 + lane;
           const bool f = x < n_out && fl[x];
           const unsigned bal = __ballot_sync(FULL, f);
-          if (f && n + __popc(bal & lanemask_lt()) < expect) {
-            const int64_t pos = out0 + n + __popc(bal & lanemask_lt());
-            C.col[pos] = sorted[x];
-            ((In*)C.val)[pos] = VT<DT>::out(al[x]);
+          const int64_t pos = nn + __popc(bal & lt);
+          if (f && pos < expect) {
+            C.col[out0 + pos] = srt[x];
+            ((In*)C.val)[out0 + pos] = VT<DT>::out(al[x]);
           }
-          n += __popc(bal);
+          nn += __popc(bal);
         }
-        if (n != expect && lane == 0) raise(st, DEV_INTERNAL, 33, orow);
+        if (nn != expect && lane == 0) raise(st, DEV_INTERNAL, 33, orow);
       }
-      __syncthreads();
     }
+    group_sync(gw, gid);
   }
 }
 

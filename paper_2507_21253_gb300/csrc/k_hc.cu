@@ -238,15 +238,18 @@ cudaError_t hc_candidates_run(const int64_t* arp, const int32_t* acol, int64_t n
   if (e != cudaSuccess) return e;
   const unsigned g = grid_for(nrows, 8, sms, 8);
   k_tr_count<<<g, 256, 0, s>>>(arp, acol, nrows, (unsigned long long*)(trp + 1));
+  note_launches(1);
   e = inclusive_scan_i64(trp + 1, ncols, scan_tmp, s);
   if (e != cudaSuccess) return e;
   k_tr_scatter<<<g, 256, 0, s>>>(arp, acol, nrows, trp, cursor, tcol);
+  note_launches(1);
   // ---- bins by the flop bound of A*A^T rows
   e = cudaMemsetAsync(bins.count, 0, sizeof(int32_t) * NBIN_ALL, s);
   if (e != cudaSuccess) return e;
   const ACsrView av{arp, acol, nullptr, nrows};
   const BView atv{trp, tcol, nullptr, ncols, nrows, nnz};
   k_bin_rows_sym<<<g, 256, 0, s>>>(av, atv, dummy_rp, bins, 75);
+  note_launches(1);
   // rows with no overlap at all produce no candidates: fill all outputs with -1 first
   e = cudaMemsetAsync(cj, 0xff, sizeof(int32_t) * nrows * topk, s);
   if (e != cudaSuccess) return e;
@@ -269,11 +272,13 @@ cudaError_t hc_candidates_run(const int64_t* arp, const int32_t* acol, int64_t n
     const int b = lg - LOG2T_MIN;
     kh<<<grid_for(nrows, warps, sms, occ), warps * 32, smem, s>>>(av, atv, bins.row_items + (int64_t)b * nrows,
                                                                    bins.count + NDB + b, lg, th, to, status);
+    note_launches(1);
   }
   const size_t hsmem = 4 * TOPK_W + sizeof(Cand) * 48 + 16;
   const int occ = occupancy(k_topk_heavy, TOPK_THREADS, hsmem);
   k_topk_heavy<<<grid_for(nrows, 1, sms, occ), TOPK_THREADS, hsmem, s>>>(av, atv, bins.heavy_items,
                                                                           bins.count + BIN_HEAVY, th, to);
+  note_launches(1);
   return cudaGetLastError();
 }
 

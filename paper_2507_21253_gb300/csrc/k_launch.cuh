@@ -50,6 +50,7 @@ cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const B
     const int b = lg - LOG2T_MIN;
     kh<<<grid, warps * 32, smem, L.s>>>(Ac, Acl, B, C, c_rp, bins.row_items + (int64_t)b * bins.nrows,
                                          bins.count + NDB + b, lg, status);
+    note_launches(1);
   }
   auto kv = k_row_heavy<SYM, DT, SRC>;
   const size_t hsmem = row_heavy_smem(SYM, sizeof(Acc));
@@ -61,6 +62,7 @@ cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const B
   const int occ = occupancy(kv, HEAVY_THREADS, hsmem);
   const unsigned grid = grid_for(bins.nrows, 1, L.sms, occ);
   kv<<<grid, HEAVY_THREADS, hsmem, L.s>>>(Ac, Acl, B, C, c_rp, bins.heavy_items, bins.count + BIN_HEAVY, status);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -77,7 +79,8 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
   else
     k_bin_cluster_num<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, (int)sizeof(In),
                                             (int)sizeof(Acc));
-  auto kd = k_cluster_dense<SYM, DT>;
+  note_launches(1);
+  auto kd = k_cluster_group<SYM, DT>;
   static bool attr = false;
   if (!attr) {
     e = allow_smem(kd);
@@ -85,11 +88,15 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
     attr = true;
   }
   for (int b = 0; b < NDB; ++b) {
-    const size_t smem = (size_t)dense_budget(b);
-    const int occ = occupancy(kd, CL_THREADS, smem);
-    const unsigned grid = grid_for(A.ncl, 1, L.sms, occ);
-    kd<<<grid, CL_THREADS, smem, L.s>>>(A, B, C, c_rp, bins.dense_items + (int64_t)b * bins.ncl, bins.count + b,
-                                         bins.nout_rec, bins.uc_rec, L.mode, status);
+    const int gw = group_warps(b), groups = groups_per_cta(b);
+    const int rbytes = warp_class_bytes(b);
+    const size_t smem = (size_t)groups * rbytes;
+    const int threads = groups * gw * 32;
+    const int occ = occupancy(kd, threads, smem);
+    const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
+    kd<<<grid, threads, smem, L.s>>>(A, B, C, c_rp, bins.dense_items + (int64_t)b * bins.ncl, bins.count + b,
+                                      bins.nout_rec, bins.uc_rec, L.mode, rbytes, gw, status);
+    note_launches(1);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -105,9 +112,11 @@ cudaError_t run_rows_phase(const ACsrView& A, const BView& B, const CView& C, in
   if (SYM) {
     const unsigned gb = grid_for(A.nrows, 8, L.sms, 8);
     k_bin_rows_sym<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct);
+    note_launches(1);
   } else {
     const unsigned gb = grid_for(A.nrows, 256, L.sms, 8);
     k_bin_rows_num<<<gb, 256, 0, L.s>>>(A.nrows, c_rp, bins, L.o.load_pct);
+    note_launches(1);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

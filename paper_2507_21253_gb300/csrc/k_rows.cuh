@@ -94,8 +94,69 @@ __device__ __forceinline__ int64_t item_row(const AClusterView& Acl, int64_t ite
 }
 
 // ---------------------------------------------------------------------------
-// Warp-per-row hash kernel (symbolic: count; numeric: accumulate, sort, write)
-// items: int64 row items of one bin; count at ws.bin_count[bin]
+// Rank n distinct keys in ascending order in O(n) expected work: bucket by an
+// interpolated key (monotone in the key), then count the smaller keys inside
+// the key's bucket.  bst, bcur, srt: n ints of scratch.  Warp-collective;
+// rank_of(x) for x in [0, n) is valid after the call, via the returned lambda
+// inputs (bst, bcur, srt).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int interp_bucket(int32_t key, int32_t kmin, int n, uint64_t range) {
+  return (int)(((uint64_t)(uint32_t)(key - kmin) * (uint64_t)n) / range);
+}
+
+struct RankCtx {
+  int32_t kmin;
+  uint64_t range;
+};
+
+__device__ __forceinline__ RankCtx warp_rank_prepare(const int32_t* keys, int n, int32_t* bst, int32_t* bcur,
+                                                     int32_t* srt) {
+  const int lane = lane_id();
+  int32_t kmin = PAD_KEY, kmax = -1;
+  for (int x = lane; x < n; x += 32) {
+    kmin = min(kmin, keys[x]);
+    kmax = max(kmax, keys[x]);
+    bst[x] = 0;
+  }
+  kmin = warp_min(kmin);
+  kmax = warp_max(kmax);
+  const uint64_t range = (uint64_t)((int64_t)kmax - (int64_t)kmin + 1);
+  __syncwarp();
+  for (int x = lane; x < n; x += 32) atomicAdd(&bst[interp_bucket(keys[x], kmin, n, range)], 1);
+  __syncwarp();
+  int carry = 0;
+  for (int x0 = 0; x0 < n; x0 += 32) {
+    const int x = x0 + lane;
+    const int v = x < n ? bst[x] : 0;
+    const int ex = warp_incl_scan(v) - v;
+    if (x < n) {
+      bst[x] = carry + ex;
+      bcur[x] = carry + ex;
+    }
+    carry += __shfl_sync(FULL, ex + v, 31);
+  }
+  __syncwarp();
+  for (int x = lane; x < n; x += 32) srt[atomicAdd(&bcur[interp_bucket(keys[x], kmin, n, range)], 1)] = keys[x];
+  __syncwarp();
+  return RankCtx{kmin, range};
+}
+
+__device__ __forceinline__ int warp_rank_of(int32_t key, int n, const RankCtx& rc, const int32_t* bst,
+                                            const int32_t* bcur, const int32_t* srt) {
+  const int b = interp_bucket(key, rc.kmin, n, rc.range);
+  const int bs = bst[b], be = bcur[b];
+  int r = bs;
+  for (int y = bs; y < be; ++y) r += srt[y] < key;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Warp-per-row hash kernel (symbolic: count; numeric: accumulate, rank, write).
+// The bounds of the B rows of 32 entries of the A row are loaded at once, so
+// the warp has 32 independent loads in flight instead of one B row at a time.
+// items: int64 row items of one bin; count at *count_ptr.
+// Shared memory per warp: keys[T], and for numeric vals[T] plus 3*T ints of
+// ranking scratch.
 // ---------------------------------------------------------------------------
 template <bool SYM, int DT, int SRC>
 __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl, BView B, CView C,
@@ -109,6 +170,7 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
   const int w = threadIdx.x >> 5, lane = lane_id();
   int32_t* keys = (int32_t*)sm + (size_t)w * T;
   Acc* vals = SYM ? nullptr : (Acc*)(sm + (size_t)warps * T * 4) + (size_t)w * T;
+  int32_t* scr = SYM ? nullptr : (int32_t*)(sm + (size_t)warps * T * (4 + sizeof(Acc))) + (size_t)w * 3 * T;
   DevStatus* st = (DevStatus*)status;
   const int32_t count = *count_ptr;
   for (int64_t it = (int64_t)blockIdx.x * warps + w; it < count; it += (int64_t)gridDim.x * warps) {
@@ -126,8 +188,7 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
     __syncwarp();
     int64_t cnt = 0;
     bool full = false;
-    for_row_entries<SRC, DT>(Ac, Acl, item, [&](int32_t k, In a) {
-      const int64_t s = B.rp[k], e = B.rp[k + 1];
+    auto apply = [&](int64_t s, int64_t e, In a) {
       for (int64_t q = s + lane; q < e; q += 32) {
         bool nw;
         const int slot = hash_find_or_insert(keys, log2T, B.col[q], &nw);
@@ -142,7 +203,26 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
         }
       }
       __syncwarp();
-    });
+    };
+    if constexpr (SRC == SRC_CSR) {
+      const int64_t rs = Ac.rp[row], re = Ac.rp[row + 1];
+      for (int64_t pb = rs; pb < re; pb += 32) {
+        const int64_t p = pb + lane;
+        int64_t s = 0, e = 0;
+        In a{};
+        if (p < re) {
+          const int32_t k = Ac.col[p];
+          if (Ac.val) a = ((const In*)Ac.val)[p];
+          s = B.rp[k];
+          e = B.rp[k + 1];
+        }
+        const int n = (int)min64(32, re - pb);
+        for (int i = 0; i < n; ++i)
+          apply(__shfl_sync(FULL, s, i), __shfl_sync(FULL, e, i), __shfl_sync(FULL, a, i));
+      }
+    } else {
+      for_row_entries_cluster<DT>(Acl, item, [&](int32_t k, In a) { apply(B.rp[k], B.rp[k + 1], a); });
+    }
     if (__any_sync(FULL, full)) {
       if (lane == 0) raise(st, DEV_TABLE_FULL, 10, row);
       continue;
@@ -156,14 +236,14 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
         if (lane == 0) raise(st, DEV_INTERNAL, 11, row);
         continue;
       }
-      int P = 1;
-      while (P < n) P <<= 1;
-      for (int i = n + lane; i < P; i += 32) keys[i] = PAD_KEY;
-      __syncwarp();
-      warp_bitonic_sort(keys, vals, P);
-      for (int i = lane; i < n; i += 32) {
-        C.col[out0 + i] = keys[i];
-        ((In*)C.val)[out0 + i] = VT<DT>::out(vals[i]);
+      int32_t* bst = scr;
+      int32_t* bcur = scr + T;
+      int32_t* srt = scr + 2 * T;
+      const RankCtx rc = warp_rank_prepare(keys, n, bst, bcur, srt);
+      for (int x = lane; x < n; x += 32) {
+        const int r = warp_rank_of(keys[x], n, rc, bst, bcur, srt);
+        C.col[out0 + r] = keys[x];
+        ((In*)C.val)[out0 + r] = VT<DT>::out(vals[x]);
       }
     }
     __syncwarp();
@@ -171,7 +251,8 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
 }
 
 inline size_t row_hash_smem(int warps, int log2T, bool sym, int acc_bytes) {
-  return (size_t)warps * ((size_t)4 << log2T) + (sym ? 0 : (size_t)warps * ((size_t)acc_bytes << log2T));
+  return (size_t)warps * ((size_t)4 << log2T) +
+         (sym ? 0 : (size_t)warps * ((size_t)(acc_bytes + 12) << log2T));
 }
 
 // ---------------------------------------------------------------------------

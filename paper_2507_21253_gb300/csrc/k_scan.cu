@@ -62,8 +62,11 @@ cudaError_t inclusive_scan_i64(int64_t* data, int64_t n, int64_t* tmp, cudaStrea
   if (n <= 0) return cudaSuccess;
   const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   k_scan_reduce<<<(unsigned)nb, ST, 0, s>>>(data, n, tmp);
+  note_launches(1);
   k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb);
+  note_launches(1);
   k_scan_apply<<<(unsigned)nb, ST, 0, s>>>(data, n, tmp);
+  note_launches(1);
   return cudaGetLastError();
 }
 

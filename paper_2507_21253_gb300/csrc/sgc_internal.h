@@ -15,6 +15,9 @@ void set_last_error(const std::string& msg);
 
 int num_sms();
 
+// Count of kernels this library has launched (all threads), for reporting.
+void note_launches(int n);
+
 // ---- scan (k_scan.cu): in-place inclusive scan of n int64 values ----------
 constexpr int SCAN_TILE = 2048;  // 256 threads x 8 items
 inline int64_t scan_tmp_elems(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 2; }

@@ -24,7 +24,7 @@ struct AClusterView {
   const uint32_t* mask;
   const int64_t* vptr;
   const void* val;
-  int64_t ncl, nrows;
+  int64_t ncl, nrows, nvals;
   int layout;
 };
 
@@ -43,7 +43,7 @@ struct CView {
 
 // Work bins (k_bins.cuh): NDB dense-kernel budget classes, NRB row-hash table
 // sizes (log2 T = LOG2T_MIN..LOG2T_MAX), one heavy-row list.
-constexpr int NDB = 8;
+constexpr int NDB = 13;  // per-warp shared-memory classes of the cluster kernel
 constexpr int NRB = LOG2T_MAX - LOG2T_MIN + 1;
 constexpr int BIN_HEAVY = NDB + NRB;
 constexpr int NBIN_ALL = NDB + NRB + 1;

@@ -68,6 +68,7 @@ def _sig(name, *args):
 
 _lib.sgc_last_error.restype = ctypes.c_char_p
 _lib.sgc_abi_version.restype = ctypes.c_int
+_lib.sgc_kernel_launches.restype = ctypes.c_longlong
 P = ctypes.POINTER
 _c = {
     "sgc_default_options": _sig("sgc_default_options", P(Options)),
@@ -104,6 +105,11 @@ def _call(name, *args):
 
 def abi_version() -> int:
     return int(_lib.sgc_abi_version())
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(_lib.sgc_kernel_launches())
 
 
 def _stream():
