@@ -157,6 +157,24 @@ int csr_cluster_build_count(const sgc_csr* A, const int32_t* perm, const int64_t
                             int64_t* nucols_host, int64_t* nvals_host, void* ws, size_t ws_bytes,
                             void* stream);
 
+/* csr_cluster_build_count_noalloc: the same counting step as
+ * csr_cluster_build_count, for callers that cannot allocate device memory (an
+ * application whose allocator owns all device memory, a loop that must not
+ * risk an allocation's implicit synchronisation, a tool that accounts for
+ * every byte).  The paper has no counterpart; it is a convenience of this
+ * library.  It takes no workspace: its scratch (about 16 MiB) is one static
+ * device array inside the library, present on every GPU that loads the
+ * library until the process exits.  Inputs above SGC_NOALLOC_MAX_ROWS rows or
+ * clusters are rejected with SGC_INVALID_ARG.  The first call on a device
+ * looks up the array's address (cudaGetSymbolAddress) with that device
+ * current; make it before any stream capture.  All calls share the array
+ * (cleared at the start of each call): calls that overlap on the GPU race and
+ * must be serialised by the caller.  Synchronises; calls no allocator. */
+#define SGC_NOALLOC_MAX_ROWS 4194304
+int csr_cluster_build_count_noalloc(const sgc_csr* A, const int32_t* perm, const int64_t* cluster_ptr,
+                                    int64_t nclusters, int32_t layout, int64_t* ucol_ptr, int64_t* val_ptr,
+                                    int64_t* nucols_host, int64_t* nvals_host, void* stream);
+
 /* csr_cluster_build: fills out->ucol, out->mask and out->val (arrays of
  * out->nucols / out->nucols / out->nvals elements allocated by the caller)
  * from A.  out must carry nrows, ncols, nclusters, nucols, nvals, layout,
