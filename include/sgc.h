@@ -24,9 +24,9 @@
  *  - Output C is CSR in A's ORIGINAL row order, columns sorted within each
  *    row, structural entries whose value cancels to zero kept (the symbolic
  *    structure of Sec. 2.2).  FP32 products are accumulated in FP64 and
- *    rounded once; FP64 accumulates without FMA in ascending k per (i, j),
- *    except rows with more than 3072 outputs (see SGC_HEAVY_ROW_OUTPUTS);
- *    int64 wraps modulo 2^64.
+ *    rounded once; FP64 accumulates in ascending k per (i, j), without FMA
+ *    unless sgc_options.fused_fma = 1, except rows with more than 3072 outputs
+ *    (see SGC_HEAVY_ROW_OUTPUTS); int64 wraps modulo 2^64.
  *  - Errors: SGC_INVALID_ARG (null pointer, negative or inconsistent size),
  *    SGC_UNSUPPORTED (dtype mismatch, cluster larger than 32 rows),
  *    SGC_WORKSPACE_TOO_SMALL, SGC_CUDA_ERROR (a CUDA call failed; the CUDA
@@ -116,7 +116,11 @@ typedef struct sgc_options {
   int32_t stage_elems;      /* B elements per staging buffer, 0 = default (2048 numeric, 4096 symbolic) */
   int32_t max_warps;        /* warps (cluster rows in flight) per CTA, 0 = default 8; 1..8 */
   int32_t load_pct;         /* hash table fill limit in percent, 0 = default 75; 25..90 */
-  int32_t reserved[11];
+  int32_t fused_fma;        /* FP64 values: 1 = accumulate with fused multiply-add (one rounding per
+                               term; within the FP64 bound, not bit-identical to separate rounding);
+                               0 (default) = product and sum rounded separately.  FP32 inputs always
+                               use the fused form: their FP64 products are exact, so it changes nothing. */
+  int32_t reserved[10];
 } sgc_options;
 
 /* Version of this ABI (SGC_ABI_VERSION). */

@@ -38,6 +38,7 @@ ResolvedOptions resolve(const sgc_options* opt) {
   r.load_pct = (opt && opt->load_pct > 0) ? opt->load_pct : 75;
   if (r.load_pct < 25) r.load_pct = 25;
   if (r.load_pct > 90) r.load_pct = 90;
+  r.fused = (opt && opt->fused_fma) ? 1 : 0;
   return r;
 }
 

@@ -69,7 +69,7 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
     int cls = -1;
     if (use_dense && U < (1ll << 28) && T < (1ll << 24)) {
       const int64_t nb = min64(U, B.ncols);
-      const WarpLayout L = warp_layout(true, T, U, 0, table_log2(nb, 75), nb, K, 4, 8, bulk != 0);
+      const WarpLayout L = warp_layout(true, T, U, 0, cluster_table_log2(true, nb), nb, K, 4, 8, bulk != 0);
       cls = warp_class(L.total);
     }
     if (lane == 0) {
@@ -103,7 +103,7 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, 
     if (nout >= 0) {
       const int64_t nva = A.vptr[c + 1] - A.vptr[c];
       const WarpLayout L =
-          warp_layout(false, T, o.uc_rec[c], nva, table_log2(nout, 75), nout, K, in_bytes, acc_bytes, bulk != 0);
+          warp_layout(false, T, o.uc_rec[c], nva, cluster_table_log2(false, nout), nout, K, in_bytes, acc_bytes, bulk != 0);
       cls = warp_class(L.total);
     }
     if (cls >= 0) {

@@ -35,6 +35,16 @@ __host__ __device__ inline int warp_class_bytes(int b) {
   return kb[b] * 1024;
 }
 
+// Hash-table fill limits of the cluster kernel.  The symbolic table is sized by
+// the bound min(U, ncols(B)) on the cluster's output columns, so its real fill
+// is usually far lower; the numeric table is sized by the exact count from the
+// symbolic phase and kept sparse so that most lookups take one probe.
+constexpr int SYM_TABLE_LOAD = 75;
+constexpr int NUM_TABLE_LOAD = 30;
+__host__ __device__ inline int cluster_table_log2(bool sym, int64_t nb) {
+  return table_log2(nb, sym ? SYM_TABLE_LOAD : NUM_TABLE_LOAD);
+}
+
 struct WarpLayout {
   int desc, stage_c, stage_v, stage_a, table, sorted, scratch, acc, flags, total;
 };
@@ -46,7 +56,7 @@ __host__ __device__ inline WarpLayout warp_layout(bool sym, int64_t T, int64_t U
                                                   int K, int in_bytes, int acc_bytes, bool bulk) {
   WarpLayout L{};
   const int64_t pad_c = bulk ? 6 : 0, pad_v = bulk ? (in_bytes == 8 ? 2 : 6) : 0;
-  int64_t o = 128;  // mbarrier, counters, scan partials
+  int64_t o = 256;  // mbarrier, counters, scan partials (group header)
   L.desc = (int)o;
   o += 20 * T;
   o = (o + 15) & ~15ll;
@@ -65,8 +75,8 @@ __host__ __device__ inline WarpLayout warp_layout(bool sym, int64_t T, int64_t U
   L.table = (int)o;
   o += 4ll << LH;
   if (sym) {
-    L.flags = (int)o;  // per-row bitmaps over local ids
-    o += 4ll * K * ((nout + 31) / 32);
+    L.flags = (int)o;  // per-row bitmaps over hash slots
+    o += 4ll * K * (((1ll << LH) + 31) / 32);
   } else {
     L.sorted = (int)o;
     o += 4 * nout;
@@ -145,11 +155,33 @@ __device__ __forceinline__ int group_excl_scan(int v, int gw, int gid, int wg, i
   return base + incl - v;
 }
 
+// Same over 64-bit values (three packed counters per thread); red: 2*gw int64.
+__device__ __forceinline__ uint64_t group_excl_scan64(uint64_t v, int gw, int gid, int wg, uint64_t* red,
+                                                      uint64_t* total) {
+  const int lane = lane_id();
+  const uint64_t incl = warp_incl_scan(v);
+  if (gw == 1) {
+    *total = __shfl_sync(FULL, incl, 31);
+    return incl - v;
+  }
+  if (lane == 31) red[wg] = incl;
+  group_sync(gw, gid);
+  uint64_t base = 0, tot = 0;
+  for (int q = 0; q < gw; ++q) {
+    const uint64_t x = red[q];
+    if (q < wg) base += x;
+    tot += x;
+  }
+  group_sync(gw, gid);
+  *total = tot;
+  return base + incl - v;
+}
+
 template <bool SYM, int DT>
 __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BView B, CView C, int64_t* c_rp_sym,
                                                               const int32_t* items, const int32_t* count_ptr,
                                                               int32_t* nout_rec, const int32_t* uc_rec, int mode,
-                                                              int region_bytes, int gw, void* status) {
+                                                              int region_bytes, int gw, int fused, void* status) {
   using In = typename VT<DT>::In;
   using Acc = typename VT<DT>::Acc;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -158,7 +190,12 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
   const int ngroups = (blockDim.x >> 5) / gw;
   unsigned char* my = sm + (size_t)gid * region_bytes;
   uint64_t* bar = (uint64_t*)my;
-  int* hdr = (int*)(my + 8);  // [0] distinct count, [1..gw] copy flags, [2..gw+1] scan partials (phases apart)
+  // group header: [0,8) mbarrier; [8,72) ints: [0] distinct count, [1..8] copy flags;
+  // [72,104) / [104,136) per-warp key min / max; [136,200) per-warp 64-bit scan partials
+  int* hdr = (int*)(my + 8);
+  int* wmin = (int*)(my + 72);
+  int* wmax = (int*)(my + 104);
+  uint64_t* red64 = (uint64_t*)(my + 136);
   DevStatus* st = (DevStatus*)status;
   const bool bulk = mode == 1;
   if (bulk) {
@@ -179,7 +216,7 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
     const int64_t v0 = A.vptr[c], nva = A.vptr[c + 1] - v0;
     const int64_t U = uc_rec[c];
     const int64_t nb = SYM ? min64(U, B.ncols) : (int64_t)nout_rec[c];  // bound / exact output columns
-    const int LH = table_log2(nb, 75);
+    const int LH = cluster_table_log2(SYM, nb);
     const WarpLayout Ly = warp_layout(SYM, T, U, SYM ? 0 : nva, LH, nb, K, sizeof(In), sizeof(Acc), bulk);
     WDesc d;
     d.off_c = (int32_t*)(my + Ly.desc);
@@ -225,11 +262,12 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
           wv = SYM ? 0 : len;
         }
       }
-      int tc, tv = 0, ta;
-      const int oc = group_excl_scan(wc, gw, gid, wg, hdr + 2, &tc);
-      const int ov = SYM ? 0 : group_excl_scan(wv, gw, gid, wg, hdr + 2, &tv);
-      const int pa = __popc(m);
-      const int oa = group_excl_scan(pa, gw, gid, wg, hdr + 2, &ta);
+      // one scan of three packed counters: col window (21 bits), val window (21 bits), mask bits
+      uint64_t tot;
+      const uint64_t ex = group_excl_scan64((uint64_t)wc | ((uint64_t)wv << 21) | ((uint64_t)__popc(m) << 42), gw,
+                                            gid, wg, red64, &tot);
+      const int oc = (int)(ex & 0x1fffff), ov = (int)((ex >> 21) & 0x1fffff), oa = (int)(ex >> 42);
+      const int tc = (int)(tot & 0x1fffff), tv = (int)((tot >> 21) & 0x1fffff), ta = (int)(tot >> 42);
       if (i < T) {
         d.off_c[i] = (int32_t)(run_c + oc + shc) | (ldg ? (int32_t)0x80000000 : 0);
         d.off_v[i] = (int32_t)(run_v + ov + shv);
@@ -301,84 +339,152 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
     }
     group_sync(gw, gid);
 
-    // ---- 2. map staged column ids to slots ---------------------------------
-    bool full = false;
-    int newk = 0;
-    for (int64_t i = wg; i < T; i += gw) {
-      const int n = d.len[i];
-      const int dc = d.off_c[i] & 0x7fffffff;
-      for (int q = lane; q < n; q += 32) {
-        bool nwk;
-        const int slot = hash_find_or_insert(table, LH, stage_c[dc + q], &nwk);
-        if (slot < 0) {
-          full = true;
-          continue;
+    if constexpr (SYM) {
+      // ---- 2s/3s. map and per-row bitmaps in one pass, in Algorithm 1 order:
+      // for each union column t (split over the group's warps), each lane takes
+      // one entry j of B row t, finds j's slot in the cluster table and sets
+      // bit `slot` in the bitmap of every row l that has a_lt.
+      const int WPR = TH / 32;
+      uint32_t* rb = (uint32_t*)(my + Ly.flags);
+      for (int x = gt; x < K * WPR; x += GT) rb[x] = 0;
+      group_sync(gw, gid);
+      bool full = false;
+      int newk = 0;
+      for (int64_t i = wg; i < T; i += gw) {
+        const uint32_t m = d.mask[i];
+        const int n = d.len[i];
+        const int dc = d.off_c[i] & 0x7fffffff;
+        for (int q = lane; q < n; q += 32) {
+          bool nwk;
+          const int slot = hash_find_or_insert(table, LH, stage_c[dc + q], &nwk);
+          if (slot < 0) {
+            full = true;
+            continue;
+          }
+          newk += nwk;
+          const uint32_t bit = 1u << (slot & 31);
+          uint32_t* w0 = rb + (slot >> 5);
+          uint32_t mm = m;
+          while (mm) {
+            const int l = __ffs(mm) - 1;
+            mm &= mm - 1;
+            atomicOr(w0 + (size_t)l * WPR, bit);
+          }
         }
-        newk += nwk;
-        stage_c[dc + q] = slot;
       }
-    }
-    newk = warp_sum(newk);
-    if (lane == 0 && newk) atomicAdd(&hdr[0], newk);
-    if (__any_sync(FULL, full) && lane == 0) raise(st, DEV_TABLE_FULL, 31, c);
-    group_sync(gw, gid);
-    const int n_out = hdr[0];
-    // ---- 2b. local ids: compaction order (symbolic) or rank in column order (numeric)
-    if (wg == 0) {
-      if constexpr (SYM) {
-        int base = 0;
-        for (int x0 = 0; x0 < TH; x0 += 32) {
-          const int x = x0 + lane;
-          const bool occ = table[x] != EMPTY_KEY;
-          const unsigned bal = __ballot_sync(FULL, occ);
-          if (occ) table[x] = base + __popc(bal & lt);
-          base += __popc(bal);
+      newk = warp_sum(newk);
+      if (lane == 0 && newk) atomicAdd(&hdr[0], newk);
+      if (__any_sync(FULL, full) && lane == 0) raise(st, DEV_TABLE_FULL, 31, c);
+      group_sync(gw, gid);
+      for (int l = wg; l < K; l += gw) {
+        int cc = 0;
+        for (int x = lane; x < WPR; x += 32) cc += __popc(rb[(size_t)l * WPR + x]);
+        cc = warp_sum(cc);
+        if (lane == 0) c_rp_sym[A.perm[p0 + l] + 1] = cc;
+      }
+      if (gt == 0) nout_rec[c] = hdr[0];
+    } else {
+      // ---- 2. map staged column ids to slots ---------------------------------
+      bool full = false;
+      int newk = 0;
+      for (int64_t i = wg; i < T; i += gw) {
+        const int n = d.len[i];
+        const int dc = d.off_c[i] & 0x7fffffff;
+        for (int q = lane; q < n; q += 32) {
+          bool nwk;
+          const int slot = hash_find_or_insert(table, LH, stage_c[dc + q], &nwk);
+          if (slot < 0) {
+            full = true;
+            continue;
+          }
+          newk += nwk;
+          stage_c[dc + q] = slot;
         }
-      } else if (n_out == nb) {
-        int32_t* srt = (int32_t*)(my + Ly.sorted);
-        int32_t* bst = (int32_t*)(my + Ly.scratch);
-        int32_t* bcur = bst + nb;
-        int32_t* bkey = bcur + nb;
-        int32_t* kslot = bkey + nb;
-        int32_t kmin = PAD_KEY, kmax = -1;
-        int base = 0;
-        for (int x0 = 0; x0 < TH; x0 += 32) {
+      }
+      newk = warp_sum(newk);
+      if (lane == 0 && newk) atomicAdd(&hdr[0], newk);
+      if (__any_sync(FULL, full) && lane == 0) raise(st, DEV_TABLE_FULL, 31, c);
+      group_sync(gw, gid);
+      const int n_out = hdr[0];
+      if (n_out != nb) {
+        if (gt == 0) raise(st, DEV_INTERNAL, 32, c);
+        group_sync(gw, gid);
+        continue;
+      }
+      // ---- 2b. rank the output columns in column order (group-parallel):
+      // compact the occupied slots, bucket the keys by an interpolated key
+      // (monotone in the key), scan the bucket counts, count smaller keys
+      // within a bucket.  table[slot] becomes the rank; srt[rank] the key.
+      int32_t* srt = (int32_t*)(my + Ly.sorted);
+      int32_t* bst = (int32_t*)(my + Ly.scratch);
+      int32_t* bcur = bst + nb;
+      int32_t* bkey = bcur + nb;
+      int32_t* kslot = bkey + nb;
+      {
+        // compaction: warp wg owns slots [s0, s1)
+        const int per = (TH + gw - 1) / gw;
+        const int s0 = min(wg * per, TH), s1 = min(s0 + per, TH);
+        int mine = 0;
+        for (int x0 = s0; x0 < s1; x0 += 32) {
           const int x = x0 + lane;
+          mine += __popc(__ballot_sync(FULL, x < s1 && table[x] != EMPTY_KEY));
+        }
+        int32_t kmin = PAD_KEY, kmax = -1;
+        for (int x = gt; x < TH; x += GT) {
           const int32_t key = table[x];
+          if (key != EMPTY_KEY) {
+            kmin = min(kmin, key);
+            kmax = max(kmax, key);
+          }
+        }
+        kmin = warp_min(kmin);
+        kmax = warp_max(kmax);
+        if (lane == 0) {
+          red64[wg] = (uint64_t)mine;
+          wmin[wg] = kmin;
+          wmax[wg] = kmax;
+        }
+        group_sync(gw, gid);
+        int base = 0;
+        for (int q = 0; q < gw; ++q) {
+          if (q < wg) base += (int)red64[q];
+          kmin = min(kmin, wmin[q]);
+          kmax = max(kmax, wmax[q]);
+        }
+        for (int x0 = s0; x0 < s1; x0 += 32) {
+          const int x = x0 + lane;
+          const int32_t key = x < s1 ? table[x] : EMPTY_KEY;
           const bool occ = key != EMPTY_KEY;
           const unsigned bal = __ballot_sync(FULL, occ);
           if (occ) {
             const int pos = base + __popc(bal & lt);
             bkey[pos] = key;
             kslot[pos] = x;
-            kmin = min(kmin, key);
-            kmax = max(kmax, key);
           }
           base += __popc(bal);
         }
-        kmin = warp_min(kmin);
-        kmax = warp_max(kmax);
+        for (int x = gt; x < n_out; x += GT) bst[x] = 0;
+        group_sync(gw, gid);
         const uint64_t range = (uint64_t)((int64_t)kmax - (int64_t)kmin + 1);
-        for (int x = lane; x < n_out; x += 32) bst[x] = 0;
-        __syncwarp();
-        for (int x = lane; x < n_out; x += 32) atomicAdd(&bst[bucket_of(bkey[x], kmin, n_out, range)], 1);
-        __syncwarp();
+        for (int x = gt; x < n_out; x += GT) atomicAdd(&bst[bucket_of(bkey[x], kmin, n_out, range)], 1);
+        group_sync(gw, gid);
         int carry = 0;
-        for (int x0 = 0; x0 < n_out; x0 += 32) {
-          const int x = x0 + lane;
+        for (int x0 = 0; x0 < n_out; x0 += GT) {
+          const int x = x0 + gt;
           const int v = x < n_out ? bst[x] : 0;
-          const int ex = warp_incl_scan(v) - v;
+          uint64_t tot;
+          const int ex = (int)group_excl_scan64((uint64_t)v, gw, gid, wg, red64, &tot);
           if (x < n_out) {
             bst[x] = carry + ex;  // bucket start
             bcur[x] = carry + ex;
           }
-          carry += __shfl_sync(FULL, ex + v, 31);
+          carry += (int)tot;
         }
-        __syncwarp();
-        for (int x = lane; x < n_out; x += 32)
+        group_sync(gw, gid);
+        for (int x = gt; x < n_out; x += GT)
           srt[atomicAdd(&bcur[bucket_of(bkey[x], kmin, n_out, range)], 1)] = bkey[x];
-        __syncwarp();
-        for (int x = lane; x < n_out; x += 32) {
+        group_sync(gw, gid);
+        for (int x = gt; x < n_out; x += GT) {
           const int32_t key = bkey[x];
           const int b = bucket_of(key, kmin, n_out, range);
           const int bs = bst[b], be = bcur[b];
@@ -386,53 +492,15 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
           for (int y = bs; y < be; ++y) r += srt[y] < key;
           table[kslot[x]] = r;  // slot -> rank
         }
-        __syncwarp();
-        for (int x = lane; x < n_out; x += 32) srt[table[kslot[x]]] = bkey[x];  // sorted keys
+        group_sync(gw, gid);
+        for (int x = gt; x < n_out; x += GT) srt[table[kslot[x]]] = bkey[x];  // sorted keys
       }
-    }
-    group_sync(gw, gid);
-    if (!SYM && n_out != nb) {
-      if (gt == 0) raise(st, DEV_INTERNAL, 32, c);
-      group_sync(gw, gid);
-      continue;
-    }
-    // rewrite staged ids: slot -> local id
-    for (int64_t i = wg; i < T; i += gw) {
-      const int n = d.len[i];
-      const int dc = d.off_c[i] & 0x7fffffff;
-      for (int q = lane; q < n; q += 32) stage_c[dc + q] = table[stage_c[dc + q]];
-    }
-    if constexpr (SYM) {
-      const int WPR = (n_out + 31) / 32;
-      uint32_t* rb = (uint32_t*)(my + Ly.flags);
-      for (int x = gt; x < K * WPR; x += GT) rb[x] = 0;
-      group_sync(gw, gid);
-      // ---- 3s. per-row bitmaps over local ids: warp per row, own columns only
-      for (int l = wg; l < K; l += gw) {
-        uint32_t* mine = rb + (size_t)l * WPR;
-        for (int64_t tb = 0; tb < T; tb += 32) {
-          const uint32_t mm = tb + lane < T ? d.mask[tb + lane] : 0u;
-          unsigned bits = __ballot_sync(FULL, (mm >> l) & 1u);
-          while (bits) {
-            const int64_t i = tb + __ffs(bits) - 1;
-            bits &= bits - 1;
-            const int n = d.len[i];
-            const int dc = d.off_c[i] & 0x7fffffff;
-            for (int q = lane; q < n; q += 32) {
-              const int lid = stage_c[dc + q];
-              atomicOr(&mine[lid >> 5], 1u << (lid & 31));
-            }
-          }
-        }
-        __syncwarp();
-        int cc = 0;
-        for (int x = lane; x < WPR; x += 32) cc += __popc(mine[x]);
-        cc = warp_sum(cc);
-        if (lane == 0) c_rp_sym[A.perm[p0 + l] + 1] = cc;
+      // rewrite staged ids: slot -> rank
+      for (int64_t i = wg; i < T; i += gw) {
+        const int n = d.len[i];
+        const int dc = d.off_c[i] & 0x7fffffff;
+        for (int q = lane; q < n; q += 32) stage_c[dc + q] = table[stage_c[dc + q]];
       }
-      if (gt == 0) nout_rec[c] = n_out;
-    } else {
-      const int32_t* srt = (const int32_t*)(my + Ly.sorted);
       Acc* acc = (Acc*)(my + Ly.acc);
       uint8_t* flg = (uint8_t*)(my + Ly.flags);
       for (int64_t x = gt; x < (int64_t)K * n_out; x += GT) {
@@ -458,10 +526,18 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
             const int n = d.len[i];
             const int dc = d.off_c[i] & 0x7fffffff, dv = d.off_v[i];
             const In a = padded ? av[i * K + l] : av[d.aoff[i] + __popc(m & below)];
-            for (int q = lane; q < n; q += 32) {
-              const int lid = stage_c[dc + q];
-              al[lid] = VT<DT>::add(al[lid], VT<DT>::mul(a, stage_v[dv + q]));
-              fl[lid] = 1;
+            if (fused) {
+              for (int q = lane; q < n; q += 32) {
+                const int lid = stage_c[dc + q];
+                al[lid] = VT<DT>::madd(al[lid], a, stage_v[dv + q], true);
+                fl[lid] = 1;
+              }
+            } else {
+              for (int q = lane; q < n; q += 32) {
+                const int lid = stage_c[dc + q];
+                al[lid] = VT<DT>::madd(al[lid], a, stage_v[dv + q], false);
+                fl[lid] = 1;
+              }
             }
             __syncwarp();
           }

@@ -49,7 +49,7 @@ cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const B
     const unsigned grid = grid_for(bins.nrows, warps, L.sms, occ);
     const int b = lg - LOG2T_MIN;
     kh<<<grid, warps * 32, smem, L.s>>>(Ac, Acl, B, C, c_rp, bins.row_items + (int64_t)b * bins.nrows,
-                                         bins.count + NDB + b, lg, status);
+                                         bins.count + NDB + b, lg, L.o.fused, status);
     note_launches(1);
   }
   auto kv = k_row_heavy<SYM, DT, SRC>;
@@ -95,7 +95,7 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
     const int occ = occupancy(kd, threads, smem);
     const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
     kd<<<grid, threads, smem, L.s>>>(A, B, C, c_rp, bins.dense_items + (int64_t)b * bins.ncl, bins.count + b,
-                                      bins.nout_rec, bins.uc_rec, L.mode, rbytes, gw, status);
+                                      bins.nout_rec, bins.uc_rec, L.mode, rbytes, gw, L.o.fused, status);
     note_launches(1);
   }
   e = cudaGetLastError();

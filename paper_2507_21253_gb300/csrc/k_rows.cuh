@@ -161,7 +161,7 @@ __device__ __forceinline__ int warp_rank_of(int32_t key, int n, const RankCtx& r
 template <bool SYM, int DT, int SRC>
 __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl, BView B, CView C,
                                                   int64_t* c_rp_sym, const int64_t* items,
-                                                  const int32_t* count_ptr, int log2T, void* status) {
+                                                  const int32_t* count_ptr, int log2T, int fused, void* status) {
   using In = typename VT<DT>::In;
   using Acc = typename VT<DT>::Acc;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
         if constexpr (SYM) {
           cnt += nw;
         } else {
-          vals[slot] = VT<DT>::add(vals[slot], VT<DT>::mul(a, ((const In*)B.val)[q]));
+          vals[slot] = VT<DT>::madd(vals[slot], a, ((const In*)B.val)[q], fused != 0);
         }
       }
       __syncwarp();

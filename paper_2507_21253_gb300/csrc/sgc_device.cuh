@@ -49,6 +49,8 @@ template <> struct VT<SGC_F32> {
   __device__ static __forceinline__ Acc add(Acc x, Acc y) { return __dadd_rn(x, y); }
   __device__ static __forceinline__ In out(Acc x) { return __double2float_rn(x); }
   __device__ static __forceinline__ void atomic_add(Acc* p, Acc v) { atomicAdd(p, v); }
+  // the FP64 product of two FP32 values is exact, so the fused form rounds once, like mul + add
+  __device__ static __forceinline__ Acc madd(Acc acc, In a, In b, bool) { return __fma_rn((double)a, (double)b, acc); }
 };
 template <> struct VT<SGC_F64> {
   using In = double;
@@ -57,6 +59,10 @@ template <> struct VT<SGC_F64> {
   __device__ static __forceinline__ Acc add(Acc x, Acc y) { return __dadd_rn(x, y); }
   __device__ static __forceinline__ In out(Acc x) { return x; }
   __device__ static __forceinline__ void atomic_add(Acc* p, Acc v) { atomicAdd(p, v); }
+  // fused: one rounding of a*b + acc; otherwise the product and the sum are rounded separately
+  __device__ static __forceinline__ Acc madd(Acc acc, In a, In b, bool fused) {
+    return fused ? __fma_rn(a, b, acc) : __dadd_rn(acc, __dmul_rn(a, b));
+  }
 };
 template <> struct VT<SGC_I64> {
   using In = long long;
@@ -65,6 +71,7 @@ template <> struct VT<SGC_I64> {
   __device__ static __forceinline__ Acc add(Acc x, Acc y) { return x + y; }
   __device__ static __forceinline__ In out(Acc x) { return (In)x; }
   __device__ static __forceinline__ void atomic_add(Acc* p, Acc v) { atomicAdd(p, v); }
+  __device__ static __forceinline__ Acc madd(Acc acc, In a, In b, bool) { return acc + (Acc)a * (Acc)b; }
 };
 
 // ---------------------------------------------------------------------------

@@ -54,6 +54,7 @@ struct ResolvedOptions {
   int stage_elems_sym;
   int max_warps;
   int load_pct;
+  int fused;
 };
 ResolvedOptions resolve(const sgc_options* opt);
 

@@ -170,3 +170,21 @@ def test_workspace_too_small(sgc):
     with pytest.raises(sgc.SgcError) as ei:
         sgc.spgemm_rowwise_symbolic(Ad, Ad, ws)
     assert ei.value.code == sgc.SGC_WORKSPACE_TOO_SMALL
+
+
+@pytest.mark.parametrize("name,A", [c for c in CASES if c[0] in ("laplacian64", "rand_f64", "rand_f32",
+                                                               "rmat12_f32", "powerlaw", "stencil14")],
+                         ids=["laplacian64", "rand_f64", "rand_f32", "rmat12_f32", "powerlaw", "stencil14"])
+def test_fused_fma_mode(sgc, name, A):
+    """fused_fma = 1: FP64 within the tolerance; FP32 identical to the unfused mode
+    (the FP64 product of two FP32 values is exact)."""
+    Ad = dev(sgc, A)
+    perm, cptr = synth.random_clusters(A.nrows, 5, kmax=8)
+    Acl = sgc.csr_cluster_build(Ad, perm, cptr)
+    Cf = sgc.spgemm(Acl, Ad, sgc.options(fused_fma=1))
+    compare(Cf, A, A)
+    Rf = sgc.spgemm_rowwise(Ad, Ad, sgc.options(fused_fma=1))
+    compare(Rf, A, A)
+    if A.val.dtype == np.float32:
+        Cu = sgc.spgemm(Acl, Ad, sgc.options(fused_fma=0))
+        assert np.array_equal(Cf.val.cpu().numpy(), Cu.val.cpu().numpy())
