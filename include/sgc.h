@@ -263,6 +263,76 @@ int hcluster_candidates(const sgc_csr* A, float jacc_th, int32_t topk, int32_t* 
 int hcluster_reorder(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm, int64_t* cluster_ptr,
                      int64_t* nclusters_host, void* ws, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned per-cluster output-column predictor and the symbolic-free path.
+ * The paper has no predictor (its future work names learned choices, Sec. 5);
+ * this library predicts, per cluster, n_out = the number of distinct output
+ * columns of the cluster's rows (the cluster's nonzeros in CSR_Cluster form of
+ * C) with an FP32 MLP 8 -> 32 -> 32 -> 1 (ReLU), target log1p(n_out).
+ *
+ * cluster_features: 8 FP32 features per cluster (row-major nclusters x 8):
+ *   K/32, log1p(T)/8, log1p(nnz of the rows)/8, log1p(U)/8,
+ *   log1p(sum of row flop bounds)/8, log1p(max row flop bound)/8,
+ *   log1p(ncols(B))/16, (last - first union column + 1)/ncols(B);
+ *   T = union columns, U = sum of nnz(B_t) over them, row flop bound
+ *   ub_l = sum of nnz(B_t) over the row's columns.  Asynchronous.
+ * nnz_predictor_targets: y[c] = log1p(n_out) for the clusters the symbolic
+ *   phase handled in the cluster kernel, -1 for the others (ignored by
+ *   training); ws must be the workspace of a completed spgemm_symbolic.
+ * Parameters: 1377 FP32 values W1[32][8], b1[32], W2[32][32], b2[32], w3[32], b3.
+ * nnz_predictor_train: `steps` Adam steps (beta 0.9/0.999, eps 1e-8, rate lr)
+ *   from `init`, batch `batch` (<= 256) samples order[s*batch .. +batch) at
+ *   step s, loss = mean over valid samples (y >= 0) of (yhat - y)^2 / 2; one
+ *   CTA, fixed summation order (deterministic).  loss_out: per step (nullable).
+ * nnz_predictor_grad: the loss and gradient of one batch (samples idx[0..batch)).
+ * nnz_predictor_infer: yhat for n samples.
+ *
+ * spgemm_learned_*: C = A*B without the exact symbolic pass.
+ *   plan: features -> MLP (or the caller's per-cluster capacities) -> per
+ *     cluster n_cap = min(min(U, ncols(B)), max(1, ceil(margin * scale *
+ *     max(expm1(yhat), 0)))) (FP32) -> per row slab capacity min(h_l, n_cap),
+ *     h_l = min(ub_l, ncols(B)); returns the slab size (elements) in
+ *     *slab_elems_host.  Synchronises.
+ *   phase1: one cluster-wise pass computes every cluster whose n_out <= n_cap
+ *     into the caller's slab (slab_col int32, slab_val of A's dtype, slab_elems
+ *     each) and writes its row counts; a cluster with more output columns
+ *     (an under-prediction) is flagged and its rows go through the exact
+ *     symbolic pass; c_row_ptr (nrows+1) is C's row pointer;
+ *     *c_nnz_host = nnz(C), *n_overflow_host = clusters sent to the exact path.
+ *     Synchronises.
+ *   phase2: copies slab rows into C and runs the exact numeric pass on the
+ *     flagged clusters.  C (allocated by the caller with nnz(C)) equals the
+ *     result of spgemm_symbolic + spgemm_numeric exactly.  Asynchronous.
+ *   All three take the same workspace (spgemm_learned_workspace_size).
+ * ------------------------------------------------------------------------- */
+#define SGC_NNZ_PREDICTOR_PARAMS 1377
+typedef struct sgc_predictor {
+  const float* params;   /* device, SGC_NNZ_PREDICTOR_PARAMS FP32 values (ignored if ncap is set) */
+  float margin;          /* capacity margin over the prediction (e.g. 1.25) */
+  float scale;           /* multiplies the prediction (1 = as predicted) */
+  const int32_t* ncap;   /* optional device array of nclusters capacities used instead of the MLP */
+} sgc_predictor;
+
+int cluster_features(const sgc_csr_cluster* A, const sgc_csr* B, float* features, void* stream);
+int nnz_predictor_targets(const sgc_csr_cluster* A, const sgc_csr* B, const void* ws, size_t ws_bytes, float* y,
+                          void* stream);
+int nnz_predictor_infer(const float* params, const float* features, int64_t n, float* yhat, void* stream);
+int nnz_predictor_grad(const float* params, const float* features, const float* y, const int32_t* idx,
+                       int32_t batch, float* grad, float* loss, void* stream);
+int nnz_predictor_train(const float* features, const float* y, int64_t n, const int32_t* order, int64_t steps,
+                        int32_t batch, float lr, const float* init, float* params_out, float* loss_out,
+                        void* stream);
+int spgemm_learned_workspace_size(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_options* opt,
+                                  size_t* bytes);
+int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_predictor* pred,
+                        int64_t* slab_elems_host, void* ws, size_t ws_bytes, const sgc_options* opt, void* stream);
+int spgemm_learned_phase1(const sgc_csr_cluster* A, const sgc_csr* B, int32_t* slab_col, void* slab_val,
+                          int64_t* c_row_ptr, int64_t* c_nnz_host, int64_t* n_overflow_host, void* ws,
+                          size_t ws_bytes, const sgc_options* opt, void* stream);
+int spgemm_learned_phase2(const sgc_csr_cluster* A, const sgc_csr* B, const int32_t* slab_col,
+                          const void* slab_val, sgc_csr* C, void* ws, size_t ws_bytes, const sgc_options* opt,
+                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

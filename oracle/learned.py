@@ -15,12 +15,20 @@ with bit l of len_B(ucol_t), the row's flop upper bound):
   x5 = log1p(max_l ub_l) / 8         largest row flop bound
   x6 = log1p(ncols_B) / 16
   x7 = (ucol_last - ucol_first + 1) / ncols_B   column span (0 if empty)
-Target: log1p(sum_l nnz(C_l)).  Loss: mean over the batch of (yhat - y)^2 / 2.
+Target: log1p(n_out), n_out = |union over the cluster's rows l of cols(C_l)|,
+the cluster's output-column count (its nonzeros in CSR_Cluster form of C).
+Loss: mean over the batch of (yhat - y)^2 / 2.
 Parameters, flat: W1[32][8], b1[32], W2[32][32], b2[32], w3[32], b3 (1377).
+
+Use (all in FP32): P = max(expm1(yhat), 0) * scale;
+n_cap = min(min(U, ncols_B), max(1, ceil(margin * P))) with U the staged B
+elements (a bound on n_out); each row's slab capacity is min(h_l, n_cap) with
+h_l = min(ub_l, ncols_B).  A cluster overflows iff n_out > n_cap (then every
+row fits: nnz(C_l) <= n_out).
 
 Pinned in tests/test_oracle_learned.py: the gradient by central finite
 differences, the first Adam step by its closed form, features by hand-counted
-clusters, the overflow rule by brute force.
+clusters, the capacity rule by hand, the overflow rule by brute force.
 """
 from __future__ import annotations
 
@@ -127,31 +135,28 @@ def adam_step(p, m, v, g, t: int, lr: float):
     return p - lr * mhat / (np.sqrt(vhat) + ADAM_EPS), m, v
 
 
-def row_capacity_f32(yhat: np.ndarray, row_ub: np.ndarray, row_h: np.ndarray,
-                     cluster_ptr: np.ndarray, margin: float, scale: float) -> np.ndarray:
-    """Per-row capacity from a cluster prediction, every step in FP32:
-    P = max(expm1(yhat), 0) * scale; e_l = P * ub_l / sum(ub); cap_l = min(h_l, max(1, ceil(margin * e_l))).
-    (h_l = min(ub_l, ncols_B) is the exact bound on the row's output.)  Rows with
-    ub_l = 0 get 0."""
+def cluster_capacity_f32(yhat: np.ndarray, U: np.ndarray, ncols_b: int, margin: float, scale: float) -> np.ndarray:
+    """n_cap per cluster: min(min(U, ncols_B), max(1, ceil(margin * max(expm1(yhat), 0) * scale))), in FP32."""
     f = np.float32
-    caps = np.zeros(row_ub.size, dtype=np.int64)
-    for c in range(cluster_ptr.size - 1):
-        s, e = int(cluster_ptr[c]), int(cluster_ptr[c + 1])
-        tot = f(row_ub[s:e].sum())
+    out = np.zeros(yhat.size, dtype=np.int64)
+    for c in range(yhat.size):
         P = f(max(f(np.expm1(f(yhat[c]))), f(0.0))) * f(scale)
-        for q in range(s, e):
-            if row_ub[q] == 0:
-                continue
-            est = f(f(P * f(row_ub[q])) / tot)
-            want = int(np.ceil(f(f(margin) * est)))
-            caps[q] = min(int(row_h[q]), max(1, want))
-    return caps
-
-
-def overflowing_clusters(row_count: np.ndarray, caps: np.ndarray, cluster_ptr: np.ndarray) -> np.ndarray:
-    """Cluster c overflows iff some row's exact output count exceeds its capacity."""
-    out = np.zeros(cluster_ptr.size - 1, dtype=bool)
-    for c in range(cluster_ptr.size - 1):
-        s, e = int(cluster_ptr[c]), int(cluster_ptr[c + 1])
-        out[c] = bool(np.any(row_count[s:e] > caps[s:e]))
+        want = int(np.ceil(f(f(margin) * P)))
+        out[c] = min(int(min(int(U[c]), ncols_b)), max(1, want))
     return out
+
+
+def union_counts(cc: dict, C_rows: list) -> np.ndarray:
+    """n_out per cluster from the rows of C (list over ORIGINAL rows of column arrays)."""
+    out = np.zeros(cc["nclusters"], dtype=np.int64)
+    for c in range(cc["nclusters"]):
+        cols = set()
+        for p in range(int(cc["cluster_ptr"][c]), int(cc["cluster_ptr"][c + 1])):
+            cols.update(int(x) for x in C_rows[int(cc["perm"][p])])
+        out[c] = len(cols)
+    return out
+
+
+def overflowing_clusters(n_out: np.ndarray, n_cap: np.ndarray) -> np.ndarray:
+    """Cluster c overflows iff its output-column count exceeds its capacity."""
+    return np.asarray(n_out) > np.asarray(n_cap)

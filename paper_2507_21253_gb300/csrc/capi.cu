@@ -528,4 +528,193 @@ int hcluster_reorder(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32
   return SGC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Learned predictor and the symbolic-free path
+// ---------------------------------------------------------------------------
+namespace {
+struct LwWs {
+  SpWs sp;
+  BinOut lb;
+  float* X;
+  float* yhat;
+  int32_t *ncap, *flag, *flist, *flist_count, *flist_plan, *h_pos;
+  int64_t* slab_off;
+  size_t bytes;
+};
+LwWs carve_lw(void* base, size_t cap, int64_t nrows, int64_t ncl) {
+  LwWs w{};
+  w.sp = carve_sp(base, cap, nrows, ncl);
+  Carver cv(base, cap);
+  cv.off = w.sp.bytes;
+  w.lb.count = cv.take<int32_t>(NBIN_ALL);
+  w.lb.dense_items = cv.take<int32_t>((int64_t)NDB * ncl);
+  w.lb.ncl = ncl;
+  w.lb.nrows = nrows;
+  w.lb.uc_rec = w.sp.bins.uc_rec;
+  w.X = cv.take<float>(ncl * 8);
+  w.yhat = cv.take<float>(ncl);
+  w.ncap = cv.take<int32_t>(ncl);
+  w.flag = cv.take<int32_t>(ncl);
+  w.flist = cv.take<int32_t>(ncl);
+  w.flist_count = cv.take<int32_t>(1);
+  w.flist_plan = cv.take<int32_t>(1);
+  w.h_pos = cv.take<int32_t>(nrows);
+  w.slab_off = cv.take<int64_t>(nrows + 1);
+  w.bytes = cv.off + 256;
+  return w;
+}
+}  // namespace
+
+int cluster_features(const sgc_csr_cluster* A, const sgc_csr* B, float* features, void* stream) {
+  int rc = check_product(A, B, false);
+  if (rc) return rc;
+  if (A->nclusters > 0 && !features) SGC_FAIL(SGC_INVALID_ARG, "features is NULL");
+  SGC_CUDA(features_run(cview(A, false), bview(B, false), features, nullptr, nullptr, num_sms(),
+                        (cudaStream_t)stream));
+  return SGC_OK;
+}
+
+int nnz_predictor_targets(const sgc_csr_cluster* A, const sgc_csr* B, const void* ws, size_t ws_bytes, float* y,
+                          void* stream) {
+  int rc = check_product(A, B, false);
+  if (rc) return rc;
+  SpWs w = carve_sp((void*)ws, ws_bytes, A->nrows, A->nclusters);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "not a symbolic workspace of this A");
+  if (A->nclusters > 0 && !y) SGC_FAIL(SGC_INVALID_ARG, "y is NULL");
+  SGC_CUDA(targets_run(w.bins.nout_rec, A->nclusters, y, num_sms(), (cudaStream_t)stream));
+  return SGC_OK;
+}
+
+int nnz_predictor_infer(const float* params, const float* features, int64_t n, float* yhat, void* stream) {
+  if (n < 0 || (n > 0 && (!params || !features || !yhat))) SGC_FAIL(SGC_INVALID_ARG, "bad arguments");
+  SGC_CUDA(mlp_infer_run(params, features, n, yhat, num_sms(), (cudaStream_t)stream));
+  return SGC_OK;
+}
+
+int nnz_predictor_grad(const float* params, const float* features, const float* y, const int32_t* idx,
+                       int32_t batch, float* grad, float* loss, void* stream) {
+  if (batch < 32 || batch > 256 || batch % 32 || !params || !features || !y || !idx || !grad)
+    SGC_FAIL(SGC_INVALID_ARG, "batch must be a multiple of 32 in 32..256; NULL pointer");
+  SGC_CUDA(mlp_train_run(features, y, idx, 1, batch, 0.0f, params, nullptr, loss, 1, grad, (cudaStream_t)stream));
+  return SGC_OK;
+}
+
+int nnz_predictor_train(const float* features, const float* y, int64_t n, const int32_t* order, int64_t steps,
+                        int32_t batch, float lr, const float* init, float* params_out, float* loss_out,
+                        void* stream) {
+  if (batch < 32 || batch > 256 || batch % 32) SGC_FAIL(SGC_INVALID_ARG, "batch must be a multiple of 32 in 32..256");
+  if (n <= 0 || steps < 0 || !features || !y || !order || !init || !params_out)
+    SGC_FAIL(SGC_INVALID_ARG, "bad arguments");
+  SGC_CUDA(mlp_train_run(features, y, order, steps, batch, lr, init, params_out, loss_out, 0, nullptr,
+                         (cudaStream_t)stream));
+  return SGC_OK;
+}
+
+int spgemm_learned_workspace_size(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_options* opt,
+                                  size_t* bytes) {
+  (void)opt;
+  if (!A || !B || !bytes) SGC_FAIL(SGC_INVALID_ARG, "NULL argument");
+  *bytes = carve_lw(nullptr, 0, A->nrows, A->nclusters).bytes;
+  return SGC_OK;
+}
+
+int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_predictor* pred,
+                        int64_t* slab_elems_host, void* ws, size_t ws_bytes, const sgc_options* opt, void* stream) {
+  int rc = check_product(A, B, false);
+  if (rc) return rc;
+  if (!pred || !slab_elems_host || (!pred->params && !pred->ncap)) SGC_FAIL(SGC_INVALID_ARG, "bad predictor");
+  if (!(pred->margin > 0.0f) || !(pred->scale >= 0.0f)) SGC_FAIL(SGC_INVALID_ARG, "margin must be > 0, scale >= 0");
+  LwWs w = carve_lw(ws, ws_bytes, A->nrows, A->nclusters);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const ResolvedOptions o = resolve(opt);
+  int mode = 0;
+  rc = resolve_mode(o, B, true, &mode);
+  if (rc) return rc;
+  const int sms = num_sms();
+  SGC_CUDA(cudaMemsetAsync(w.sp.status, 0, sizeof(DevStatus), s));
+  const AClusterView av = cview(A, false);
+  const BView bv = bview(B, false);
+  SGC_CUDA(features_run(av, bv, w.X, w.sp.bins.uc_rec, w.h_pos, sms, s));
+  if (!pred->ncap) SGC_CUDA(mlp_infer_run(pred->params, w.X, A->nclusters, w.yhat, sms, s));
+  const int inb = dtype_bytes(A->dtype);
+  SGC_CUDA(learned_bin_run(av, bv, w.yhat, pred->ncap, pred->margin, pred->scale, w.sp.bins.uc_rec, w.h_pos, w.ncap,
+                           w.slab_off, w.flag, w.flist, w.flist_count, w.lb, inb, 8, mode, sms, s));
+  SGC_CUDA(inclusive_scan_i64(w.slab_off + 1, A->nrows, w.sp.scan_tmp, s));
+  SGC_CUDA(cudaMemcpyAsync(w.flist_plan, w.flist_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  SGC_CUDA(cudaMemcpyAsync(slab_elems_host, w.slab_off + A->nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  return sync_status(w.sp.status, s);
+}
+
+int spgemm_learned_phase1(const sgc_csr_cluster* A, const sgc_csr* B, int32_t* slab_col, void* slab_val,
+                          int64_t* c_row_ptr, int64_t* c_nnz_host, int64_t* n_overflow_host, void* ws,
+                          size_t ws_bytes, const sgc_options* opt, void* stream) {
+  int rc = check_product(A, B, true);
+  if (rc) return rc;
+  if (!c_row_ptr || !c_nnz_host || !n_overflow_host) SGC_FAIL(SGC_INVALID_ARG, "NULL output");
+  LwWs w = carve_lw(ws, ws_bytes, A->nrows, A->nclusters);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const ResolvedOptions o = resolve(opt);
+  Launch L{s, o, num_sms(), 0};
+  rc = resolve_mode(o, B, true, &L.mode);
+  if (rc) return rc;
+  SGC_CUDA(cudaMemsetAsync(w.sp.status, 0, sizeof(DevStatus), s));
+  SGC_CUDA(cudaMemsetAsync(c_row_ptr, 0, sizeof(int64_t), s));
+  SGC_CUDA(cudaMemcpyAsync(w.flist_count, w.flist_plan, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  if (A->nrows > 0) {
+    const AClusterView av = cview(A, true);
+    const BView bv = bview(B, true);
+    const LearnedOut lo{1, w.ncap, w.slab_off, slab_col, slab_val, c_row_ptr, w.flag, w.flist, w.flist_count};
+    switch (A->dtype) {
+      case SGC_F32: SGC_CUDA(run_cluster_learned<SGC_F32>(av, bv, w.lb, lo, w.sp.status, L)); break;
+      case SGC_F64: SGC_CUDA(run_cluster_learned<SGC_F64>(av, bv, w.lb, lo, w.sp.status, L)); break;
+      default: SGC_CUDA(run_cluster_learned<SGC_I64>(av, bv, w.lb, lo, w.sp.status, L)); break;
+    }
+    BinOut eb = w.sp.bins;
+    eb.clist = w.flist;
+    eb.clist_count = w.flist_count;
+    SGC_CUDA((run_cluster_phase<true, SGC_F64>(cview(A, false), bview(B, false), CView{}, c_row_ptr, eb, w.sp.status,
+                                               L)));
+  }
+  int32_t nflag = 0;
+  SGC_CUDA(cudaMemcpyAsync(&nflag, w.flist_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  rc = finish_symbolic(c_row_ptr, A->nrows, c_nnz_host, w.sp.status, w.sp.scan_tmp, s);
+  *n_overflow_host = nflag;
+  return rc;
+}
+
+int spgemm_learned_phase2(const sgc_csr_cluster* A, const sgc_csr* B, const int32_t* slab_col,
+                          const void* slab_val, sgc_csr* C, void* ws, size_t ws_bytes, const sgc_options* opt,
+                          void* stream) {
+  int rc = check_product(A, B, true);
+  if (rc) return rc;
+  rc = check_csr(C, "C", true);
+  if (rc) return rc;
+  if (C->nrows != A->nrows || C->ncols != B->ncols || C->dtype != A->dtype)
+    SGC_FAIL(SGC_INVALID_ARG, "C shape or dtype inconsistent with A*B");
+  LwWs w = carve_lw(ws, ws_bytes, A->nrows, A->nclusters);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const ResolvedOptions o = resolve(opt);
+  Launch L{s, o, num_sms(), 0};
+  rc = resolve_mode(o, B, true, &L.mode);
+  if (rc) return rc;
+  if (A->nrows == 0 || C->nnz == 0) return SGC_OK;
+  const AClusterView av = cview(A, true);
+  SGC_CUDA(compact_run(av, w.flag, w.slab_off, slab_col, slab_val, dtype_bytes(A->dtype), C->row_ptr, C->col, C->val,
+                       L.sms, s));
+  BinOut eb = w.sp.bins;
+  eb.clist = w.flist;
+  eb.clist_count = w.flist_count;
+  const BView bv = bview(B, true);
+  const CView cv{C->row_ptr, C->col, C->val};
+  switch (A->dtype) {
+    case SGC_F32: SGC_CUDA((run_cluster_phase<false, SGC_F32>(av, bv, cv, C->row_ptr, eb, w.sp.status, L))); break;
+    case SGC_F64: SGC_CUDA((run_cluster_phase<false, SGC_F64>(av, bv, cv, C->row_ptr, eb, w.sp.status, L))); break;
+    default: SGC_CUDA((run_cluster_phase<false, SGC_I64>(av, bv, cv, C->row_ptr, eb, w.sp.status, L))); break;
+  }
+  return SGC_OK;
+}
+
 }  // extern "C"

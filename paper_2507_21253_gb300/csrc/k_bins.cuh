@@ -45,7 +45,9 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
   __shared__ unsigned long long s_ub[8][32];
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
-  for (int64_t c = gw; c < A.ncl; c += nwarps) {
+  const int64_t nitems = o.clist ? (int64_t)*o.clist_count : A.ncl;
+  for (int64_t q = gw; q < nitems; q += nwarps) {
+    const int64_t c = o.clist ? (int64_t)o.clist[q] : q;
     const int64_t p0 = A.cptr[c];
     const int K = (int)(A.cptr[c + 1] - p0);
     const int64_t u0 = A.uptr[c], u1 = A.uptr[c + 1];
@@ -94,7 +96,9 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, 
                                                          int load_pct, int bulk, int in_bytes, int acc_bytes) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
-  for (int64_t c = gw; c < A.ncl; c += nwarps) {
+  const int64_t nitems = o.clist ? (int64_t)*o.clist_count : A.ncl;
+  for (int64_t q = gw; q < nitems; q += nwarps) {
+    const int64_t c = o.clist ? (int64_t)o.clist[q] : q;
     const int64_t p0 = A.cptr[c];
     const int K = (int)(A.cptr[c + 1] - p0);
     const int64_t T = A.uptr[c + 1] - A.uptr[c];

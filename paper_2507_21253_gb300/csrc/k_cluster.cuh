@@ -181,7 +181,8 @@ template <bool SYM, int DT>
 __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BView B, CView C, int64_t* c_rp_sym,
                                                               const int32_t* items, const int32_t* count_ptr,
                                                               int32_t* nout_rec, const int32_t* uc_rec, int mode,
-                                                              int region_bytes, int gw, int fused, void* status) {
+                                                              int region_bytes, int gw, int fused, LearnedOut lo,
+                                                              void* status) {
   using In = typename VT<DT>::In;
   using Acc = typename VT<DT>::Acc;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -215,7 +216,8 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
     const int64_t u0 = A.uptr[c], T = A.uptr[c + 1] - u0;
     const int64_t v0 = A.vptr[c], nva = A.vptr[c + 1] - v0;
     const int64_t U = uc_rec[c];
-    const int64_t nb = SYM ? min64(U, B.ncols) : (int64_t)nout_rec[c];  // bound / exact output columns
+    // output columns: bound (symbolic), exact count (numeric) or predicted capacity (learned)
+    const int64_t nb = SYM ? min64(U, B.ncols) : (lo.active ? (int64_t)lo.ncap[c] : (int64_t)nout_rec[c]);
     const int LH = cluster_table_log2(SYM, nb);
     const WarpLayout Ly = warp_layout(SYM, T, U, SYM ? 0 : nva, LH, nb, K, sizeof(In), sizeof(Acc), bulk);
     WDesc d;
@@ -403,10 +405,30 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
       }
       newk = warp_sum(newk);
       if (lane == 0 && newk) atomicAdd(&hdr[0], newk);
-      if (__any_sync(FULL, full) && lane == 0) raise(st, DEV_TABLE_FULL, 31, c);
+      const bool anyfull = __any_sync(FULL, full);
+      if (anyfull && lane == 0) {
+        if (lo.active)
+          hdr[1 + wg] = -1;  // table full: more output columns than the capacity
+        else
+          raise(st, DEV_TABLE_FULL, 31, c);
+      } else if (lane == 0 && lo.active) {
+        hdr[1 + wg] = 0;
+      }
       group_sync(gw, gid);
       const int n_out = hdr[0];
-      if (n_out != nb) {
+      if (lo.active) {
+        bool over = n_out > nb;
+        for (int q = 0; q < gw; ++q) over |= hdr[1 + q] != 0;
+        if (over) {  // overflow: leave the cluster to the exact path
+          if (gt == 0) {
+            lo.flag[c] = 1;
+            lo.flist[atomicAdd(lo.flist_count, 1)] = c;
+          }
+          group_sync(gw, gid);
+          continue;
+        }
+        if (gt == 0) lo.flag[c] = 0;
+      } else if (n_out != nb) {
         if (gt == 0) raise(st, DEV_INTERNAL, 32, c);
         group_sync(gw, gid);
         continue;
@@ -544,7 +566,18 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
         }
         // ---- 4. emit row l in column order ----------------------------------
         const int64_t orow = A.perm[p0 + l];
-        const int64_t out0 = C.rp[orow], expect = C.rp[orow + 1] - out0;
+        int64_t out0, expect;
+        int32_t* ocol = C.col;
+        In* oval = (In*)C.val;
+        if (lo.active) {  // slab slot of this position; capacity = distance to the next
+          out0 = lo.slab_off[p0 + l];
+          expect = lo.slab_off[p0 + l + 1] - out0;
+          ocol = lo.slab_col;
+          oval = (In*)lo.slab_val;
+        } else {
+          out0 = C.rp[orow];
+          expect = C.rp[orow + 1] - out0;
+        }
         int64_t nn = 0;
         for (int x0 = 0; x0 < n_out; x0 += 32) {
           const int x = x0 + lane;
@@ -552,12 +585,19 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
           const unsigned bal = __ballot_sync(FULL, f);
           const int64_t pos = nn + __popc(bal & lt);
           if (f && pos < expect) {
-            C.col[out0 + pos] = srt[x];
-            ((In*)C.val)[out0 + pos] = VT<DT>::out(al[x]);
+            ocol[out0 + pos] = srt[x];
+            oval[out0 + pos] = VT<DT>::out(al[x]);
           }
           nn += __popc(bal);
         }
-        if (nn != expect && lane == 0) raise(st, DEV_INTERNAL, 33, orow);
+        if (lo.active) {
+          if (lane == 0) {
+            lo.cnt[orow + 1] = nn;
+            if (nn > expect) raise(st, DEV_INTERNAL, 34, orow);
+          }
+        } else if (nn != expect && lane == 0) {
+          raise(st, DEV_INTERNAL, 33, orow);
+        }
       }
     }
     group_sync(gw, gid);

@@ -95,13 +95,39 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
     const int occ = occupancy(kd, threads, smem);
     const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
     kd<<<grid, threads, smem, L.s>>>(A, B, C, c_rp, bins.dense_items + (int64_t)b * bins.ncl, bins.count + b,
-                                      bins.nout_rec, bins.uc_rec, L.mode, rbytes, gw, L.o.fused, status);
+                                      bins.nout_rec, bins.uc_rec, L.mode, rbytes, gw, L.o.fused, LearnedOut{},
+                                      status);
     note_launches(1);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ACsrView none{};
   return launch_row_bins<SYM, DT, SRC_CLUSTER>(none, A, B, C, c_rp, bins, status, L);
+}
+
+template <int DT>
+cudaError_t run_cluster_learned(const AClusterView& A, const BView& B, const BinOut& lbins, const LearnedOut& lo,
+                                void* status, const Launch& L) {
+  auto kd = k_cluster_group<false, DT>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = allow_smem(kd);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  for (int b = 0; b < NDB; ++b) {
+    const int gw = group_warps(b), groups = groups_per_cta(b);
+    const int rbytes = warp_class_bytes(b);
+    const size_t smem = (size_t)groups * rbytes;
+    const int threads = groups * gw * 32;
+    const int occ = occupancy(kd, threads, smem);
+    const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
+    kd<<<grid, threads, smem, L.s>>>(A, B, CView{}, nullptr, lbins.dense_items + (int64_t)b * lbins.ncl,
+                                      lbins.count + b, nullptr, lbins.uc_rec, L.mode, rbytes, gw, L.o.fused, lo,
+                                      status);
+    note_launches(1);
+  }
+  return cudaGetLastError();
 }
 
 template <bool SYM, int DT>
@@ -125,6 +151,11 @@ cudaError_t run_rows_phase(const ACsrView& A, const BView& B, const CView& C, in
 }
 
 }  // namespace sgc
+
+#define SGC_INSTANTIATE_LEARNED(DT)                                                                        \
+  template cudaError_t sgc::run_cluster_learned<DT>(const sgc::AClusterView&, const sgc::BView&,               \
+                                                    const sgc::BinOut&, const sgc::LearnedOut&, void*,         \
+                                                    const sgc::Launch&);
 
 #define SGC_INSTANTIATE_PHASES(SYM, DT)                                                                   \
   template cudaError_t sgc::run_cluster_phase<SYM, DT>(const sgc::AClusterView&, const sgc::BView&,          \

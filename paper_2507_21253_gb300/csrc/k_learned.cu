@@ -1,0 +1,343 @@
+// Learned per-cluster output-column predictor and the symbolic-free learned
+// path.  The paper has no predictor (its future work names learned choices,
+// Sec. 5); this is the library's extension:
+//  * cluster features (8 FP32 values per cluster from A's cluster structure
+//    and B's row lengths),
+//  * an 8-32-32-1 ReLU MLP in FP32: forward, exact backward, Adam, trained by
+//    one persistent CTA with a fixed summation order (deterministic),
+//  * capacities n_cap = ceil(margin * expm1(yhat)) per cluster, binning,
+//    slab offsets, and the compaction of slab rows into CSR.
+#include "k_launch.cuh"
+
+namespace sgc {
+
+constexpr int NFEAT = 8, NH = 32;
+constexpr int NPARAM = NH * NFEAT + NH + NH * NH + NH + NH + 1;  // 1377
+constexpr int OW1 = 0, OB1 = OW1 + NH * NFEAT, OW2 = OB1 + NH, OB2 = OW2 + NH * NH, OW3 = OB2 + NH, OB3 = OW3 + NH;
+constexpr int PPAD = 1380;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// features: warp per cluster
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_features(AClusterView A, BView B, float* X, int32_t* uc_out,
+                                                  int32_t* h_pos) {
+  __shared__ unsigned long long s_ub[8][32];
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t c = gw; c < A.ncl; c += nwarps) {
+    const int64_t p0 = A.cptr[c];
+    const int K = (int)(A.cptr[c + 1] - p0);
+    const int64_t u0 = A.uptr[c], u1 = A.uptr[c + 1], T = u1 - u0;
+    s_ub[w][lane] = 0;
+    __syncwarp();
+    int64_t U = 0, nA = 0;
+    for (int64_t t = u0 + lane; t < u1; t += 32) {
+      const int32_t k = A.ucol[t];
+      const int64_t len = B.rp[k + 1] - B.rp[k];
+      uint32_t m = A.mask[t];
+      U += len;
+      nA += __popc(m);
+      while (m) {
+        const int l = __ffs(m) - 1;
+        m &= m - 1;
+        atomicAdd(&s_ub[w][l], (unsigned long long)len);
+      }
+    }
+    U = warp_sum(U);
+    nA = warp_sum(nA);
+    __syncwarp();
+    const int64_t ub = lane < K ? (int64_t)s_ub[w][lane] : 0;
+    const int64_t sub = warp_sum(ub), mub = warp_max(ub);
+    if (lane < K && h_pos) h_pos[p0 + lane] = (int32_t)min64(ub, B.ncols);
+    if (lane == 0) {
+      float* x = X + c * NFEAT;
+      const float span = T > 0 ? (float)(A.ucol[u1 - 1] - A.ucol[u0] + 1) / (float)B.ncols : 0.0f;
+      x[0] = (float)K / 32.0f;
+      x[1] = log1pf((float)T) / 8.0f;
+      x[2] = log1pf((float)nA) / 8.0f;
+      x[3] = log1pf((float)U) / 8.0f;
+      x[4] = log1pf((float)sub) / 8.0f;
+      x[5] = log1pf((float)mub) / 8.0f;
+      x[6] = log1pf((float)B.ncols) / 16.0f;
+      x[7] = span;
+      if (uc_out) uc_out[c] = (int32_t)min64(U, 0x7fffffff);
+    }
+    __syncwarp();
+  }
+}
+
+// training targets log1p(n_out) from the symbolic phase's per-cluster record; -1 if absent
+__global__ void k_targets(const int32_t* nout, int64_t ncl, float* y) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncl; c += (int64_t)gridDim.x * blockDim.x)
+    y[c] = nout[c] >= 0 ? log1pf((float)nout[c]) : -1.0f;
+}
+
+// ---------------------------------------------------------------------------
+// MLP: forward for one sample (thread), parameters in shared memory
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float mlp_forward(const float* P, const float* x, float* h1, float* h2) {
+  for (int o = 0; o < NH; ++o) {
+    float z = P[OB1 + o];
+    for (int f = 0; f < NFEAT; ++f) z = __fmaf_rn(P[OW1 + o * NFEAT + f], x[f], z);
+    h1[o] = fmaxf(z, 0.0f);
+  }
+  for (int o = 0; o < NH; ++o) {
+    float z = P[OB2 + o];
+    for (int k = 0; k < NH; ++k) z = __fmaf_rn(P[OW2 + o * NH + k], h1[k], z);
+    h2[o] = fmaxf(z, 0.0f);
+  }
+  float y = P[OB3];
+  for (int k = 0; k < NH; ++k) y = __fmaf_rn(P[OW3 + k], h2[k], y);
+  return y;
+}
+
+__global__ void __launch_bounds__(256) k_mlp_infer(const float* params, const float* X, int64_t n, float* yhat) {
+  __shared__ float P[PPAD];
+  for (int i = threadIdx.x; i < NPARAM; i += blockDim.x) P[i] = params[i];
+  __syncthreads();
+  float h1[NH], h2[NH];
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+    yhat[s] = mlp_forward(P, X + s * NFEAT, h1, h2);
+}
+
+// One CTA; batch = blockDim.x samples per step (thread i = sample i).  Each
+// step: forward, loss gradient (mean over the valid samples: y >= 0), exact
+// backward, per-parameter gradient sums over the batch in sample order, Adam.
+// grad_only: one step on samples order[0..B), gradient and loss written, no update.
+__global__ void __launch_bounds__(256) k_mlp_train(const float* X, const float* y, const int32_t* order,
+                                                   int64_t steps, float lr, const float* init, float* params_out,
+                                                   float* loss_out, int grad_only, float* grad_out) {
+  extern __shared__ __align__(16) float smf[];
+  const int B = blockDim.x, i = threadIdx.x;
+  float* P = smf;
+  float* M = P + PPAD;
+  float* V = M + PPAD;
+  float* Xs = V + PPAD;          // B * 8
+  float* H1 = Xs + B * NFEAT;    // B * 32 (after ReLU)
+  float* H2 = H1 + B * NH;
+  float* D1 = H2 + B * NH;       // dL/dz1
+  float* D2 = D1 + B * NH;       // dL/dz2
+  float* DY = D2 + B * NH;       // dL/dyhat
+  float* LS = DY + B;            // per-sample loss terms
+  for (int q = i; q < NPARAM; q += B) {
+    P[q] = init[q];
+    M[q] = 0.0f;
+    V[q] = 0.0f;
+  }
+  __syncthreads();
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  float b1t = 1.0f, b2t = 1.0f;
+  for (int64_t st = 0; st < steps; ++st) {
+    const int32_t s = order[st * B + i];
+    const float yv = y[s];
+    for (int f = 0; f < NFEAT; ++f) Xs[i * NFEAT + f] = X[(int64_t)s * NFEAT + f];
+    const bool valid = yv >= 0.0f;
+    const float yh = mlp_forward(P, Xs + i * NFEAT, H1 + i * NH, H2 + i * NH);
+    const int nvalid = __syncthreads_count(valid);
+    const float r = valid ? yh - yv : 0.0f;
+    const float dy = nvalid > 0 ? r / (float)nvalid : 0.0f;
+    DY[i] = dy;
+    LS[i] = nvalid > 0 ? 0.5f * r * r / (float)nvalid : 0.0f;
+    for (int o = 0; o < NH; ++o) D2[i * NH + o] = H2[i * NH + o] > 0.0f ? dy * P[OW3 + o] : 0.0f;
+    for (int k = 0; k < NH; ++k) {
+      float g = 0.0f;
+      for (int o = 0; o < NH; ++o) g = __fmaf_rn(D2[i * NH + o], P[OW2 + o * NH + k], g);
+      D1[i * NH + k] = H1[i * NH + k] > 0.0f ? g : 0.0f;
+    }
+    __syncthreads();
+    // gradients: parameter q summed over samples 0..B-1 in order
+    for (int q = i; q < NPARAM; q += B) {
+      float g = 0.0f;
+      if (q < OB1) {
+        const int o = q / NFEAT, f = q % NFEAT;
+        for (int b = 0; b < B; ++b) g = __fmaf_rn(D1[b * NH + o], Xs[b * NFEAT + f], g);
+      } else if (q < OW2) {
+        const int o = q - OB1;
+        for (int b = 0; b < B; ++b) g += D1[b * NH + o];
+      } else if (q < OB2) {
+        const int o = (q - OW2) / NH, k = (q - OW2) % NH;
+        for (int b = 0; b < B; ++b) g = __fmaf_rn(D2[b * NH + o], H1[b * NH + k], g);
+      } else if (q < OW3) {
+        const int o = q - OB2;
+        for (int b = 0; b < B; ++b) g += D2[b * NH + o];
+      } else if (q < OB3) {
+        const int k = q - OW3;
+        for (int b = 0; b < B; ++b) g = __fmaf_rn(DY[b], H2[b * NH + k], g);
+      } else {
+        for (int b = 0; b < B; ++b) g += DY[b];
+      }
+      if (grad_only) {
+        grad_out[q] = g;
+      } else {
+        M[q] = b1 * M[q] + (1.0f - b1) * g;
+        V[q] = b2 * V[q] + (1.0f - b2) * g * g;
+      }
+    }
+    if (loss_out || grad_only) {
+      __syncthreads();
+      if (i == 0) {
+        float l = 0.0f;
+        for (int b = 0; b < B; ++b) l += LS[b];
+        if (loss_out) loss_out[st] = l;
+      }
+    }
+    if (grad_only) return;
+    b1t *= b1;
+    b2t *= b2;
+    __syncthreads();
+    for (int q = i; q < NPARAM; q += B) {
+      const float mh = M[q] / (1.0f - b1t), vh = V[q] / (1.0f - b2t);
+      P[q] -= lr * mh / (sqrtf(vh) + eps);
+    }
+    __syncthreads();
+  }
+  for (int q = i; q < NPARAM; q += B) params_out[q] = P[q];
+}
+
+// ---------------------------------------------------------------------------
+// learned plan: capacities, binning, slab sizes.  Warp per cluster.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t capacity_of(float yhat, int64_t bound, float margin, float scale) {
+  const float P = __fmul_rn(fmaxf(expm1f(yhat), 0.0f), scale);
+  const float want = ceilf(__fmul_rn(margin, P));
+  int64_t cap = want >= 2.0e9f ? (int64_t)2000000000 : (int64_t)want;
+  if (cap < 1) cap = 1;
+  return (int32_t)min64(bound, cap);
+}
+
+__global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, const float* yhat, const int32_t* ncap_in,
+                                                     float margin, float scale, const int32_t* uc, const int32_t* h_pos,
+                                                     int32_t* ncap_out, int64_t* capw, int32_t* flag, int32_t* flist,
+                                                     int32_t* flist_count, BinOut lb, int in_bytes, int acc_bytes,
+                                                     int bulk) {
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t c = gw; c < A.ncl; c += nwarps) {
+    const int64_t p0 = A.cptr[c];
+    const int K = (int)(A.cptr[c + 1] - p0);
+    const int64_t T = A.uptr[c + 1] - A.uptr[c];
+    const int64_t nva = A.vptr[c + 1] - A.vptr[c];
+    const int64_t U = uc[c];
+    const int64_t bound = min64(U, B.ncols);
+    const int32_t ncap = ncap_in ? (int32_t)min64(ncap_in[c], bound) : capacity_of(yhat[c], bound, margin, scale);
+    int cls = -1;
+    if (U < (1ll << 28) && T < (1ll << 24)) {
+      const WarpLayout L =
+          warp_layout(false, T, U, nva, cluster_table_log2(false, ncap), ncap, K, in_bytes, acc_bytes, bulk != 0);
+      cls = warp_class(L.total);
+    }
+    if (lane == 0) {
+      ncap_out[c] = ncap;
+      flag[c] = cls < 0 ? 1 : 0;
+      if (cls >= 0) {
+        const int32_t idx = atomicAdd(&lb.count[cls], 1);
+        lb.dense_items[(int64_t)cls * lb.ncl + idx] = (int32_t)c;
+      } else {
+        flist[atomicAdd(flist_count, 1)] = (int32_t)c;
+      }
+    }
+    if (lane < K) capw[p0 + lane + 1] = cls >= 0 ? min64((int64_t)h_pos[p0 + lane], (int64_t)ncap) : 0;
+  }
+}
+
+// copy the slab rows of clusters that did not overflow into C (warp per cluster)
+template <class V>
+__global__ void __launch_bounds__(256) k_compact(AClusterView A, const int32_t* flag, const int64_t* slab_off,
+                                                 const int32_t* slab_col, const V* slab_val, const int64_t* c_rp,
+                                                 int32_t* ccol, V* cval) {
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t c = gw; c < A.ncl; c += nwarps) {
+    if (flag[c]) continue;
+    const int64_t p0 = A.cptr[c], p1 = A.cptr[c + 1];
+    for (int64_t p = p0; p < p1; ++p) {
+      const int64_t r = A.perm[p];
+      const int64_t dst = c_rp[r], n = c_rp[r + 1] - dst, src = slab_off[p];
+      for (int64_t q = lane; q < n; q += 32) {
+        ccol[dst + q] = slab_col[src + q];
+        cval[dst + q] = slab_val[src + q];
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t features_run(const AClusterView& A, const BView& B, float* X, int32_t* uc, int32_t* h_pos, int sms,
+                         cudaStream_t s) {
+  if (A.ncl <= 0) return cudaSuccess;
+  k_features<<<grid_for(A.ncl, 8, sms, 8), 256, 0, s>>>(A, B, X, uc, h_pos);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t targets_run(const int32_t* nout, int64_t ncl, float* y, int sms, cudaStream_t s) {
+  if (ncl <= 0) return cudaSuccess;
+  k_targets<<<grid_for(ncl, 256, sms, 8), 256, 0, s>>>(nout, ncl, y);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_infer_run(const float* params, const float* X, int64_t n, float* yhat, int sms, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_mlp_infer<<<grid_for(n, 256, sms, 4), 256, 0, s>>>(params, X, n, yhat);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+size_t mlp_train_smem(int B) { return sizeof(float) * (3 * PPAD + (size_t)B * (NFEAT + 4 * NH + 2)); }
+
+cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, int64_t steps, int B, float lr,
+                          const float* init, float* params_out, float* loss_out, int grad_only, float* grad_out,
+                          cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_mlp_train<<<1, B, mlp_train_smem(B), s>>>(X, y, order, steps, lr, init, params_out, loss_out, grad_only,
+                                              grad_out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const int32_t* ncap_in,
+                            float margin, float scale, const int32_t* uc, const int32_t* h_pos, int32_t* ncap_out,
+                            int64_t* capw, int32_t* flag, int32_t* flist, int32_t* flist_count, const BinOut& lb,
+                            int in_bytes, int acc_bytes, int bulk, int sms, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(lb.count, 0, sizeof(int32_t) * NBIN_ALL, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(flist_count, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(capw, 0, sizeof(int64_t), s);
+  if (e != cudaSuccess) return e;
+  if (A.ncl <= 0) return cudaSuccess;
+  k_learned_bin<<<grid_for(A.ncl, 8, sms, 8), 256, 0, s>>>(A, B, yhat, ncap_in, margin, scale, uc, h_pos, ncap_out,
+                                                            capw, flag, flist, flist_count, lb, in_bytes, acc_bytes,
+                                                            bulk);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t compact_run(const AClusterView& A, const int32_t* flag, const int64_t* slab_off, const int32_t* slab_col,
+                        const void* slab_val, int val_bytes, const int64_t* c_rp, int32_t* ccol, void* cval, int sms,
+                        cudaStream_t s) {
+  if (A.ncl <= 0) return cudaSuccess;
+  const unsigned g = grid_for(A.ncl, 8, sms, 8);
+  if (val_bytes == 4)
+    k_compact<uint32_t><<<g, 256, 0, s>>>(A, flag, slab_off, slab_col, (const uint32_t*)slab_val, c_rp, ccol,
+                                          (uint32_t*)cval);
+  else
+    k_compact<uint64_t><<<g, 256, 0, s>>>(A, flag, slab_off, slab_col, (const uint64_t*)slab_val, c_rp, ccol,
+                                          (uint64_t*)cval);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace sgc

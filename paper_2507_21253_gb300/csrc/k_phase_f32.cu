@@ -2,3 +2,4 @@
 #include "k_launch.cuh"
 
 SGC_INSTANTIATE_PHASES(false, SGC_F32)
+SGC_INSTANTIATE_LEARNED(SGC_F32)

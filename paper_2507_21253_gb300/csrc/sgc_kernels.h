@@ -56,6 +56,22 @@ struct BinOut {
   int32_t* uc_rec;       // ncl: staged B elements per cluster
   int32_t* nout_rec;     // ncl: output-column union size (-1: rows handled row-level)
   int64_t ncl, nrows;
+  const int32_t* clist;        // optional: only these clusters (device ids) ...
+  const int32_t* clist_count;  // ... and their count (device); both NULL = all clusters
+};
+
+// Learned mode of the numeric cluster kernel: capacities instead of exact
+// counts, output into a slab indexed by row position, overflow flags.
+struct LearnedOut {
+  int active;                // 0: exact numeric into C; 1: learned (fields below)
+  const int32_t* ncap;       // per cluster: capacity for the cluster's output columns
+  const int64_t* slab_off;   // per position (cluster order), nrows+1: slab offsets
+  int32_t* slab_col;
+  void* slab_val;
+  int64_t* cnt;              // per original row r: row count at cnt[r + 1]
+  int32_t* flag;             // per cluster: 0 = done, 1 = overflow (exact path)
+  int32_t* flist;            // overflow cluster list (appended) ...
+  int32_t* flist_count;      // ... and its count
 };
 
 struct Launch {
@@ -68,6 +84,10 @@ struct Launch {
 template <bool SYM, int DT>
 cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView& C, int64_t* c_rp,
                               const BinOut& bins, void* status, const Launch& L);
+// learned numeric: launch the cluster kernel in learned mode over pre-binned classes
+template <int DT>
+cudaError_t run_cluster_learned(const AClusterView& A, const BView& B, const BinOut& lbins, const LearnedOut& lo,
+                                void* status, const Launch& L);
 template <bool SYM, int DT>
 cudaError_t run_rows_phase(const ACsrView& A, const BView& B, const CView& C, int64_t* c_rp,
                            const BinOut& bins, void* status, const Launch& L);
@@ -85,6 +105,23 @@ cudaError_t validate_csr_run(const int64_t* rp, const int32_t* col, int64_t nrow
                              int64_t nnz, void* status, int where, cudaStream_t s);
 cudaError_t validate_cluster_run(const AClusterView& A, int64_t ncols, void* status,
                                  cudaStream_t s);
+
+// k_learned.cu
+cudaError_t features_run(const AClusterView& A, const BView& B, float* X, int32_t* uc, int32_t* h_pos, int sms,
+                         cudaStream_t s);
+cudaError_t targets_run(const int32_t* nout, int64_t ncl, float* y, int sms, cudaStream_t s);
+cudaError_t mlp_infer_run(const float* params, const float* X, int64_t n, float* yhat, int sms, cudaStream_t s);
+size_t mlp_train_smem(int B);
+cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, int64_t steps, int B, float lr,
+                          const float* init, float* params_out, float* loss_out, int grad_only, float* grad_out,
+                          cudaStream_t s);
+cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const int32_t* ncap_in,
+                            float margin, float scale, const int32_t* uc, const int32_t* h_pos, int32_t* ncap_out,
+                            int64_t* capw, int32_t* flag, int32_t* flist, int32_t* flist_count, const BinOut& lb,
+                            int in_bytes, int acc_bytes, int bulk, int sms, cudaStream_t s);
+cudaError_t compact_run(const AClusterView& A, const int32_t* flag, const int64_t* slab_off, const int32_t* slab_col,
+                        const void* slab_val, int val_bytes, const int64_t* c_rp, int32_t* ccol, void* cval, int sms,
+                        cudaStream_t s);
 
 // k_hc.cu / hc_merge.cpp
 cudaError_t hc_candidates_run(const int64_t* arp, const int32_t* acol, int64_t nrows, int64_t ncols, int64_t nnz,

@@ -54,6 +54,10 @@ class ClusterStruct(ctypes.Structure):
                 ("ucol", vp), ("mask", vp), ("val_ptr", vp), ("val", vp)]
 
 
+class Predictor(ctypes.Structure):
+    _fields_ = [("params", vp), ("margin", ctypes.c_float), ("scale", ctypes.c_float), ("ncap", vp)]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("staging", i32), ("validate", i32), ("stage_elems", i32), ("max_warps", i32),
                 ("load_pct", i32), ("fused_fma", i32), ("reserved", i32 * 10)]
@@ -92,6 +96,20 @@ _c = {
                                 ctypes.c_size_t, vp),
     "hcluster_reorder": _sig("hcluster_reorder", P(CsrStruct), ctypes.c_float, i32, vp, vp, P(i64), vp,
                              ctypes.c_size_t, vp),
+    "cluster_features": _sig("cluster_features", P(ClusterStruct), P(CsrStruct), vp, vp),
+    "nnz_predictor_targets": _sig("nnz_predictor_targets", P(ClusterStruct), P(CsrStruct), vp, ctypes.c_size_t, vp,
+                                  vp),
+    "nnz_predictor_infer": _sig("nnz_predictor_infer", vp, vp, i64, vp, vp),
+    "nnz_predictor_grad": _sig("nnz_predictor_grad", vp, vp, vp, vp, i32, vp, vp, vp),
+    "nnz_predictor_train": _sig("nnz_predictor_train", vp, vp, i64, vp, i64, i32, ctypes.c_float, vp, vp, vp, vp),
+    "spgemm_learned_workspace_size": _sig("spgemm_learned_workspace_size", P(ClusterStruct), P(CsrStruct),
+                                          P(Options), P(ctypes.c_size_t)),
+    "spgemm_learned_plan": _sig("spgemm_learned_plan", P(ClusterStruct), P(CsrStruct), P(Predictor), P(i64), vp,
+                                ctypes.c_size_t, P(Options), vp),
+    "spgemm_learned_phase1": _sig("spgemm_learned_phase1", P(ClusterStruct), P(CsrStruct), vp, vp, vp, P(i64),
+                                  P(i64), vp, ctypes.c_size_t, P(Options), vp),
+    "spgemm_learned_phase2": _sig("spgemm_learned_phase2", P(ClusterStruct), P(CsrStruct), vp, vp, P(CsrStruct), vp,
+                                  ctypes.c_size_t, P(Options), vp),
     "spgemm_rowwise_numeric": _sig("spgemm_rowwise_numeric", P(CsrStruct), P(CsrStruct), P(CsrStruct), vp,
                                    ctypes.c_size_t, P(Options), vp),
 }
@@ -356,3 +374,104 @@ def hcluster_reorder(A: DeviceCsr, jacc_th: float = JACC_TH, max_cluster: int = 
     _call("hcluster_reorder", ctypes.byref(a), float(jacc_th), max_cluster, _ptr(perm), _ptr(cptr),
           ctypes.byref(ncl), ws.ptr, ws.nbytes, _stream())
     return perm[:A.nrows], cptr[:ncl.value + 1]
+
+
+# ---------------------------------------------------------------------------
+# learned per-cluster output-column predictor
+# ---------------------------------------------------------------------------
+NPARAM = 1377
+
+
+def _o(opt):
+    return ctypes.byref(opt) if opt else None
+
+
+def cluster_features(A: DeviceCsrCluster, B: DeviceCsr) -> torch.Tensor:
+    X = torch.empty((A.nclusters, 8), dtype=torch.float32, device=B.row_ptr.device)
+    a, b = A.struct(), B.struct()
+    _call("cluster_features", ctypes.byref(a), ctypes.byref(b), _ptr(X), _stream())
+    return X
+
+
+def nnz_predictor_targets(A: DeviceCsrCluster, B: DeviceCsr, ws: Workspace) -> torch.Tensor:
+    """log1p(n_out) per cluster from a completed symbolic phase (-1 where not recorded)."""
+    y = torch.empty(A.nclusters, dtype=torch.float32, device=B.row_ptr.device)
+    a, b = A.struct(), B.struct()
+    _call("nnz_predictor_targets", ctypes.byref(a), ctypes.byref(b), ws.ptr, ws.nbytes, _ptr(y), _stream())
+    return y
+
+
+def nnz_predictor_infer(params: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
+    y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _call("nnz_predictor_infer", _ptr(params), _ptr(X), X.shape[0], _ptr(y), _stream())
+    return y
+
+
+def nnz_predictor_grad(params, X, y, idx):
+    g = torch.empty(NPARAM, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _call("nnz_predictor_grad", _ptr(params), _ptr(X), _ptr(y), _ptr(idx), int(idx.numel()), _ptr(g), _ptr(loss),
+          _stream())
+    return g, loss
+
+
+def nnz_predictor_train(X, y, order, steps: int, batch: int, lr: float, init, with_loss: bool = True):
+    """Returns (params, per-step loss or None)."""
+    params = torch.empty(NPARAM, dtype=torch.float32, device=X.device)
+    loss = torch.empty(max(steps, 1), dtype=torch.float32, device=X.device) if with_loss else None
+    _call("nnz_predictor_train", _ptr(X), _ptr(y), X.shape[0], _ptr(order), int(steps), int(batch), float(lr),
+          _ptr(init), _ptr(params), _ptr(loss), _stream())
+    return params, loss
+
+
+class LearnedSpgemm:
+    """The symbolic-free learned path: plan (capacities), phase 1 (slab + row counts), phase 2 (C)."""
+
+    def __init__(self, A: DeviceCsrCluster, B: DeviceCsr, params=None, margin=1.25, scale=1.0, ncap=None,
+                 opt: Options | None = None):
+        self.A, self.B, self.opt = A, B, opt
+        n = ctypes.c_size_t()
+        a, b = A.struct(), B.struct()
+        _call("spgemm_learned_workspace_size", ctypes.byref(a), ctypes.byref(b), _o(opt), ctypes.byref(n))
+        self.ws = Workspace(n.value, B.row_ptr.device)
+        self.params, self.ncap = params, ncap
+        self.pred = Predictor(_ptr(params) if params is not None else vp(0), float(margin), float(scale),
+                              _ptr(ncap) if ncap is not None else vp(0))
+        self.c_row_ptr = torch.empty(A.nrows + 1, dtype=torch.int64, device=B.row_ptr.device)
+        self.plan()
+
+    def plan(self):
+        elems = i64()
+        a, b = self.A.struct(), self.B.struct()
+        _call("spgemm_learned_plan", ctypes.byref(a), ctypes.byref(b), ctypes.byref(self.pred), ctypes.byref(elems),
+              self.ws.ptr, self.ws.nbytes, _o(self.opt), _stream())
+        dev = self.B.row_ptr.device
+        self.slab_elems = elems.value
+        self.slab_col = torch.empty(max(elems.value, 1), dtype=torch.int32, device=dev)
+        self.slab_val = torch.empty(max(elems.value, 1), dtype=self.B.val.dtype, device=dev)
+
+    def phase1(self):
+        nnz, nover = i64(), i64()
+        a, b = self.A.struct(), self.B.struct()
+        _call("spgemm_learned_phase1", ctypes.byref(a), ctypes.byref(b), _ptr(self.slab_col), _ptr(self.slab_val),
+              _ptr(self.c_row_ptr), ctypes.byref(nnz), ctypes.byref(nover), self.ws.ptr, self.ws.nbytes,
+              _o(self.opt), _stream())
+        self.nnz, self.n_overflow = nnz.value, nover.value
+        return self.nnz, self.n_overflow
+
+    def phase2(self, C: DeviceCsr | None = None) -> DeviceCsr:
+        dev = self.B.row_ptr.device
+        if C is None:
+            C = DeviceCsr(self.A.nrows, self.B.ncols, self.c_row_ptr, torch.empty(self.nnz, dtype=torch.int32,
+                                                                                  device=dev),
+                          torch.empty(self.nnz, dtype=self.B.val.dtype, device=dev))
+        a, b, c = self.A.struct(), self.B.struct(), C.struct()
+        _call("spgemm_learned_phase2", ctypes.byref(a), ctypes.byref(b), _ptr(self.slab_col), _ptr(self.slab_val),
+              ctypes.byref(c), self.ws.ptr, self.ws.nbytes, _o(self.opt), _stream())
+        return C
+
+    def run(self) -> DeviceCsr:
+        self.phase1()
+        C = self.phase2()
+        workspace_status(self.ws)
+        return C

@@ -1,0 +1,158 @@
+"""GPU learned predictor and the symbolic-free learned path vs the oracle.
+
+Features, inference, gradient and Adam steps are checked against the FP64
+definitions in oracle/learned.py; the learned SpGEMM must reproduce the
+oracle's C exactly whatever the predictor says (under-predicted clusters go
+through the exact path), and its overflow set must be the oracle's rule
+n_out > n_cap on the capacities given.
+"""
+import numpy as np
+import pytest
+
+from oracle import csr_cluster as occ
+from oracle import gustavson as og
+from oracle import hcluster as oh
+from oracle import learned as ol
+from paper_2507_21253_gb300 import synth
+from tests.gpu_helpers import compare, lib
+from tests.test_oracle_gustavson import random_sparse
+
+pytestmark = pytest.mark.gpu
+TH = float(np.float32(0.3))
+
+
+@pytest.fixture(scope="module")
+def sgc():
+    return lib()
+
+
+def clustered(sgc, A, how="hc"):
+    Ad = sgc.DeviceCsr.from_host(A)
+    if how == "hc":
+        perm, cptr = oh.hierarchical(A, TH, 8) if A.nrows <= 4096 else synth.random_clusters(A.nrows, 3, 8)
+    else:
+        perm, cptr = synth.random_clusters(A.nrows, 7, kmax=how)
+    return Ad, sgc.csr_cluster_build(Ad, perm, cptr), perm, cptr
+
+
+def test_features_match_oracle(sgc):
+    for A in (synth.planted_groups(2048, 4003), synth.stencil27_3d(9, 8, 7, seed=5),
+              random_sparse(300, 300, 0.04, 4, "f64")):
+        Ad, Acl, perm, cptr = clustered(sgc, A)
+        X = sgc.cluster_features(Acl, Ad).cpu().numpy()
+        ref = ol.features(occ.build(A, perm, cptr), np.diff(A.row_ptr), A.ncols)
+        assert np.allclose(X, ref, rtol=1e-5, atol=1e-6)
+
+
+def test_infer_matches_oracle(sgc):
+    import torch
+    rs = synth.Stream(8, 8)
+    X = (rs.uniform(1000 * 8).reshape(1000, 8) * 2.0).astype(np.float32)
+    p = synth.mlp_init(11)
+    y = sgc.nnz_predictor_infer(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
+    ref, _ = ol.forward(p.astype(np.float64), X.astype(np.float64))
+    assert np.allclose(y, ref, rtol=1e-4, atol=1e-5)
+
+
+@pytest.mark.parametrize("batch", [32, 256])
+def test_gradient_matches_oracle(sgc, batch):
+    import torch
+    rs = synth.Stream(9, batch)
+    n = 700
+    X = (rs.uniform(n * 8).reshape(n, 8) * 1.5).astype(np.float32)
+    y = (rs.uniform(n) * 6.0).astype(np.float32)
+    y[::17] = -1.0                                    # invalid samples are ignored
+    idx = rs.permutation(n)[:batch].astype(np.int32)
+    p = synth.mlp_init(12)
+    g, loss = sgc.nnz_predictor_grad(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda(),
+                                     torch.from_numpy(y).cuda(), torch.from_numpy(idx).cuda())
+    keep = idx[y[idx] >= 0]
+    rl, rg = ol.loss_and_grad(p.astype(np.float64), X[keep].astype(np.float64), y[keep].astype(np.float64))
+    g = g.cpu().numpy()
+    assert np.max(np.abs(g - rg)) <= 1e-4 * np.max(np.abs(rg))
+    assert abs(float(loss.item()) - rl) <= 1e-5 * max(1.0, rl)
+
+
+def test_adam_steps_match_oracle(sgc):
+    import torch
+    rs = synth.Stream(10, 1)
+    n, B, steps, lr = 512, 64, 6, 1e-3
+    X = (rs.uniform(n * 8).reshape(n, 8)).astype(np.float32)
+    y = (rs.uniform(n) * 4.0).astype(np.float32)
+    order = synth.minibatch_order(n, 1, 5)[: steps * B]
+    p0 = synth.mlp_init(13)
+    params, loss = sgc.nnz_predictor_train(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(),
+                                           torch.from_numpy(order).cuda(), steps, B, lr,
+                                           torch.from_numpy(p0).cuda())
+    p = p0.astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for t in range(steps):
+        ids = order[t * B:(t + 1) * B]
+        _, g = ol.loss_and_grad(p, X[ids].astype(np.float64), y[ids].astype(np.float64))
+        p, m, v = ol.adam_step(p, m, v, g, t + 1, lr)
+    got = params.cpu().numpy()
+    # each Adam step moves a parameter by about lr; FP32 vs FP64 agree to a small fraction of it
+    assert np.max(np.abs(got - p)) <= 0.05 * lr * steps
+    assert loss.cpu().numpy()[-1] <= loss.cpu().numpy()[0] * 1.01
+
+
+def test_targets_are_union_counts(sgc):
+    A = synth.planted_groups(2048, 4004)
+    Ad, Acl, perm, cptr = clustered(sgc, A)
+    ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad))
+    sgc.spgemm_symbolic(Acl, Ad, ws)
+    y = sgc.nnz_predictor_targets(Acl, Ad, ws).cpu().numpy()
+    rp, col, _, _ = og.spgemm(A, A, want_mag=False)
+    rows = [col[rp[r]:rp[r + 1]] for r in range(A.nrows)]
+    n_out = ol.union_counts(occ.build(A, perm, cptr), rows)
+    ok = y >= 0
+    assert ok.mean() > 0.9
+    assert np.allclose(y[ok], np.log1p(n_out[ok]).astype(np.float32), rtol=1e-6)
+
+
+LEARNED_CASES = [("planted_f64", lambda: synth.planted_groups(2048, 4005)),
+                 ("stencil_f64", lambda: synth.stencil27_3d(10, 9, 8, seed=6)),
+                 ("rmat_i64", lambda: synth.workload_rmat("i64", seed=4, scale=11)),
+                 ("rand_f32", lambda: random_sparse(400, 400, 0.03, 9, "f32"))]
+
+
+@pytest.mark.parametrize("name,make", LEARNED_CASES, ids=[c[0] for c in LEARNED_CASES])
+def test_learned_explicit_caps_overflow_rule(sgc, name, make):
+    """Caps around the true n_out: exactly the clusters with n_out > n_cap overflow, C exact."""
+    import torch
+    A = make()
+    Ad, Acl, perm, cptr = clustered(sgc, A, how=8)
+    cc = occ.build(A, perm, cptr)
+    rp, col, _, _ = og.spgemm(A, A, want_mag=False)
+    n_out = ol.union_counts(cc, [col[rp[r]:rp[r + 1]] for r in range(A.nrows)])
+    rs = synth.Stream(21, 1)
+    caps = np.maximum(1, (n_out * (0.7 + 0.6 * rs.uniform(n_out.size))).astype(np.int64)).astype(np.int32)
+    U = np.array([int(np.sum(np.diff(A.row_ptr)[cc["ucol"][cc["ucol_ptr"][c]:cc["ucol_ptr"][c + 1]]]))
+                  for c in range(cc["nclusters"])])
+    caps_eff = np.minimum(caps, np.minimum(U, A.ncols))
+    L = sgc.LearnedSpgemm(Acl, Ad, ncap=torch.from_numpy(caps).cuda(), margin=1.0)
+    C = L.run()
+    expect_over = int(ol.overflowing_clusters(n_out, caps_eff).sum())
+    if name == "rmat_i64":
+        assert L.n_overflow >= expect_over  # hub clusters too large for shared memory also take the exact path
+    else:
+        assert L.n_overflow == expect_over
+    compare(C, A, A, exact_f64=(A.val.dtype == np.float64))
+
+
+@pytest.mark.parametrize("scale", [1.0, 0.05])
+@pytest.mark.parametrize("name,make", LEARNED_CASES, ids=[c[0] for c in LEARNED_CASES])
+def test_learned_with_mlp_is_exact(sgc, name, make, scale):
+    import torch
+    A = make()
+    Ad, Acl, perm, cptr = clustered(sgc, A, how=8)
+    params = torch.from_numpy(synth.mlp_init(3)).cuda()
+    L = sgc.LearnedSpgemm(Acl, Ad, params=params, margin=1.25, scale=scale)
+    C = L.run()
+    compare(C, A, A, exact_f64=(A.val.dtype == np.float64))
+    if scale < 0.1:
+        assert L.n_overflow > 0
+    # a second run on the same plan gives the same result
+    C2 = L.run()
+    assert np.array_equal(C2.col.cpu().numpy(), C.col.cpu().numpy())

@@ -77,21 +77,24 @@ def test_features_by_hand():
 
 
 def test_capacity_rule_by_hand():
-    # one cluster of 3 rows, ub = [10, 30, 0], h = [10, 8, 0]; yhat = log(41) -> P = 40
-    caps = ol.row_capacity_f32(np.array([math.log(41.0)], dtype=np.float32), np.array([10, 30, 0]),
-                               np.array([10, 8, 0]), np.array([0, 3]), margin=1.5, scale=1.0)
-    # e = [10, 30] -> ceil(1.5 e) = [15, 45] -> min with h -> [10, 8]
-    assert caps.tolist() == [10, 8, 0]
-    caps = ol.row_capacity_f32(np.array([math.log(41.0)], dtype=np.float32), np.array([10, 30, 0]),
-                               np.array([100, 100, 0]), np.array([0, 3]), margin=1.0, scale=0.5)
-    assert caps.tolist() == [5, 15, 0]
+    # yhat = log(41) -> P = 40; margin 1.5 -> 60; bounded by min(U, ncols)
+    y = np.array([math.log(41.0)] * 3, dtype=np.float32)
+    caps = ol.cluster_capacity_f32(y, np.array([100, 50, 100]), ncols_b=70, margin=1.5, scale=1.0)
+    assert caps.tolist() == [60, 50, 60]
+    caps = ol.cluster_capacity_f32(y, np.array([100, 100, 100]), ncols_b=1000, margin=1.0, scale=0.5)
+    assert caps.tolist() == [20, 20, 20]
+    caps = ol.cluster_capacity_f32(np.array([-3.0], dtype=np.float32), np.array([9]), 9, 1.2, 1.0)
+    assert caps.tolist() == [1]                       # expm1 < 0 -> P = 0 -> at least 1
 
 
-def test_overflow_rule_brute_force():
+def test_union_counts_and_overflow_by_brute_force():
+    A = synth.Csr(4, 5, np.array([0, 2, 3, 5, 6]), np.array([0, 1, 1, 2, 4, 3], dtype=np.int32), np.ones(6))
+    cc = occ.build(A, np.array([0, 2, 1, 3]), np.array([0, 2, 4]))
+    C_rows = [[0, 3], [1], [2, 3, 4], [4]]          # rows of some C, original order
+    n_out = ol.union_counts(cc, C_rows)
+    assert n_out.tolist() == [4, 2]                  # {0,3} | {2,3,4}; {1} | {4}
     rs = synth.Stream(4, 4)
-    cnt = rs.randint(20, 50)
-    caps = rs.randint(20, 50)
-    cptr = np.array([0, 3, 4, 10, 25, 50])
-    got = ol.overflowing_clusters(cnt, caps, cptr)
-    for c in range(5):
-        assert got[c] == any(cnt[q] > caps[q] for q in range(cptr[c], cptr[c + 1]))
+    a = rs.randint(20, 50)
+    b = rs.randint(20, 50)
+    got = ol.overflowing_clusters(a, b)
+    assert got.tolist() == [bool(x > y) for x, y in zip(a, b)]
