@@ -1,0 +1,96 @@
+"""Training and checkpoints of the per-cluster output-column predictor.
+
+Orchestration only: each step calls the library (hierarchical clustering,
+CSR_Cluster build, symbolic phase, features, targets, the training kernel);
+the arithmetic runs in libsgc's kernels.  Training data are the symbolic
+phase's own per-cluster output-column counts on seeded smaller instances of
+the workload's generator.
+"""
+from __future__ import annotations
+
+import os
+import struct
+
+import numpy as np
+import torch
+
+from . import sgc, synth
+
+MAGIC = b"SGCNNZP1"
+
+
+def instance_data(A, jacc_th: float = sgc.JACC_TH, max_cluster: int = sgc.MAX_CLUSTER, device="cuda"):
+    """(features [ncl, 8], targets [ncl]) of one instance, clustered hierarchically."""
+    Ad = sgc.DeviceCsr.from_host(A, device)
+    perm, cptr = sgc.hcluster_reorder(Ad, jacc_th, max_cluster)
+    Acl = sgc.csr_cluster_build(Ad, perm, cptr, sgc.LAYOUT_MASKED)
+    ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad), device)
+    sgc.spgemm_symbolic(Acl, Ad, ws)
+    X = sgc.cluster_features(Acl, Ad)
+    y = sgc.nnz_predictor_targets(Acl, Ad, ws)
+    return X, y
+
+
+def train(make_instance, seeds, epochs: int = 4, batch: int = 256, lr: float = 2e-3, init_seed: int = 1,
+          device="cuda"):
+    """Trains on instances make_instance(seed) for seed in seeds; returns (params, per-step loss)."""
+    feats, ys = [], []
+    for s in seeds:
+        X, y = instance_data(make_instance(s), device=device)
+        feats.append(X)
+        ys.append(y)
+    X = torch.cat(feats)
+    y = torch.cat(ys)
+    n = int(X.shape[0])
+    order = synth.minibatch_order(n, epochs, init_seed)
+    steps = order.size // batch
+    order_d = torch.from_numpy(order[: steps * batch]).to(device)
+    init = torch.from_numpy(synth.mlp_init(init_seed)).to(device)
+    params, loss = sgc.nnz_predictor_train(X, y, order_d, steps, batch, lr, init)
+    return params, loss
+
+
+def save(path: str, params: torch.Tensor, meta: str = "") -> None:
+    """Versioned checkpoint: magic, parameter count, metadata, FP32 parameters."""
+    p = params.detach().float().cpu().numpy()
+    m = meta.encode()
+    with open(path, "wb") as fh:
+        fh.write(MAGIC + struct.pack("<II", p.size, len(m)) + m + p.tobytes())
+
+
+def load(path: str, device="cuda") -> torch.Tensor:
+    with open(path, "rb") as fh:
+        data = fh.read()
+    if data[:8] != MAGIC:
+        raise ValueError(f"{path}: not a predictor checkpoint")
+    n, mlen = struct.unpack("<II", data[8:16])
+    if n != sgc.NPARAM:
+        raise ValueError(f"{path}: {n} parameters, expected {sgc.NPARAM}")
+    p = np.frombuffer(data[16 + mlen:16 + mlen + 4 * n], dtype=np.float32).copy()
+    return torch.from_numpy(p).to(device)
+
+
+# generators of training instances, by workload family
+def planted_instance(seed: int):
+    return synth.planted_groups(synth.planted_training_size(seed), seed)
+
+
+def stencil_instance(seed: int):
+    rs = synth.Stream(seed, 505)
+    nx = 12 + int(rs.randint(37, 1)[0])          # 12 .. 48
+    return synth.stencil27_3d(nx, nx, nx, seed)
+
+
+def powerlaw_instance(seed: int):
+    return synth.powerlaw_matrix(seed)
+
+
+def rmat_instance(seed: int):
+    rs = synth.Stream(seed, 606)
+    return synth.rmat(10 + int(rs.randint(4, 1)[0]), 16, 0.57, 0.19, 0.19, seed, "f64")
+
+
+def laplacian_instance(seed: int):
+    rs = synth.Stream(seed, 707)
+    nx = 16 + int(rs.randint(49, 1)[0])           # 16 .. 64
+    return synth.workload_laplacian(seed, nx=nx)

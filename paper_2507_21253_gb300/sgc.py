@@ -438,17 +438,20 @@ class LearnedSpgemm:
         self.pred = Predictor(_ptr(params) if params is not None else vp(0), float(margin), float(scale),
                               _ptr(ncap) if ncap is not None else vp(0))
         self.c_row_ptr = torch.empty(A.nrows + 1, dtype=torch.int64, device=B.row_ptr.device)
+        self.slab_col = self.slab_val = None
         self.plan()
 
     def plan(self):
+        """Capacities and slab size; (re)allocates the slab only when it must grow."""
         elems = i64()
         a, b = self.A.struct(), self.B.struct()
         _call("spgemm_learned_plan", ctypes.byref(a), ctypes.byref(b), ctypes.byref(self.pred), ctypes.byref(elems),
               self.ws.ptr, self.ws.nbytes, _o(self.opt), _stream())
         dev = self.B.row_ptr.device
         self.slab_elems = elems.value
-        self.slab_col = torch.empty(max(elems.value, 1), dtype=torch.int32, device=dev)
-        self.slab_val = torch.empty(max(elems.value, 1), dtype=self.B.val.dtype, device=dev)
+        if getattr(self, "slab_col", None) is None or self.slab_col.numel() < max(elems.value, 1):
+            self.slab_col = torch.empty(max(elems.value, 1), dtype=torch.int32, device=dev)
+            self.slab_val = torch.empty(max(elems.value, 1), dtype=self.B.val.dtype, device=dev)
 
     def phase1(self):
         nnz, nover = i64(), i64()

@@ -156,3 +156,41 @@ def test_learned_with_mlp_is_exact(sgc, name, make, scale):
     # a second run on the same plan gives the same result
     C2 = L.run()
     assert np.array_equal(C2.col.cpu().numpy(), C.col.cpu().numpy())
+
+
+def test_training_gain_over_untrained(sgc):
+    """What the trained network gains: on a held-out planted instance, the GPU-trained
+    predictor (trained on the symbolic phase's counts of seeded smaller instances of the
+    same generator) predicts n_out far better than the untrained network, so the learned
+    path sends far fewer clusters to the exact fallback at the same margin and needs a
+    smaller slab; C stays exact either way."""
+    import torch
+    from paper_2507_21253_gb300 import learned
+    params, loss = learned.train(lambda s: synth.planted_groups(2048 + 8 * (s % 7), 7000 + s), range(8),
+                                 epochs=30, batch=128, lr=3e-3)
+    loss = loss.cpu().numpy()
+    assert loss[-20:].mean() < 0.2 * loss[:20].mean()
+    A = synth.planted_groups(4096, 4100)
+    Ad, Acl, perm, cptr = clustered(sgc, A, how="hc")
+    X, y = learned.instance_data(A)
+    init = torch.from_numpy(synth.mlp_init(1)).cuda()
+    ok = y >= 0
+    err_t = (sgc.nnz_predictor_infer(params, X) - y)[ok].abs().mean().item()
+    err_u = (sgc.nnz_predictor_infer(init, X) - y)[ok].abs().mean().item()
+    assert err_t < 0.25 * err_u and err_t < 0.2
+    Lt = sgc.LearnedSpgemm(Acl, Ad, params=params, margin=1.25)
+    Lu = sgc.LearnedSpgemm(Acl, Ad, params=init, margin=1.25)
+    Ct, Cu = Lt.run(), Lu.run()
+    compare(Ct, A, A, exact_f64=True)
+    compare(Cu, A, A, exact_f64=True)
+    assert Lt.n_overflow < 0.1 * Acl.nclusters
+    assert Lt.n_overflow < Lu.n_overflow or Lt.slab_elems < Lu.slab_elems
+
+
+def test_checkpoint_round_trip(sgc, tmp_path):
+    import torch
+    from paper_2507_21253_gb300 import learned
+    p = torch.from_numpy(synth.mlp_init(5)).cuda()
+    f = str(tmp_path / "pred.bin")
+    learned.save(f, p, meta="planted")
+    assert torch.equal(learned.load(f), p)
