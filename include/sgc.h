@@ -264,6 +264,37 @@ int hcluster_reorder(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32
                      int64_t* nclusters_host, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched products and CUDA graphs (no counterpart in the paper, which
+ * motivates repeated SpGEMMs with betweenness centrality, Sec. 4.2).
+ *
+ * csr_batch_pack: k independent products A_i * B_i are one product of the
+ * block-diagonal matrices diag(A_i) * diag(B_i), whose result is diag(C_i);
+ * this packs k CSR matrices (host array `mats` of structs holding device
+ * pointers, one value type) into one block-diagonal CSR `out` whose arrays the
+ * caller allocated with nrows = sum nrows_i, ncols = sum ncols_i, nnz = sum
+ * nnz_i.  row_off / col_off (host, k+1 each) receive the block offsets: C_i is
+ * rows [row_off[i], row_off[i+1]) of the packed C, its columns shifted by the
+ * B blocks' column offsets.  Asynchronous (2k small launches + k copies).
+ *
+ * spgemm_graph_create: captures spgemm_symbolic (without the host read of
+ * nnz) followed by spgemm_numeric into one CUDA graph on `stream` (a created
+ * stream, not the legacy default stream) and instantiates it.  C must be
+ * allocated with the nnz a previous spgemm_symbolic on the same structure
+ * returned; the graph recomputes row pointer, columns and values on each
+ * launch, so values of A and B may change between launches, the structure
+ * may not.  All bins, grids and shared-memory classes are fixed at capture;
+ * the persistent kernels read their work counts on the device.
+ * spgemm_graph_launch / spgemm_graph_destroy: replay on a stream / free.
+ * ------------------------------------------------------------------------- */
+int csr_batch_pack(int32_t k, const sgc_csr* mats, sgc_csr* out, int64_t* row_off, int64_t* col_off,
+                   void* stream);
+typedef struct sgc_graph sgc_graph;
+int spgemm_graph_create(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, void* ws, size_t ws_bytes,
+                        const sgc_options* opt, void* stream, sgc_graph** graph);
+int spgemm_graph_launch(sgc_graph* graph, void* stream);
+int spgemm_graph_destroy(sgc_graph* graph);
+
+/* ---------------------------------------------------------------------------
  * Learned per-cluster output-column predictor and the symbolic-free path.
  * The paper has no predictor (its future work names learned choices, Sec. 5);
  * this library predicts, per cluster, n_out = the number of distinct output

@@ -717,4 +717,96 @@ int spgemm_learned_phase2(const sgc_csr_cluster* A, const sgc_csr* B, const int3
   return SGC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched products and CUDA graphs
+// ---------------------------------------------------------------------------
+int csr_batch_pack(int32_t k, const sgc_csr* mats, sgc_csr* out, int64_t* row_off, int64_t* col_off,
+                   void* stream) {
+  if (k < 0 || (k > 0 && !mats) || !out || !row_off || !col_off) SGC_FAIL(SGC_INVALID_ARG, "bad arguments");
+  int rc = check_csr(out, "out", true);
+  if (rc) return rc;
+  int64_t nr = 0, nc = 0, nz = 0;
+  row_off[0] = 0;
+  col_off[0] = 0;
+  for (int32_t i = 0; i < k; ++i) {
+    rc = check_csr(&mats[i], "mats[i]", true);
+    if (rc) return rc;
+    if (mats[i].dtype != out->dtype) SGC_FAIL(SGC_UNSUPPORTED, "all matrices need out's value type");
+    nr += mats[i].nrows;
+    nc += mats[i].ncols;
+    nz += mats[i].nnz;
+    row_off[i + 1] = nr;
+    col_off[i + 1] = nc;
+  }
+  if (nr != out->nrows || nc != out->ncols || nz != out->nnz)
+    SGC_FAIL(SGC_INVALID_ARG, "out must have the summed shape and nnz");
+  if (nc > 0x7fffffffll) SGC_FAIL(SGC_UNSUPPORTED, "packed column count must fit int32");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int vb = dtype_bytes(out->dtype);
+  int64_t zoff = 0;
+  SGC_CUDA(cudaMemsetAsync(out->row_ptr, 0, sizeof(int64_t), s));
+  for (int32_t i = 0; i < k; ++i) {
+    const sgc_csr& M = mats[i];
+    SGC_CUDA(add_offset_i64(M.row_ptr + 1, out->row_ptr + row_off[i] + 1, M.nrows, zoff, s));
+    SGC_CUDA(add_offset_i32(M.col, out->col + zoff, M.nnz, (int32_t)col_off[i], s));
+    if (M.nnz > 0)
+      SGC_CUDA(cudaMemcpyAsync((char*)out->val + zoff * vb, M.val, (size_t)M.nnz * vb, cudaMemcpyDeviceToDevice, s));
+    zoff += M.nnz;
+  }
+  return SGC_OK;
+}
+
+struct sgc_graph {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+int spgemm_graph_create(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, void* ws, size_t ws_bytes,
+                        const sgc_options* opt, void* stream, sgc_graph** graph) {
+  if (!graph || !stream) SGC_FAIL(SGC_INVALID_ARG, "graph output and a created stream are required");
+  int rc = check_product(A, B, true);
+  if (rc) return rc;
+  rc = check_csr(C, "C", true);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  // set kernel attributes outside the capture: one uncaptured run
+  rc = spgemm_symbolic(A, B, C->row_ptr, nullptr, ws, ws_bytes, opt, stream);
+  if (rc) return rc;
+  rc = spgemm_numeric(A, B, C, ws, ws_bytes, opt, stream);
+  if (rc) return rc;
+  SGC_CUDA(cudaStreamSynchronize(s));
+  SGC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc1 = spgemm_symbolic(A, B, C->row_ptr, nullptr, ws, ws_bytes, opt, stream);
+  int rc2 = rc1 ? rc1 : spgemm_numeric(A, B, C, ws, ws_bytes, opt, stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc2) {
+    if (g) cudaGraphDestroy(g);
+    return rc2;
+  }
+  if (e != cudaSuccess) SGC_FAIL(SGC_CUDA_ERROR, std::string("stream capture failed: ") + cudaGetErrorString(e));
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    SGC_FAIL(SGC_CUDA_ERROR, std::string("graph instantiate failed: ") + cudaGetErrorString(e));
+  }
+  *graph = new sgc_graph{g, x};
+  return SGC_OK;
+}
+
+int spgemm_graph_launch(sgc_graph* graph, void* stream) {
+  if (!graph) SGC_FAIL(SGC_INVALID_ARG, "graph is NULL");
+  SGC_CUDA(cudaGraphLaunch(graph->exec, (cudaStream_t)stream));
+  return SGC_OK;
+}
+
+int spgemm_graph_destroy(sgc_graph* graph) {
+  if (!graph) return SGC_OK;
+  cudaGraphExecDestroy(graph->exec);
+  cudaGraphDestroy(graph->graph);
+  delete graph;
+  return SGC_OK;
+}
+
 }  // extern "C"

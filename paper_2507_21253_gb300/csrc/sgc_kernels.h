@@ -106,6 +106,10 @@ cudaError_t validate_csr_run(const int64_t* rp, const int32_t* col, int64_t nrow
 cudaError_t validate_cluster_run(const AClusterView& A, int64_t ncols, void* status,
                                  cudaStream_t s);
 
+// k_batch.cu
+cudaError_t add_offset_i32(const int32_t* src, int32_t* dst, int64_t n, int32_t add, cudaStream_t s);
+cudaError_t add_offset_i64(const int64_t* src, int64_t* dst, int64_t n, int64_t add, cudaStream_t s);
+
 // k_learned.cu
 cudaError_t features_run(const AClusterView& A, const BView& B, float* X, int32_t* uc, int32_t* h_pos, int sms,
                          cudaStream_t s);

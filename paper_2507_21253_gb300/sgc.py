@@ -110,6 +110,11 @@ _c = {
                                   P(i64), vp, ctypes.c_size_t, P(Options), vp),
     "spgemm_learned_phase2": _sig("spgemm_learned_phase2", P(ClusterStruct), P(CsrStruct), vp, vp, P(CsrStruct), vp,
                                   ctypes.c_size_t, P(Options), vp),
+    "csr_batch_pack": _sig("csr_batch_pack", i32, vp, P(CsrStruct), vp, vp, vp),
+    "spgemm_graph_create": _sig("spgemm_graph_create", P(ClusterStruct), P(CsrStruct), P(CsrStruct), vp,
+                                ctypes.c_size_t, P(Options), vp, P(vp)),
+    "spgemm_graph_launch": _sig("spgemm_graph_launch", vp, vp),
+    "spgemm_graph_destroy": _sig("spgemm_graph_destroy", vp),
     "spgemm_rowwise_numeric": _sig("spgemm_rowwise_numeric", P(CsrStruct), P(CsrStruct), P(CsrStruct), vp,
                                    ctypes.c_size_t, P(Options), vp),
 }
@@ -478,3 +483,55 @@ class LearnedSpgemm:
         C = self.phase2()
         workspace_status(self.ws)
         return C
+
+
+# ---------------------------------------------------------------------------
+# batches and CUDA graphs
+# ---------------------------------------------------------------------------
+def csr_batch_pack(mats):
+    """Packs device CSR matrices into one block-diagonal DeviceCsr; returns (packed, row_off, col_off)."""
+    import numpy as np
+    k = len(mats)
+    dev = mats[0].row_ptr.device
+    nr = sum(m.nrows for m in mats)
+    nc = sum(m.ncols for m in mats)
+    nz = sum(m.nnz for m in mats)
+    out = DeviceCsr(nr, nc, torch.empty(nr + 1, dtype=torch.int64, device=dev),
+                    torch.empty(nz, dtype=torch.int32, device=dev), torch.empty(nz, dtype=mats[0].val.dtype, device=dev))
+    arr = (CsrStruct * k)(*[m.struct() for m in mats])
+    row_off = np.zeros(k + 1, dtype=np.int64)
+    col_off = np.zeros(k + 1, dtype=np.int64)
+    o = out.struct()
+    _call("csr_batch_pack", k, ctypes.cast(arr, vp), ctypes.byref(o), row_off.ctypes.data_as(vp),
+          col_off.ctypes.data_as(vp), _stream())
+    return out, row_off, col_off
+
+
+class SpgemmGraph:
+    """symbolic + numeric of one structure captured in a CUDA graph (replayable)."""
+
+    def __init__(self, A: DeviceCsrCluster, B: DeviceCsr, opt: Options | None = None, stream=None):
+        self.A, self.B, self.opt = A, B, opt
+        dev = B.row_ptr.device
+        self.ws = Workspace(spgemm_workspace_size(A, B, opt), dev)
+        rp, nnz = spgemm_symbolic(A, B, self.ws, opt)
+        self.C = DeviceCsr(A.nrows, B.ncols, rp, torch.empty(nnz, dtype=torch.int32, device=dev),
+                           torch.empty(nnz, dtype=B.val.dtype, device=dev))
+        self.stream = stream if stream is not None else torch.cuda.Stream(dev)
+        self.handle = vp()
+        a, b, c = A.struct(), B.struct(), self.C.struct()
+        torch.cuda.synchronize()
+        l0 = kernel_launches()
+        _call("spgemm_graph_create", ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), self.ws.ptr, self.ws.nbytes,
+              _o(opt), vp(self.stream.cuda_stream), ctypes.byref(self.handle))
+        # one uncaptured run and the captured one launch the same kernels
+        self.kernels_per_launch = (kernel_launches() - l0) // 2
+
+    def launch(self):
+        _call("spgemm_graph_launch", self.handle, vp(self.stream.cuda_stream))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _c["spgemm_graph_destroy"](h)
+            self.handle = None

@@ -73,6 +73,17 @@ class Stream:
         return np.argsort(self.u64(n), kind="stable").astype(np.int64)
 
 
+def _sorted_unique(x: np.ndarray) -> np.ndarray:
+    """Sorted distinct values (sort + adjacent compare)."""
+    x = np.sort(x, kind="stable")
+    if x.size == 0:
+        return x
+    keep = np.empty(x.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(x[1:], x[:-1], out=keep[1:])
+    return x[keep]
+
+
 @dataclass
 class Csr:
     """CSR matrix: int64 row pointer, int32 sorted unique column ids, values."""
@@ -96,7 +107,7 @@ class Csr:
 def csr_from_pattern(nrows: int, ncols: int, rows: np.ndarray, cols: np.ndarray) -> Csr:
     """Sorted CSR pattern (duplicates merged) from coordinate lists; values left empty."""
     key = rows.astype(np.int64) * ncols + cols.astype(np.int64)
-    key = np.unique(key)
+    key = _sorted_unique(key)
     r = key // ncols
     c = (key - r * ncols).astype(np.int32)
     counts = np.bincount(r, minlength=nrows)
@@ -258,24 +269,43 @@ def powerlaw_xmin() -> float:
 
 
 def _sample_rows_without_replacement(n: int, ncols: int, lens: np.ndarray, rs: Stream) -> Csr:
-    """Each row i gets lens[i] distinct uniform columns in [0, ncols)."""
+    """Each row i gets lens[i] distinct uniform columns in [0, ncols).
+
+    Rows with lens[i] > ncols/4 take a prefix of a random permutation.  The other
+    rows draw an oversample with replacement, drop repeats, and keep lens[i] of
+    the distinct draws chosen by random priority (a uniform lens[i]-subset, by
+    symmetry over column labels); a row short of distinct draws is redrawn."""
     lens = np.minimum(lens.astype(np.int64), ncols)
     rows_all, cols_all = [], []
     dense = lens * 4 > ncols
-    for i in np.nonzero(dense)[0]:           # long rows: prefix of a random permutation
+    for i in np.nonzero(dense)[0]:
         cols_all.append(rs.permutation(ncols)[: lens[i]])
         rows_all.append(np.full(lens[i], i, dtype=np.int64))
-    sparse_rows = np.nonzero(~dense)[0]
-    need = lens[sparse_rows].copy()
-    have_key = np.zeros(0, dtype=np.int64)
-    while need.sum() > 0:
-        r = np.repeat(sparse_rows, need)
-        c = rs.randint(ncols, int(need.sum()))
-        have_key = np.unique(np.concatenate([have_key, r * ncols + c]))
-        got = np.bincount(have_key // ncols, minlength=n)[sparse_rows]
-        need = lens[sparse_rows] - got
-    rows_all.append(have_key // ncols)
-    cols_all.append(have_key % ncols)
+    todo = np.nonzero(~dense & (lens > 0))[0]
+    factor = 1.3
+    while todo.size:
+        want = lens[todo]
+        m = np.ceil(want * factor).astype(np.int64) + 4
+        r = np.repeat(todo, m)
+        c = rs.randint(ncols, int(m.sum()))
+        key = _sorted_unique(r * ncols + c)
+        kr = key // ncols
+        prio = rs.u64(key.size)
+        order = np.lexsort((prio, kr))
+        key, kr = key[order], kr[order]
+        start = np.searchsorted(kr, kr, side="left")
+        rank = np.arange(kr.size) - start
+        got = np.bincount(kr, minlength=n)
+        ok = got[todo] >= want
+        okrows = np.zeros(n, dtype=bool)
+        okrows[todo[ok]] = True
+        keep = okrows[kr] & (rank < lens[kr])
+        rows_all.append(kr[keep])
+        cols_all.append(key[keep] % ncols)
+        todo = todo[~ok]
+        factor *= 1.5
+    if not rows_all:
+        return csr_from_pattern(n, ncols, np.zeros(0, np.int64), np.zeros(0, np.int64))
     return csr_from_pattern(n, ncols, np.concatenate(rows_all), np.concatenate(cols_all))
 
 
@@ -333,6 +363,21 @@ def planted_training_size(seed: int) -> int:
     rs = Stream(seed, 404)
     n = int(math.floor(math.exp(math.log(2 ** 14) + rs.uniform(1)[0] * (math.log(2 ** 18) - math.log(2 ** 14)))))
     return n - n % 8
+
+
+def block_diag(mats: list) -> Csr:
+    """Block-diagonal CSR of the given matrices (rows and columns offset per block)."""
+    rp = [np.zeros(1, dtype=np.int64)]
+    cols, vals = [], []
+    zoff = coff = 0
+    for M in mats:
+        rp.append(M.row_ptr[1:] + zoff)
+        cols.append(M.col.astype(np.int64) + coff)
+        vals.append(M.val)
+        zoff += M.nnz
+        coff += M.ncols
+    return Csr(sum(M.nrows for M in mats), coff, np.concatenate(rp), np.concatenate(cols).astype(np.int32),
+               np.concatenate(vals))
 
 
 # --------------------------------------------------------------------------
