@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--fused-fma", type=int, default=0, help="FP64: accumulate with fused multiply-add")
+    ap.add_argument("--cluster-load", type=int, default=0, help="numeric cluster-table fill limit, percent (0: default)")
     ap.add_argument("--batch", type=int, default=256, help="products in the batched workload")
     return ap.parse_args()
 
@@ -252,7 +253,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
 
-    opt = sgc.options(fused_fma=args.fused_fma)
+    opt = sgc.options(fused_fma=args.fused_fma, cluster_load_pct=args.cluster_load)
     ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad, opt), dev)
     rp, nnz = sgc.spgemm_symbolic(Acl, Ad, ws, opt)
     C = sgc.spgemm_numeric(Acl, Ad, rp, nnz, ws, opt)

@@ -25,8 +25,8 @@
  *    row, structural entries whose value cancels to zero kept (the symbolic
  *    structure of Sec. 2.2).  FP32 products are accumulated in FP64 and
  *    rounded once; FP64 accumulates in ascending k per (i, j), without FMA
- *    unless sgc_options.fused_fma = 1, except rows with more than 3072 outputs
- *    (see SGC_HEAVY_ROW_OUTPUTS); int64 wraps modulo 2^64.
+ *    unless sgc_options.fused_fma = 1, except rows computed row by row with
+ *    more than 768 outputs (see SGC_HEAVY_ROW_OUTPUTS); int64 wraps modulo 2^64.
  *  - Errors: SGC_INVALID_ARG (null pointer, negative or inconsistent size),
  *    SGC_UNSUPPORTED (dtype mismatch, cluster larger than 32 rows),
  *    SGC_WORKSPACE_TOO_SMALL, SGC_CUDA_ERROR (a CUDA call failed; the CUDA
@@ -72,11 +72,15 @@ enum {
   SGC_STAGING_LDG = 2   /* cooperative vector loads by the CTA's threads */
 };
 
-/* A row with more outputs than this (more than 6144 possible outputs in the
- * symbolic phase) is a heavy row: one CTA per row, dense accumulator over
- * column windows, shared-memory atomics (FP64 values then depend on the
- * order of atomic adds, within the FP64 bound; int64 exact). */
-#define SGC_HEAVY_ROW_OUTPUTS 3072
+/* Rows computed row by row (the row-wise method, and rows of clusters too
+ * large for the cluster kernel) use one warp and a per-warp hash table up to
+ * 768 outputs; above that one CTA and a CTA-wide hash table updated with
+ * shared-memory atomics; above SGC_HEAVY_ROW_OUTPUTS outputs (4x that many
+ * possible outputs in the symbolic phase) a heavy-row CTA with a dense
+ * accumulator over column windows, also with atomics.  FP64 values of rows
+ * with more than 768 outputs therefore depend on the order of atomic adds,
+ * within the FP64 bound; int64 stays exact. */
+#define SGC_HEAVY_ROW_OUTPUTS 6144
 
 /* CSR matrix (Sec. 2.1: row-id / col-id / value arrays). */
 typedef struct sgc_csr {
@@ -120,7 +124,9 @@ typedef struct sgc_options {
                                term; within the FP64 bound, not bit-identical to separate rounding);
                                0 (default) = product and sum rounded separately.  FP32 inputs always
                                use the fused form: their FP64 products are exact, so it changes nothing. */
-  int32_t reserved[10];
+  int32_t cluster_load_pct; /* fill limit of the numeric cluster kernel's column table, in percent of its
+                               slots; 0 = default 50; 20..75.  Lower: fewer probes, more shared memory. */
+  int32_t reserved[9];
 } sgc_options;
 
 /* Version of this ABI (SGC_ABI_VERSION). */

@@ -39,6 +39,9 @@ ResolvedOptions resolve(const sgc_options* opt) {
   if (r.load_pct < 25) r.load_pct = 25;
   if (r.load_pct > 90) r.load_pct = 90;
   r.fused = (opt && opt->fused_fma) ? 1 : 0;
+  r.cl_load = (opt && opt->cluster_load_pct > 0) ? opt->cluster_load_pct : NUM_TABLE_LOAD;
+  if (r.cl_load < 20) r.cl_load = 20;
+  if (r.cl_load > 75) r.cl_load = 75;
   return r;
 }
 
@@ -639,7 +642,7 @@ int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_pr
   if (!pred->ncap) SGC_CUDA(mlp_infer_run(pred->params, w.X, A->nclusters, w.yhat, sms, s));
   const int inb = dtype_bytes(A->dtype);
   SGC_CUDA(learned_bin_run(av, bv, w.yhat, pred->ncap, pred->margin, pred->scale, w.sp.bins.uc_rec, w.h_pos, w.ncap,
-                           w.slab_off, w.flag, w.flist, w.flist_count, w.lb, inb, 8, mode, sms, s));
+                           w.slab_off, w.flag, w.flist, w.flist_count, w.lb, inb, 8, mode, o.cl_load, sms, s));
   SGC_CUDA(inclusive_scan_i64(w.slab_off + 1, A->nrows, w.sp.scan_tmp, s));
   SGC_CUDA(cudaMemcpyAsync(w.flist_plan, w.flist_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   SGC_CUDA(cudaMemcpyAsync(slab_elems_host, w.slab_off + A->nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

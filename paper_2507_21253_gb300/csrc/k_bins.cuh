@@ -27,13 +27,13 @@ __device__ __forceinline__ void push_heavy(const BinOut& o, int64_t item) {
 
 // Classify one row by its bound h (symbolic) or exact count (numeric); h > 0.
 __device__ __forceinline__ void classify_row(const BinOut& o, int64_t item, int64_t h, int64_t heavy_limit,
-                                             int load_pct) {
+                                             int load_pct, int lg_max) {
   if (h > heavy_limit) {
     push_heavy(o, item);
     return;
   }
   const int lg = table_log2(h, load_pct);
-  if (lg > LOG2T_MAX)
+  if (lg > lg_max)
     push_heavy(o, item);
   else
     push_row(o, lg, item);
@@ -71,7 +71,7 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
     int cls = -1;
     if (use_dense && U < (1ll << 28) && T < (1ll << 24)) {
       const int64_t nb = min64(U, B.ncols);
-      const WarpLayout L = warp_layout(true, T, U, 0, cluster_table_log2(true, nb), nb, K, 4, 8, bulk != 0);
+      const WarpLayout L = warp_layout(true, T, U, 0, cluster_table_log2(true, nb, 0), nb, K, 4, 8, bulk != 0);
       cls = warp_class(L.total);
     }
     if (lane == 0) {
@@ -85,7 +85,7 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
       if (ub == 0)
         c_rp[row + 1] = 0;
       else
-        classify_row(o, (c << 5) | lane, min64(ub, B.ncols), HEAVY_SYM, load_pct);
+        classify_row(o, (c << 5) | lane, min64(ub, B.ncols), HEAVY_SYM, load_pct, SYM_LG_MAX);
     }
     __syncwarp();
   }
@@ -93,7 +93,8 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
 
 // ---- cluster path, numeric: warp per cluster -------------------------------
 static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, BView B, const int64_t* c_rp, BinOut o,
-                                                         int load_pct, int bulk, int in_bytes, int acc_bytes) {
+                                                         int load_pct, int bulk, int in_bytes, int acc_bytes,
+                                                         int cl_load) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   const int64_t nitems = o.clist ? (int64_t)*o.clist_count : A.ncl;
@@ -107,7 +108,8 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, 
     if (nout >= 0) {
       const int64_t nva = A.vptr[c + 1] - A.vptr[c];
       const WarpLayout L =
-          warp_layout(false, T, o.uc_rec[c], nva, cluster_table_log2(false, nout), nout, K, in_bytes, acc_bytes, bulk != 0);
+          warp_layout(false, T, o.uc_rec[c], nva, cluster_table_log2(false, nout, cl_load), nout, K, in_bytes, acc_bytes,
+                      bulk != 0);
       cls = warp_class(L.total);
     }
     if (cls >= 0) {
@@ -115,13 +117,14 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, 
     } else if (lane < K) {
       const int64_t row = A.perm[p0 + lane];
       const int64_t cnt = c_rp[row + 1] - c_rp[row];
-      if (cnt > 0) classify_row(o, (c << 5) | lane, cnt, HEAVY_NUM, load_pct);
+      if (cnt > 0) classify_row(o, (c << 5) | lane, cnt, HEAVY_NUM, load_pct, NUM_LG_MAX);
     }
   }
 }
 
 // ---- row-wise path, symbolic: warp per row ---------------------------------
-static __global__ void __launch_bounds__(256) k_bin_rows_sym(ACsrView A, BView B, int64_t* c_rp, BinOut o, int load_pct) {
+static __global__ void __launch_bounds__(256) k_bin_rows_sym(ACsrView A, BView B, int64_t* c_rp, BinOut o, int load_pct,
+                                                              int64_t heavy_limit, int lg_max) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   for (int64_t r = gw; r < A.nrows; r += nwarps) {
@@ -135,7 +138,7 @@ static __global__ void __launch_bounds__(256) k_bin_rows_sym(ACsrView A, BView B
       if (ub == 0)
         c_rp[r + 1] = 0;
       else
-        classify_row(o, r, min64(ub, B.ncols), HEAVY_SYM, load_pct);
+        classify_row(o, r, min64(ub, B.ncols), heavy_limit, load_pct, lg_max);
     }
   }
 }
@@ -144,7 +147,7 @@ static __global__ void __launch_bounds__(256) k_bin_rows_sym(ACsrView A, BView B
 static __global__ void __launch_bounds__(256) k_bin_rows_num(int64_t nrows, const int64_t* c_rp, BinOut o, int load_pct) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
     const int64_t cnt = c_rp[r + 1] - c_rp[r];
-    if (cnt > 0) classify_row(o, r, cnt, HEAVY_NUM, load_pct);
+    if (cnt > 0) classify_row(o, r, cnt, HEAVY_NUM, load_pct, NUM_LG_MAX);
   }
 }
 

@@ -38,11 +38,11 @@ __host__ __device__ inline int warp_class_bytes(int b) {
 // Hash-table fill limits of the cluster kernel.  The symbolic table is sized by
 // the bound min(U, ncols(B)) on the cluster's output columns, so its real fill
 // is usually far lower; the numeric table is sized by the exact count from the
-// symbolic phase and kept sparse so that most lookups take one probe.
+// symbolic phase (fill limit num_load, an option: sparser tables take fewer
+// probes but more shared memory).
 constexpr int SYM_TABLE_LOAD = 75;
-constexpr int NUM_TABLE_LOAD = 30;
-__host__ __device__ inline int cluster_table_log2(bool sym, int64_t nb) {
-  return table_log2(nb, sym ? SYM_TABLE_LOAD : NUM_TABLE_LOAD);
+__host__ __device__ inline int cluster_table_log2(bool sym, int64_t nb, int num_load) {
+  return table_log2(nb, sym ? SYM_TABLE_LOAD : num_load);
 }
 
 struct WarpLayout {
@@ -80,13 +80,15 @@ __host__ __device__ inline WarpLayout warp_layout(bool sym, int64_t T, int64_t U
   } else {
     L.sorted = (int)o;
     o += 4 * nout;
-    L.scratch = (int)o;  // bucket starts, cursors, compacted keys, their slots
-    o += 16 * nout + 16;
     o = (o + 15) & ~15ll;
+    // the ranking scratch (bucket starts, cursors, compacted keys, their slots:
+    // 16 * nout + 16 bytes) is dead before the accumulators are zeroed: alias them
     L.acc = (int)o;
-    o += (int64_t)acc_bytes * K * nout;
-    L.flags = (int)o;
-    o += (int64_t)K * nout;
+    L.scratch = (int)o;
+    const int64_t accb = (int64_t)acc_bytes * K * nout;
+    L.flags = (int)(o + accb);
+    const int64_t region = accb + (int64_t)K * nout;
+    o += region > 16 * nout + 16 ? region : 16 * nout + 16;
   }
   o = (o + 15) & ~15ll;
   L.total = o > (1 << 30) ? (1 << 30) : (int)o;
@@ -178,11 +180,11 @@ __device__ __forceinline__ uint64_t group_excl_scan64(uint64_t v, int gw, int gi
 }
 
 template <bool SYM, int DT>
-__global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BView B, CView C, int64_t* c_rp_sym,
+__global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A, BView B, CView C, int64_t* c_rp_sym,
                                                               const int32_t* items, const int32_t* count_ptr,
                                                               int32_t* nout_rec, const int32_t* uc_rec, int mode,
-                                                              int region_bytes, int gw, int fused, LearnedOut lo,
-                                                              void* status) {
+                                                              int region_bytes, int gw, int fused, int cl_load,
+                                                              LearnedOut lo, void* status) {
   using In = typename VT<DT>::In;
   using Acc = typename VT<DT>::Acc;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -218,8 +220,12 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
     const int64_t U = uc_rec[c];
     // output columns: bound (symbolic), exact count (numeric) or predicted capacity (learned)
     const int64_t nb = SYM ? min64(U, B.ncols) : (lo.active ? (int64_t)lo.ncap[c] : (int64_t)nout_rec[c]);
-    const int LH = cluster_table_log2(SYM, nb);
+    const int LH = cluster_table_log2(SYM, nb, cl_load);
     const WarpLayout Ly = warp_layout(SYM, T, U, SYM ? 0 : nva, LH, nb, K, sizeof(In), sizeof(Acc), bulk);
+    if (Ly.total > region_bytes) {  // binned with other options than this launch's: refuse, do not overflow
+      if (gt == 0) raise(st, DEV_INTERNAL, 35, c);
+      continue;
+    }
     WDesc d;
     d.off_c = (int32_t*)(my + Ly.desc);
     d.off_v = d.off_c + T;
@@ -523,6 +529,7 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_group(AClusterView A, BV
         const int dc = d.off_c[i] & 0x7fffffff;
         for (int q = lane; q < n; q += 32) stage_c[dc + q] = table[stage_c[dc + q]];
       }
+      group_sync(gw, gid);  // the ranking scratch is read up to here; the accumulators alias it
       Acc* acc = (Acc*)(my + Ly.acc);
       uint8_t* flg = (uint8_t*)(my + Ly.flags);
       for (int64_t x = gt; x < (int64_t)K * n_out; x += GT) {

@@ -248,7 +248,7 @@ cudaError_t hc_candidates_run(const int64_t* arp, const int32_t* acol, int64_t n
   if (e != cudaSuccess) return e;
   const ACsrView av{arp, acol, nullptr, nrows};
   const BView atv{trp, tcol, nullptr, ncols, nrows, nnz};
-  k_bin_rows_sym<<<g, 256, 0, s>>>(av, atv, dummy_rp, bins, 75);
+  k_bin_rows_sym<<<g, 256, 0, s>>>(av, atv, dummy_rp, bins, 75, TOPK_HEAVY, TOPK_LG_MAX);
   note_launches(1);
   // rows with no overlap at all produce no candidates: fill all outputs with -1 first
   e = cudaMemsetAsync(cj, 0xff, sizeof(int32_t) * nrows * topk, s);
@@ -263,7 +263,7 @@ cudaError_t hc_candidates_run(const int64_t* arp, const int32_t* acol, int64_t n
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  for (int lg = LOG2T_MIN; lg <= LOG2T_MAX; ++lg) {
+  for (int lg = LOG2T_MIN; lg <= TOPK_LG_MAX; ++lg) {
     const size_t per_warp = (size_t)12 << lg;
     int warps = 8;
     while (warps > 1 && (size_t)warps * per_warp > (size_t)SMEM_MAX) --warps;

@@ -28,28 +28,40 @@ inline unsigned grid_for(int64_t units, int64_t per_cta, int sms, int occ) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
-// Launch the row-hash and heavy kernels for all row bins.
+// Launch the row kernels for all row bins: warp per row up to WARP_LG_MAX,
+// CTA per row (one shared table) above, dense-window CTAs for heavy rows.
 template <bool SYM, int DT, int SRC>
 cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const BView& B, const CView& C,
                             int64_t* c_rp, const BinOut& bins, void* status, const Launch& L) {
   using Acc = typename VT<DT>::Acc;
   auto kh = k_row_hash<SYM, DT, SRC>;
+  auto kb = k_row_block<SYM, DT, SRC>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = allow_smem(kh);
+    if (e == cudaSuccess) e = allow_smem(kb);
     if (e != cudaSuccess) return e;
   }
-  for (int lg = LOG2T_MIN; lg <= LOG2T_MAX; ++lg) {
+  const int lg_top = SYM ? SYM_LG_MAX : NUM_LG_MAX;
+  for (int lg = LOG2T_MIN; lg <= lg_top; ++lg) {
+    const int b = lg - LOG2T_MIN;
+    const int64_t* items = bins.row_items + (int64_t)b * bins.nrows;
+    const int32_t* cnt = bins.count + NDB + b;
+    if (lg > WARP_LG_MAX) {
+      const size_t smem = row_block_smem(lg, SYM, sizeof(Acc));
+      const int occ = occupancy(kb, BLOCK_ROW_THREADS, smem);
+      const unsigned grid = grid_for(bins.nrows, 1, L.sms, occ);
+      kb<<<grid, BLOCK_ROW_THREADS, smem, L.s>>>(Ac, Acl, B, C, c_rp, items, cnt, lg, status);
+      note_launches(1);
+      continue;
+    }
     const size_t per_warp = row_hash_smem(1, lg, SYM, sizeof(Acc));
     int warps = L.o.max_warps;
     while (warps > 1 && (size_t)warps * per_warp > (size_t)SMEM_MAX) --warps;
-    if ((size_t)warps * per_warp > (size_t)SMEM_MAX) continue;  // cannot happen for lg <= 13
     const size_t smem = (size_t)warps * per_warp;
     const int occ = occupancy(kh, warps * 32, smem);
     const unsigned grid = grid_for(bins.nrows, warps, L.sms, occ);
-    const int b = lg - LOG2T_MIN;
-    kh<<<grid, warps * 32, smem, L.s>>>(Ac, Acl, B, C, c_rp, bins.row_items + (int64_t)b * bins.nrows,
-                                         bins.count + NDB + b, lg, L.o.fused, status);
+    kh<<<grid, warps * 32, smem, L.s>>>(Ac, Acl, B, C, c_rp, items, cnt, lg, L.o.fused, status);
     note_launches(1);
   }
   auto kv = k_row_heavy<SYM, DT, SRC>;
@@ -78,7 +90,7 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
     k_bin_cluster_sym<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, 1);
   else
     k_bin_cluster_num<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, (int)sizeof(In),
-                                            (int)sizeof(Acc));
+                                            (int)sizeof(Acc), L.o.cl_load);
   note_launches(1);
   auto kd = k_cluster_group<SYM, DT>;
   static bool attr = false;
@@ -95,8 +107,8 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
     const int occ = occupancy(kd, threads, smem);
     const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
     kd<<<grid, threads, smem, L.s>>>(A, B, C, c_rp, bins.dense_items + (int64_t)b * bins.ncl, bins.count + b,
-                                      bins.nout_rec, bins.uc_rec, L.mode, rbytes, gw, L.o.fused, LearnedOut{},
-                                      status);
+                                      bins.nout_rec, bins.uc_rec, L.mode, rbytes, gw, L.o.fused, L.o.cl_load,
+                                      LearnedOut{}, status);
     note_launches(1);
   }
   e = cudaGetLastError();
@@ -123,8 +135,8 @@ cudaError_t run_cluster_learned(const AClusterView& A, const BView& B, const Bin
     const int occ = occupancy(kd, threads, smem);
     const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
     kd<<<grid, threads, smem, L.s>>>(A, B, CView{}, nullptr, lbins.dense_items + (int64_t)b * lbins.ncl,
-                                      lbins.count + b, nullptr, lbins.uc_rec, L.mode, rbytes, gw, L.o.fused, lo,
-                                      status);
+                                      lbins.count + b, nullptr, lbins.uc_rec, L.mode, rbytes, gw, L.o.fused,
+                                      L.o.cl_load, lo, status);
     note_launches(1);
   }
   return cudaGetLastError();
@@ -137,7 +149,7 @@ cudaError_t run_rows_phase(const ACsrView& A, const BView& B, const CView& C, in
   if (e != cudaSuccess) return e;
   if (SYM) {
     const unsigned gb = grid_for(A.nrows, 8, L.sms, 8);
-    k_bin_rows_sym<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct);
+    k_bin_rows_sym<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, HEAVY_SYM, SYM_LG_MAX);
     note_launches(1);
   } else {
     const unsigned gb = grid_for(A.nrows, 256, L.sms, 8);

@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, co
                                                      float margin, float scale, const int32_t* uc, const int32_t* h_pos,
                                                      int32_t* ncap_out, int64_t* capw, int32_t* flag, int32_t* flist,
                                                      int32_t* flist_count, BinOut lb, int in_bytes, int acc_bytes,
-                                                     int bulk) {
+                                                     int bulk, int cl_load) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   for (int64_t c = gw; c < A.ncl; c += nwarps) {
@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, co
     int cls = -1;
     if (U < (1ll << 28) && T < (1ll << 24)) {
       const WarpLayout L =
-          warp_layout(false, T, U, nva, cluster_table_log2(false, ncap), ncap, K, in_bytes, acc_bytes, bulk != 0);
+          warp_layout(false, T, U, nva, cluster_table_log2(false, ncap, cl_load), ncap, K, in_bytes, acc_bytes,
+                      bulk != 0);
       cls = warp_class(L.total);
     }
     if (lane == 0) {
@@ -310,7 +311,7 @@ cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, 
 cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const int32_t* ncap_in,
                             float margin, float scale, const int32_t* uc, const int32_t* h_pos, int32_t* ncap_out,
                             int64_t* capw, int32_t* flag, int32_t* flist, int32_t* flist_count, const BinOut& lb,
-                            int in_bytes, int acc_bytes, int bulk, int sms, cudaStream_t s) {
+                            int in_bytes, int acc_bytes, int bulk, int cl_load, int sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(lb.count, 0, sizeof(int32_t) * NBIN_ALL, s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(flist_count, 0, sizeof(int32_t), s);
@@ -320,7 +321,7 @@ cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* 
   if (A.ncl <= 0) return cudaSuccess;
   k_learned_bin<<<grid_for(A.ncl, 8, sms, 8), 256, 0, s>>>(A, B, yhat, ncap_in, margin, scale, uc, h_pos, ncap_out,
                                                             capw, flag, flist, flist_count, lb, in_bytes, acc_bytes,
-                                                            bulk);
+                                                            bulk, cl_load);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -316,6 +316,214 @@ __device__ __forceinline__ void gather_chunk(const ACsrView& Ac, const AClusterV
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Medium rows: one CTA per row and one hash table for the whole CTA (the hash
+// accumulator of the row-wise method at CTA scale).  The products of a chunk
+// of the row's entries are spread evenly over the threads: thread p takes
+// product p of the chunk, located by a binary search over the chunk's prefix
+// of B row lengths, so long and short B rows cost the same per product.  Keys
+// go in with shared-memory CAS, values with shared-memory atomic adds.  The
+// numeric result is ranked straight out of the table by the interpolated
+// bucket ranking, permuted into column order in shared memory and written
+// with coalesced stores.
+// Shared memory: header (scan scratch, chunk keys, values, prefix, offsets),
+// keys[T], and for numeric vals[T] plus 3*T ints of ranking scratch.
+// ---------------------------------------------------------------------------
+constexpr int BLOCK_ROW_THREADS = 512;
+constexpr int BLOCK_ROW_SPT = 16;  // table slots a thread ranks (numeric T <= 16 * threads)
+constexpr size_t BLOCK_ROW_HEAD = 512 + (size_t)BLOCK_ROW_THREADS * (4 + 8) + 8 * (size_t)(BLOCK_ROW_THREADS + 8) +
+                                  8 * (size_t)BLOCK_ROW_THREADS;
+
+template <bool SYM, int DT, int SRC>
+__global__ void __launch_bounds__(BLOCK_ROW_THREADS, 2) k_row_block(ACsrView Ac, AClusterView Acl, BView B, CView C,
+                                                                 int64_t* c_rp_sym, const int64_t* items,
+                                                                 const int32_t* count_ptr, int log2T, void* status) {
+  using In = typename VT<DT>::In;
+  using Acc = typename VT<DT>::Acc;
+  extern __shared__ __align__(16) unsigned char sm[];
+  int64_t* tmp = (int64_t*)sm;                      // 34 int64: block scans
+  int* s_misc = (int*)(sm + 34 * 8);                // [0] chunk size, [1] table full, [2] kmin, [3] kmax
+  int64_t* s_run = (int64_t*)(sm + 34 * 8 + 16);    // running MASKED offset
+  int32_t* s_k = (int32_t*)(sm + 512);
+  In* s_a = (In*)(sm + 512 + 4 * BLOCK_ROW_THREADS);
+  int64_t* s_pre = (int64_t*)(sm + 512 + 12 * BLOCK_ROW_THREADS);
+  int64_t* s_off = s_pre + BLOCK_ROW_THREADS + 8;
+  const int T = 1 << log2T;
+  int32_t* keys = (int32_t*)(sm + BLOCK_ROW_HEAD);
+  Acc* vals = (Acc*)(sm + BLOCK_ROW_HEAD + 4 * (size_t)T);
+  int32_t* bst = (int32_t*)(sm + BLOCK_ROW_HEAD + (4 + sizeof(Acc)) * (size_t)T);
+  int32_t* bcur = bst + T;
+  int32_t* srt = bcur + T;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  DevStatus* st = (DevStatus*)status;
+  const int32_t count = *count_ptr;
+  for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
+    const int64_t item = items[it];
+    const int64_t row = item_row<SRC>(Acl, item);
+    int64_t nent;
+    if constexpr (SRC == SRC_CSR) {
+      nent = Ac.rp[item + 1] - Ac.rp[item];
+    } else {
+      const int64_t c = item >> 5;
+      nent = Acl.uptr[c + 1] - Acl.uptr[c];
+    }
+    for (int i = tid; i < T; i += nt) {
+      keys[i] = EMPTY_KEY;
+      if (!SYM) vals[i] = Acc(0);
+    }
+    if (tid == 0) {
+      *s_run = 0;
+      s_misc[1] = 0;
+      s_misc[2] = PAD_KEY;
+      s_misc[3] = -1;
+    }
+    __syncthreads();
+    int64_t cnt = 0;
+    bool full = false;
+    for (int64_t cb = 0; cb < nent; cb += nt) {
+      gather_chunk<DT>(Ac, Acl, SRC, item, cb, s_k, s_a, tmp, &s_misc[0], s_run);
+      const int n = s_misc[0];
+      int64_t bs = 0, len = 0;
+      if (tid < n) {
+        const int32_t k = s_k[tid];
+        bs = B.rp[k];
+        len = B.rp[k + 1] - bs;
+      }
+      int64_t P;
+      const int64_t pre = block_excl_scan<int64_t>(len, tmp, &P);
+      if (tid < n) {
+        s_pre[tid] = pre;
+        s_off[tid] = bs - pre;
+      }
+      __syncthreads();
+      int e0 = 0;  // entry of the previous product: the search starts there
+      for (int64_t p = tid; p < P && !full; p += nt) {
+        int hi = n - 1;
+        while (e0 < hi) {
+          const int mid = (e0 + hi + 1) >> 1;
+          if (s_pre[mid] <= p) e0 = mid; else hi = mid - 1;
+        }
+        const int64_t q = s_off[e0] + p;
+        bool nw;
+        const int slot = hash_find_or_insert(keys, log2T, B.col[q], &nw);
+        if (slot < 0) {
+          full = true;
+          break;
+        }
+        if constexpr (SYM) {
+          cnt += nw;
+        } else {
+          VT<DT>::atomic_add(&vals[slot], VT<DT>::mul(s_a[e0], ((const In*)B.val)[q]));
+        }
+      }
+      __syncthreads();
+    }
+    if (full) s_misc[1] = 1;
+    __syncthreads();
+    if (s_misc[1]) {
+      if (tid == 0) raise(st, DEV_TABLE_FULL, 12, row);
+      __syncthreads();
+      continue;
+    }
+    if constexpr (SYM) {
+      int64_t tot;
+      block_excl_scan<int64_t>(cnt, tmp, &tot);
+      if (tid == 0) c_rp_sym[row + 1] = tot;
+    } else {
+      const int64_t out0 = C.rp[row], expect = C.rp[row + 1] - out0;
+      int c = 0;
+      int32_t kmin = PAD_KEY, kmax = -1;
+      for (int i = tid; i < T; i += nt) {
+        const int32_t k = keys[i];
+        if (k != EMPTY_KEY) {
+          ++c;
+          kmin = min(kmin, k);
+          kmax = max(kmax, k);
+        }
+      }
+      kmin = warp_min(kmin);
+      kmax = warp_max(kmax);
+      if (lane_id() == 0) {
+        atomicMin(&s_misc[2], kmin);
+        atomicMax(&s_misc[3], kmax);
+      }
+      int64_t n64;
+      block_excl_scan<int64_t>(c, tmp, &n64);
+      const int n = (int)n64;
+      if (n != expect || n == 0 || T > BLOCK_ROW_SPT * nt) {
+        if (tid == 0 && (n != expect || T > BLOCK_ROW_SPT * nt)) raise(st, DEV_INTERNAL, 13, row);
+        __syncthreads();
+        continue;
+      }
+      kmin = s_misc[2];
+      kmax = s_misc[3];
+      const uint64_t range = (uint64_t)((int64_t)kmax - (int64_t)kmin + 1);
+      for (int x = tid; x < n; x += nt) bst[x] = 0;
+      __syncthreads();
+      for (int i = tid; i < T; i += nt) {
+        const int32_t k = keys[i];
+        if (k != EMPTY_KEY) atomicAdd(&bst[interp_bucket(k, kmin, n, range)], 1);
+      }
+      __syncthreads();
+      // exclusive scan of the n bucket sizes: each thread a contiguous segment
+      const int per = (n + nt - 1) / nt;
+      const int x0 = min(tid * per, n), x1 = min(x0 + per, n);
+      int64_t seg = 0;
+      for (int x = x0; x < x1; ++x) seg += bst[x];
+      int64_t tot;
+      int64_t run = block_excl_scan<int64_t>(seg, tmp, &tot);
+      for (int x = x0; x < x1; ++x) {
+        const int v = bst[x];
+        bst[x] = (int)run;
+        bcur[x] = (int)run;
+        run += v;
+      }
+      __syncthreads();
+      for (int i = tid; i < T; i += nt) {
+        const int32_t k = keys[i];
+        if (k != EMPTY_KEY) srt[atomicAdd(&bcur[interp_bucket(k, kmin, n, range)], 1)] = k;
+      }
+      __syncthreads();
+      int rk[BLOCK_ROW_SPT];
+#pragma unroll
+      for (int j = 0; j < BLOCK_ROW_SPT; ++j) {
+        const int i = tid + j * nt;
+        rk[j] = -1;
+        if (i < T) {
+          const int32_t k = keys[i];
+          if (k != EMPTY_KEY) {
+            const int b = interp_bucket(k, kmin, n, range);
+            int r = bst[b];
+            for (int y = bst[b], ye = bcur[b]; y < ye; ++y) r += srt[y] < k;
+            rk[j] = r;
+          }
+        }
+      }
+      __syncthreads();
+      // permute into column order: keys into srt, values over bst/bcur (8 bytes a slot)
+      Acc* sv = (Acc*)bst;
+#pragma unroll
+      for (int j = 0; j < BLOCK_ROW_SPT; ++j) {
+        const int i = tid + j * nt;
+        if (rk[j] >= 0) {
+          srt[rk[j]] = keys[i];
+          sv[rk[j]] = vals[i];
+        }
+      }
+      __syncthreads();
+      for (int x = tid; x < n; x += nt) {
+        C.col[out0 + x] = srt[x];
+        ((In*)C.val)[out0 + x] = VT<DT>::out(sv[x]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+inline size_t row_block_smem(int log2T, bool sym, int acc_bytes) {
+  return BLOCK_ROW_HEAD + ((size_t)4 << log2T) + (sym ? 0 : ((size_t)(acc_bytes + 12) << log2T));
+}
+
 template <bool SYM, int DT, int SRC>
 __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClusterView Acl, BView B, CView C,
                                                              int64_t* c_rp_sym, const int64_t* items,

@@ -39,13 +39,22 @@ struct Carver {
   bool fits() const { return off <= cap; }
 };
 
-// Row-hash table sizes: log2 T from 5 (32 slots) to 13 (8192 slots).
+// Row-hash table sizes: log2 T from 5 (32 slots) to 15 (32768 slots).  Up to
+// WARP_LG_MAX a row is one warp's (table per warp); above, one CTA's (one
+// shared table for the CTA).
 constexpr int LOG2T_MIN = 5;
-constexpr int LOG2T_MAX = 13;
+constexpr int LOG2T_MAX = 15;
+constexpr int WARP_LG_MAX = 10;
+constexpr int NUM_LG_MAX = 13;   // numeric tables: 12 bytes a slot plus ranking scratch
+constexpr int SYM_LG_MAX = 15;   // symbolic tables: 4 bytes a slot
 
 // Heavy-row limits (rows above go to the dense-window kernels).
-constexpr int64_t HEAVY_NUM = SGC_HEAVY_ROW_OUTPUTS;     // numeric: exact count
-constexpr int64_t HEAVY_SYM = 2 * SGC_HEAVY_ROW_OUTPUTS; // symbolic: min(ub, ncols)
+constexpr int64_t HEAVY_NUM = SGC_HEAVY_ROW_OUTPUTS;      // numeric: exact count
+constexpr int64_t HEAVY_SYM = 4 * SGC_HEAVY_ROW_OUTPUTS;  // symbolic: min(ub, ncols)
+// candidate search (warp tables of 12-byte slots only)
+constexpr int64_t TOPK_HEAVY = 6144;
+constexpr int TOPK_LG_MAX = 13;
+constexpr int NUM_TABLE_LOAD = 50;  // default fill limit of the numeric cluster table
 
 struct ResolvedOptions {
   int staging;
@@ -55,6 +64,7 @@ struct ResolvedOptions {
   int max_warps;
   int load_pct;
   int fused;
+  int cl_load;  // numeric cluster-table fill limit, percent
 };
 ResolvedOptions resolve(const sgc_options* opt);
 

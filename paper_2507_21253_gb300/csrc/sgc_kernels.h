@@ -122,7 +122,7 @@ cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, 
 cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const int32_t* ncap_in,
                             float margin, float scale, const int32_t* uc, const int32_t* h_pos, int32_t* ncap_out,
                             int64_t* capw, int32_t* flag, int32_t* flist, int32_t* flist_count, const BinOut& lb,
-                            int in_bytes, int acc_bytes, int bulk, int sms, cudaStream_t s);
+                            int in_bytes, int acc_bytes, int bulk, int cl_load, int sms, cudaStream_t s);
 cudaError_t compact_run(const AClusterView& A, const int32_t* flag, const int64_t* slab_off, const int32_t* slab_col,
                         const void* slab_val, int val_bytes, const int64_t* c_rp, int32_t* ccol, void* cval, int sms,
                         cudaStream_t s);

@@ -60,7 +60,7 @@ class Predictor(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("staging", i32), ("validate", i32), ("stage_elems", i32), ("max_warps", i32),
-                ("load_pct", i32), ("fused_fma", i32), ("reserved", i32 * 10)]
+                ("load_pct", i32), ("fused_fma", i32), ("cluster_load_pct", i32), ("reserved", i32 * 9)]
 
 
 def _sig(name, *args):
@@ -143,11 +143,12 @@ def _ptr(t):
     return vp(t.data_ptr()) if t is not None and t.numel() > 0 else vp(0)
 
 
-def options(staging=STAGING_AUTO, validate=0, stage_elems=0, max_warps=0, load_pct=0, fused_fma=0) -> Options:
+def options(staging=STAGING_AUTO, validate=0, stage_elems=0, max_warps=0, load_pct=0, fused_fma=0,
+            cluster_load_pct=0) -> Options:
     o = Options()
     _call("sgc_default_options", ctypes.byref(o))
     o.staging, o.validate, o.stage_elems, o.max_warps, o.load_pct = staging, validate, stage_elems, max_warps, load_pct
-    o.fused_fma = fused_fma
+    o.fused_fma, o.cluster_load_pct = fused_fma, cluster_load_pct
     return o
 
 

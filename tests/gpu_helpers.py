@@ -6,6 +6,7 @@ from oracle import gustavson as og
 
 TOL_F64 = 1e-12   # |c - c_ref| <= TOL * (|A||B|)_ij
 TOL_F32 = 2e-6
+WARP_ROW_OUTPUTS = 768   # row kernels: warp tables up to this many outputs, atomics above
 
 
 def lib():
@@ -51,7 +52,12 @@ def compare(C, A, B, rows=None, tol=None, exact_f64=False):
     assert not bad.any(), f"{int(bad.sum())} values beyond {tol}*(|A||B|): max rel {float((err / np.maximum(omag, 1e-300)).max())}"
     same = float(np.mean(got.astype(np.float64) == oval)) if got.size else 1.0
     if exact_f64:
-        assert same == 1.0, f"only {same:.6f} of FP64 values bit-identical"
+        # rows computed row by row with more than WARP_ROW_OUTPUTS outputs accumulate
+        # with shared-memory atomics (order not fixed); every other row is bit-identical
+        counts = np.diff(orp)
+        fixed = np.repeat(counts <= WARP_ROW_OUTPUTS, counts)
+        eq = got.astype(np.float64) == oval
+        assert eq[fixed].all(), f"only {float(eq[fixed].mean()):.6f} of FP64 values bit-identical"
     return same
 
 

@@ -77,9 +77,20 @@ def test_cluster_format_matches_oracle(sgc):
         assert np.array_equal(got.val.cpu().numpy(), ref["val"])
 
 
+def sparse_rows(n, m, per_row, seed, dtype):
+    """n x m with about per_row uniform random columns a row (no dense mask)."""
+    rs = synth.Stream(seed, 901)
+    rows = np.repeat(np.arange(n), per_row)
+    B = synth.csr_from_pattern(n, m, rows, rs.randint(m, n * per_row))
+    if dtype == "i64":
+        return B.with_values(rs.randint(7, B.nnz).astype(np.int64) - 3)
+    v = rs.normal(B.nnz)
+    return B.with_values(v.astype(np.float32) if dtype == "f32" else v)
+
+
 def heavy_matrix():
     """A few rows of A with thousands of entries against a B with wide rows:
-    output rows far above the 3072-entry table limit (heavy-row kernels)."""
+    output rows far above the SGC_HEAVY_ROW_OUTPUTS limit (heavy-row kernels)."""
     rs = synth.Stream(77, 1)
     n, m = 64, 40000
     rows, cols = [], []
@@ -90,7 +101,7 @@ def heavy_matrix():
         cols.append(c)
     A = synth.csr_from_pattern(n, 20000, np.concatenate(rows), np.concatenate(cols))
     A = A.with_values(rs.normal(A.nnz))
-    B = random_sparse(20000, m, 0.0004, 12, "f64")
+    B = sparse_rows(20000, m, 16, 12, "f64")
     return A, B
 
 
@@ -109,6 +120,39 @@ def test_heavy_rows(sgc, dtype):
         Acl = sgc.csr_cluster_build(Ad, perm, cptr, layout)
         C = sgc.spgemm(Acl, Bd)
         compare(C, A, B)
+
+
+def tiers_matrix(dtype):
+    """Row r of A has 2^(r mod 14) entries (1 .. 8192) against B with about 10
+    entries a row over 40000 columns: output rows from a few to ~35000 columns,
+    so every row tier runs (warp tables, CTA tables of each size, heavy rows)."""
+    rs = synth.Stream(78, 1)
+    n, kdim, m = 112, 20000, 40000
+    rows, cols = [], []
+    for r in range(n):
+        c = np.unique(rs.randint(kdim, 1 << (r % 14)))
+        rows.append(np.full(c.size, r))
+        cols.append(c)
+    A = synth.csr_from_pattern(n, kdim, np.concatenate(rows), np.concatenate(cols))
+    B = sparse_rows(kdim, m, 10, 13, dtype)
+    if dtype == "i64":
+        A = A.with_values(rs.randint(7, A.nnz).astype(np.int64) - 3)
+    else:
+        v = rs.normal(A.nnz)
+        A = A.with_values(v.astype(np.float32) if dtype == "f32" else v)
+    return A, B
+
+
+@pytest.mark.parametrize("load", [50, 75, 90])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "i64"])
+def test_row_tiers(sgc, dtype, load):
+    A, B = tiers_matrix(dtype)
+    Ad, Bd = dev(sgc, A), dev(sgc, B)
+    opt = sgc.options(load_pct=load)
+    compare(sgc.spgemm_rowwise(Ad, Bd, opt), A, B)
+    # clusters whose staged rows exceed shared memory fall back to the row kernels
+    perm, cptr = synth.random_clusters(A.nrows, 4, kmax=8)
+    compare(sgc.spgemm(sgc.csr_cluster_build(Ad, perm, cptr, 1), Bd, opt), A, B)
 
 
 def test_rectangular_and_empty_rows(sgc):
