@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--fused-fma", type=int, default=0, help="FP64: accumulate with fused multiply-add")
     ap.add_argument("--cluster-load", type=int, default=0, help="numeric cluster-table fill limit, percent (0: default)")
+    ap.add_argument("--cluster-kernel", type=int, default=0,
+                    help="numeric cluster kernel: 0 warp groups (default), 1 warp per cluster where it fits")
     ap.add_argument("--batch", type=int, default=256, help="products in the batched workload")
     return ap.parse_args()
 
@@ -253,7 +255,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
 
-    opt = sgc.options(fused_fma=args.fused_fma, cluster_load_pct=args.cluster_load)
+    opt = sgc.options(fused_fma=args.fused_fma, cluster_load_pct=args.cluster_load,
+                      cluster_kernel=args.cluster_kernel)
     ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad, opt), dev)
     rp, nnz = sgc.spgemm_symbolic(Acl, Ad, ws, opt)
     C = sgc.spgemm_numeric(Acl, Ad, rp, nnz, ws, opt)

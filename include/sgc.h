@@ -65,11 +65,14 @@ enum {
   SGC_LAYOUT_MASKED = 1  /* placeholders dropped: values in (t, l ascending over set mask bits) order */
 };
 
-/* staging of B rows into shared memory */
+/* How kernels fetch B rows.  BULK: the cluster kernels copy them into shared
+ * memory with 1D bulk async copies (cp.async.bulk) completing on an mbarrier,
+ * and the warp-per-cluster and row kernels prefetch them into L2 with 1D bulk
+ * prefetches; LDG: plain loads only. */
 enum {
-  SGC_STAGING_AUTO = 0, /* bulk copies when B's col/val base pointers are 16-byte aligned */
-  SGC_STAGING_BULK = 1, /* 1D bulk async copies (cp.async.bulk) completing on an mbarrier */
-  SGC_STAGING_LDG = 2   /* cooperative vector loads by the CTA's threads */
+  SGC_STAGING_AUTO = 0, /* BULK when B's col/val base pointers are 16-byte aligned, else LDG */
+  SGC_STAGING_BULK = 1,
+  SGC_STAGING_LDG = 2
 };
 
 /* Rows computed row by row (the row-wise method, and rows of clusters too
@@ -126,7 +129,11 @@ typedef struct sgc_options {
                                use the fused form: their FP64 products are exact, so it changes nothing. */
   int32_t cluster_load_pct; /* fill limit of the numeric cluster kernel's column table, in percent of its
                                slots; 0 = default 50; 20..75.  Lower: fewer probes, more shared memory. */
-  int32_t reserved[9];
+  int32_t cluster_kernel;   /* numeric phase: 0 (default) = warp groups for every cluster; 1 = one warp
+                               per cluster (B rows prefetched into L2 and streamed through a small
+                               shared-memory ring) where the cluster's working set fits in 16 KB,
+                               warp groups otherwise */
+  int32_t reserved[8];
 } sgc_options;
 
 /* Version of this ABI (SGC_ABI_VERSION). */
@@ -334,7 +341,8 @@ int spgemm_graph_destroy(sgc_graph* graph);
  *     into the caller's slab (slab_col int32, slab_val of A's dtype, slab_elems
  *     each) and writes its row counts; a cluster with more output columns
  *     (an under-prediction) is flagged and its rows go through the exact
- *     symbolic pass; c_row_ptr (nrows+1) is C's row pointer;
+ *     symbolic pass, as do the rows of one-row clusters (the row kernels'
+ *     work in every path); c_row_ptr (nrows+1) is C's row pointer;
  *     *c_nnz_host = nnz(C), *n_overflow_host = clusters sent to the exact path.
  *     Synchronises.
  *   phase2: copies slab rows into C and runs the exact numeric pass on the

@@ -42,6 +42,7 @@ ResolvedOptions resolve(const sgc_options* opt) {
   r.cl_load = (opt && opt->cluster_load_pct > 0) ? opt->cluster_load_pct : NUM_TABLE_LOAD;
   if (r.cl_load < 20) r.cl_load = 20;
   if (r.cl_load > 75) r.cl_load = 75;
+  r.lean = (opt && opt->cluster_kernel == 1) ? 1 : 0;
   return r;
 }
 
@@ -60,6 +61,7 @@ SpWs carve_sp(void* base, size_t cap, int64_t nrows, int64_t ncl) {
   w.status = cv.take<DevStatus>(4);
   w.bins.count = cv.take<int32_t>(NBIN_ALL);
   w.bins.dense_items = cv.take<int32_t>((int64_t)NDB * ncl);
+  w.bins.lean_items = cv.take<int32_t>((int64_t)NLB * ncl);
   w.bins.row_items = cv.take<int64_t>((int64_t)NRB * nrows);
   w.bins.heavy_items = cv.take<int64_t>(nrows);
   w.bins.uc_rec = cv.take<int32_t>(ncl);
@@ -370,6 +372,8 @@ int spgemm_rowwise_symbolic(const sgc_csr* A, const sgc_csr* B, int64_t* c_row_p
   cudaStream_t s = (cudaStream_t)stream;
   const ResolvedOptions o = resolve(opt);
   Launch L{s, o, num_sms(), 0};
+  rc = resolve_mode(o, B, false, &L.mode);  // bulk: the row kernels prefetch B rows into L2
+  if (rc) return rc;
   SGC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
   SGC_CUDA(cudaMemsetAsync(c_row_ptr, 0, sizeof(int64_t), s));
   if (A->nrows == 0) return finish_symbolic(c_row_ptr, 0, c_nnz_host, w.status, w.scan_tmp, s);
@@ -397,6 +401,8 @@ int spgemm_rowwise_numeric(const sgc_csr* A, const sgc_csr* B, sgc_csr* C, void*
   cudaStream_t s = (cudaStream_t)stream;
   const ResolvedOptions o = resolve(opt);
   Launch L{s, o, num_sms(), 0};
+  rc = resolve_mode(o, B, true, &L.mode);
+  if (rc) return rc;
   SGC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
   if (A->nrows == 0 || C->nnz == 0) return SGC_OK;
   const ACsrView av{A->row_ptr, A->col, A->val, A->nrows};
@@ -436,6 +442,7 @@ HcWs carve_hc(void* base, size_t cap, const sgc_csr* A, int topk) {
   w.dummy_rp = cv.take<int64_t>(n + 1);
   w.bins.count = cv.take<int32_t>(NBIN_ALL);
   w.bins.dense_items = nullptr;
+  w.bins.lean_items = nullptr;
   w.bins.row_items = cv.take<int64_t>((int64_t)NRB * n);
   w.bins.heavy_items = cv.take<int64_t>(n);
   w.bins.uc_rec = w.bins.nout_rec = nullptr;
@@ -551,6 +558,7 @@ LwWs carve_lw(void* base, size_t cap, int64_t nrows, int64_t ncl) {
   cv.off = w.sp.bytes;
   w.lb.count = cv.take<int32_t>(NBIN_ALL);
   w.lb.dense_items = cv.take<int32_t>((int64_t)NDB * ncl);
+  w.lb.lean_items = cv.take<int32_t>((int64_t)NLB * ncl);
   w.lb.ncl = ncl;
   w.lb.nrows = nrows;
   w.lb.uc_rec = w.sp.bins.uc_rec;
@@ -642,7 +650,8 @@ int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_pr
   if (!pred->ncap) SGC_CUDA(mlp_infer_run(pred->params, w.X, A->nclusters, w.yhat, sms, s));
   const int inb = dtype_bytes(A->dtype);
   SGC_CUDA(learned_bin_run(av, bv, w.yhat, pred->ncap, pred->margin, pred->scale, w.sp.bins.uc_rec, w.h_pos, w.ncap,
-                           w.slab_off, w.flag, w.flist, w.flist_count, w.lb, inb, 8, mode, o.cl_load, sms, s));
+                           w.slab_off, w.flag, w.flist, w.flist_count, w.lb, inb, 8, mode, o.cl_load, o.lean, sms,
+                           s));
   SGC_CUDA(inclusive_scan_i64(w.slab_off + 1, A->nrows, w.sp.scan_tmp, s));
   SGC_CUDA(cudaMemcpyAsync(w.flist_plan, w.flist_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   SGC_CUDA(cudaMemcpyAsync(slab_elems_host, w.slab_off + A->nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

@@ -1,19 +1,24 @@
 // Binning of work before each phase (Sec. 2.2: the symbolic phase sizes C,
-// the numeric phase fills it).  Clusters go to the cluster kernel when their
-// staged footprint fits in shared memory (bins = shared-memory budget
-// classes); otherwise their rows go to the row-level kernels, binned by hash
-// table size, and rows beyond the table limit go to the heavy-row kernel.
+// the numeric phase fills it).  Clusters of two or more rows go to the cluster
+// kernel when their staged footprint fits in shared memory (bins = shared-memory
+// budget classes); otherwise (and for one-row clusters) their rows go to the
+// row-level kernels, binned by hash table size, and rows beyond the table
+// limit go to the heavy-row kernel.
 // Symbolic bins use the flop upper bound ub_l = sum_k nnz(B_k) (capped by
 // ncols(B)); numeric bins use the exact counts the symbolic phase produced.
 #pragma once
 
-#include "k_cluster.cuh"
+#include "k_lean.cuh"
 
 namespace sgc {
 
 __device__ __forceinline__ void push_dense(const BinOut& o, int b, int32_t c) {
   const int32_t idx = atomicAdd(&o.count[b], 1);
   o.dense_items[(int64_t)b * o.ncl + idx] = c;
+}
+__device__ __forceinline__ void push_lean(const BinOut& o, int b, int32_t c) {
+  const int32_t idx = atomicAdd(&o.count[BIN_LEAN0 + b], 1);
+  o.lean_items[(int64_t)b * o.ncl + idx] = c;
 }
 __device__ __forceinline__ void push_row(const BinOut& o, int lg, int64_t item) {
   const int b = lg - LOG2T_MIN;
@@ -69,7 +74,8 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
     __syncwarp();
     const int64_t T = u1 - u0;
     int cls = -1;
-    if (use_dense && U < (1ll << 28) && T < (1ll << 24)) {
+    // a cluster of one row gains nothing from staging: its row goes to the row kernels
+    if (use_dense && K > 1 && U < (1ll << 28) && T < (1ll << 24)) {
       const int64_t nb = min64(U, B.ncols);
       const WarpLayout L = warp_layout(true, T, U, 0, cluster_table_log2(true, nb, 0), nb, K, 4, 8, bulk != 0);
       cls = warp_class(L.total);
@@ -94,7 +100,7 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
 // ---- cluster path, numeric: warp per cluster -------------------------------
 static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, BView B, const int64_t* c_rp, BinOut o,
                                                          int load_pct, int bulk, int in_bytes, int acc_bytes,
-                                                         int cl_load) {
+                                                         int cl_load, int lean) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   const int64_t nitems = o.clist ? (int64_t)*o.clist_count : A.ncl;
@@ -104,15 +110,17 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, 
     const int K = (int)(A.cptr[c + 1] - p0);
     const int64_t T = A.uptr[c + 1] - A.uptr[c];
     const int32_t nout = o.nout_rec[c];
-    int cls = -1;
+    int cls = -1, lcls = -1;
     if (nout >= 0) {
       const int64_t nva = A.vptr[c + 1] - A.vptr[c];
-      const WarpLayout L =
-          warp_layout(false, T, o.uc_rec[c], nva, cluster_table_log2(false, nout, cl_load), nout, K, in_bytes, acc_bytes,
-                      bulk != 0);
-      cls = warp_class(L.total);
+      const int LH = cluster_table_log2(false, nout, cl_load);
+      if (lean && o.lean_items) lcls = lean_class(lean_layout(T, nva, LH, nout, K, in_bytes, acc_bytes).total);
+      if (lcls < 0) cls = warp_class(warp_layout(false, T, o.uc_rec[c], nva, LH, nout, K, in_bytes, acc_bytes,
+                                                 bulk != 0).total);
     }
-    if (cls >= 0) {
+    if (lcls >= 0) {
+      if (lane == 0) push_lean(o, lcls, (int32_t)c);
+    } else if (cls >= 0) {
       if (lane == 0) push_dense(o, cls, (int32_t)c);
     } else if (lane < K) {
       const int64_t row = A.perm[p0 + lane];

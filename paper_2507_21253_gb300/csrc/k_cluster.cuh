@@ -107,7 +107,7 @@ __host__ __device__ inline int warp_class(int64_t need) {
 // share each byte of shared memory.
 __host__ __device__ inline int group_warps(int cls) {
   const int b = warp_class_bytes(cls);
-  return b <= 8 * 1024 ? 1 : (b <= 16 * 1024 ? 2 : (b <= 48 * 1024 ? 4 : 8));
+  return b <= 8 * 1024 ? 1 : (b <= 16 * 1024 ? 2 : (b <= 32 * 1024 ? 4 : 8));
 }
 __host__ __device__ inline int groups_per_cta(int cls) {
   int g = 8 / group_warps(cls);
@@ -122,10 +122,6 @@ struct WDesc {  // struct-of-arrays per union column, in the group's region
   uint32_t* mask;
   int32_t* aoff;   // MASKED: staged value slot of (t, lowest row of the mask)
 };
-
-__device__ __forceinline__ int bucket_of(int32_t key, int32_t kmin, int n, uint64_t range) {
-  return (int)(((uint64_t)(uint32_t)(key - kmin) * (uint64_t)n) / range);
-}
 
 // Synchronises the threads of one group (one warp: __syncwarp).
 __device__ __forceinline__ void group_sync(int gw, int gid) {
@@ -493,8 +489,8 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
         }
         for (int x = gt; x < n_out; x += GT) bst[x] = 0;
         group_sync(gw, gid);
-        const uint64_t range = (uint64_t)((int64_t)kmax - (int64_t)kmin + 1);
-        for (int x = gt; x < n_out; x += GT) atomicAdd(&bst[bucket_of(bkey[x], kmin, n_out, range)], 1);
+        const Interp ip = interp_make(kmin, kmax, n_out);
+        for (int x = gt; x < n_out; x += GT) atomicAdd(&bst[interp_bucket(ip, bkey[x])], 1);
         group_sync(gw, gid);
         int carry = 0;
         for (int x0 = 0; x0 < n_out; x0 += GT) {
@@ -510,11 +506,11 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
         }
         group_sync(gw, gid);
         for (int x = gt; x < n_out; x += GT)
-          srt[atomicAdd(&bcur[bucket_of(bkey[x], kmin, n_out, range)], 1)] = bkey[x];
+          srt[atomicAdd(&bcur[interp_bucket(ip, bkey[x])], 1)] = bkey[x];
         group_sync(gw, gid);
         for (int x = gt; x < n_out; x += GT) {
           const int32_t key = bkey[x];
-          const int b = bucket_of(key, kmin, n_out, range);
+          const int b = interp_bucket(ip, key);
           const int bs = bst[b], be = bcur[b];
           int r = bs;
           for (int y = bs; y < be; ++y) r += srt[y] < key;
@@ -539,22 +535,34 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       group_sync(gw, gid);
       const In* av = stage_a + ashift;
       const bool padded = A.layout == SGC_LAYOUT_PADDED;
-      // ---- 3. accumulate: warp per row, the row's union columns in ascending order
+      // ---- 3. accumulate: warp per row, the row's union columns in ascending order.
+      // Each lane loads the descriptor and a_lt of one union column of a chunk of
+      // 32; the columns the row has are then broadcast one by one.
+      const int T32 = (int)T;
       for (int l = wg; l < K; l += gw) {
-        Acc* al = acc + (size_t)l * n_out;
-        uint8_t* fl = flg + (size_t)l * n_out;
+        Acc* al = acc + l * n_out;
+        uint8_t* fl = flg + l * n_out;
         const uint32_t below = (1u << l) - 1u;
-        for (int64_t tb = 0; tb < T; tb += 32) {
-          const uint32_t mm = tb + lane < T ? d.mask[tb + lane] : 0u;
-          unsigned bits = __ballot_sync(FULL, (mm >> l) & 1u);
+        for (int tb = 0; tb < T32; tb += 32) {
+          const int t = tb + lane;
+          const uint32_t mm = t < T32 ? d.mask[t] : 0u;
+          const bool has = (mm >> l) & 1u;
+          int tn = 0, tc = 0, tv = 0;
+          In ta{};
+          if (has) {
+            tn = d.len[t];
+            tc = d.off_c[t] & 0x7fffffff;
+            tv = d.off_v[t];
+            ta = padded ? av[t * K + l] : av[d.aoff[t] + __popc(mm & below)];
+          }
+          unsigned bits = __ballot_sync(FULL, has);
           while (bits) {
             const int src = __ffs(bits) - 1;
             bits &= bits - 1;
-            const int64_t i = tb + src;
-            const uint32_t m = __shfl_sync(FULL, mm, src);
-            const int n = d.len[i];
-            const int dc = d.off_c[i] & 0x7fffffff, dv = d.off_v[i];
-            const In a = padded ? av[i * K + l] : av[d.aoff[i] + __popc(m & below)];
+            const int n = __shfl_sync(FULL, tn, src);
+            const int dc = __shfl_sync(FULL, tc, src);
+            const int dv = __shfl_sync(FULL, tv, src);
+            const In a = __shfl_sync(FULL, ta, src);
             if (fused) {
               for (int q = lane; q < n; q += 32) {
                 const int lid = stage_c[dc + q];
@@ -568,7 +576,7 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
                 fl[lid] = 1;
               }
             }
-            __syncwarp();
+            __syncwarp();  // the next column's lanes read what these lanes wrote
           }
         }
         // ---- 4. emit row l in column order ----------------------------------

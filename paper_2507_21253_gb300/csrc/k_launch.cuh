@@ -61,7 +61,7 @@ cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const B
     const size_t smem = (size_t)warps * per_warp;
     const int occ = occupancy(kh, warps * 32, smem);
     const unsigned grid = grid_for(bins.nrows, warps, L.sms, occ);
-    kh<<<grid, warps * 32, smem, L.s>>>(Ac, Acl, B, C, c_rp, items, cnt, lg, L.o.fused, status);
+    kh<<<grid, warps * 32, smem, L.s>>>(Ac, Acl, B, C, c_rp, items, cnt, lg, L.o.fused, L.mode == 1, status);
     note_launches(1);
   }
   auto kv = k_row_heavy<SYM, DT, SRC>;
@@ -78,6 +78,50 @@ cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const B
   return cudaGetLastError();
 }
 
+// Warp-per-cluster numeric classes (k_lean.cuh): warps per CTA chosen for the
+// most resident warps per SM.
+template <int DT, bool FUSED>
+cudaError_t launch_lean_classes(const AClusterView& A, const BView& B, const CView& C, const BinOut& bins,
+                                const int32_t* nout_rec, const LearnedOut& lo, void* status, const Launch& L) {
+  auto kl = k_cluster_lean<DT, FUSED>;
+  static int best_w[NLB] = {0};
+  static int best_occ[NLB] = {0};
+  if (best_w[0] == 0) {
+    cudaError_t e = allow_smem(kl);
+    if (e != cudaSuccess) return e;
+    for (int b = 0; b < NLB; ++b) {
+      int bw = 1, bo = 1, bt = 0;
+      for (int w = 8; w >= 1; --w) {
+        const int occ = occupancy(kl, w * 32, (size_t)w * lean_class_bytes(b));
+        if (occ * w > bt) {
+          bt = occ * w;
+          bw = w;
+          bo = occ;
+        }
+      }
+      best_occ[b] = bo;
+      best_w[b] = bw;
+    }
+  }
+  for (int b = 0; b < NLB; ++b) {
+    const int w = best_w[b], rb = lean_class_bytes(b);
+    const unsigned grid = grid_for(A.ncl, w, L.sms, best_occ[b]);
+    kl<<<grid, w * 32, (size_t)w * rb, L.s>>>(A, B, C, bins.lean_items + (int64_t)b * bins.ncl,
+                                               bins.count + BIN_LEAN0 + b, nout_rec, rb, L.o.cl_load, L.mode == 1,
+                                               lo, status);
+    note_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+template <int DT>
+cudaError_t launch_lean(const AClusterView& A, const BView& B, const CView& C, const BinOut& bins,
+                        const int32_t* nout_rec, const LearnedOut& lo, void* status, const Launch& L) {
+  if (!L.o.lean || !bins.lean_items) return cudaSuccess;
+  return L.o.fused ? launch_lean_classes<DT, true>(A, B, C, bins, nout_rec, lo, status, L)
+                   : launch_lean_classes<DT, false>(A, B, C, bins, nout_rec, lo, status, L);
+}
+
 template <bool SYM, int DT>
 cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView& C, int64_t* c_rp,
                               const BinOut& bins, void* status, const Launch& L) {
@@ -90,7 +134,7 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
     k_bin_cluster_sym<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, 1);
   else
     k_bin_cluster_num<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, (int)sizeof(In),
-                                            (int)sizeof(Acc), L.o.cl_load);
+                                            (int)sizeof(Acc), L.o.cl_load, L.o.lean);
   note_launches(1);
   auto kd = k_cluster_group<SYM, DT>;
   static bool attr = false;
@@ -113,6 +157,10 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if constexpr (!SYM) {
+    e = launch_lean<DT>(A, B, C, bins, bins.nout_rec, LearnedOut{}, status, L);
+    if (e != cudaSuccess) return e;
+  }
   ACsrView none{};
   return launch_row_bins<SYM, DT, SRC_CLUSTER>(none, A, B, C, c_rp, bins, status, L);
 }
@@ -139,7 +187,9 @@ cudaError_t run_cluster_learned(const AClusterView& A, const BView& B, const Bin
                                       L.o.cl_load, lo, status);
     note_launches(1);
   }
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_lean<DT>(A, B, CView{}, lbins, nullptr, lo, status, L);
 }
 
 template <bool SYM, int DT>

@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, co
                                                      float margin, float scale, const int32_t* uc, const int32_t* h_pos,
                                                      int32_t* ncap_out, int64_t* capw, int32_t* flag, int32_t* flist,
                                                      int32_t* flist_count, BinOut lb, int in_bytes, int acc_bytes,
-                                                     int bulk, int cl_load) {
+                                                     int bulk, int cl_load, int lean) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   for (int64_t c = gw; c < A.ncl; c += nwarps) {
@@ -222,24 +222,27 @@ __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, co
     const int64_t U = uc[c];
     const int64_t bound = min64(U, B.ncols);
     const int32_t ncap = ncap_in ? (int32_t)min64(ncap_in[c], bound) : capacity_of(yhat[c], bound, margin, scale);
-    int cls = -1;
-    if (U < (1ll << 28) && T < (1ll << 24)) {
-      const WarpLayout L =
-          warp_layout(false, T, U, nva, cluster_table_log2(false, ncap, cl_load), ncap, K, in_bytes, acc_bytes,
-                      bulk != 0);
-      cls = warp_class(L.total);
+    int cls = -1, lcls = -1;
+    if (K > 1 && U < (1ll << 28) && T < (1ll << 24)) {  // one-row clusters: row kernels, exact path
+      const int LH = cluster_table_log2(false, ncap, cl_load);
+      if (lean) lcls = lean_class(lean_layout(T, nva, LH, ncap, K, in_bytes, acc_bytes).total);
+      if (lcls < 0) cls = warp_class(warp_layout(false, T, U, nva, LH, ncap, K, in_bytes, acc_bytes, bulk != 0).total);
     }
+    const bool take = cls >= 0 || lcls >= 0;
     if (lane == 0) {
       ncap_out[c] = ncap;
-      flag[c] = cls < 0 ? 1 : 0;
-      if (cls >= 0) {
+      flag[c] = take ? 0 : 1;
+      if (lcls >= 0) {
+        const int32_t idx = atomicAdd(&lb.count[BIN_LEAN0 + lcls], 1);
+        lb.lean_items[(int64_t)lcls * lb.ncl + idx] = (int32_t)c;
+      } else if (cls >= 0) {
         const int32_t idx = atomicAdd(&lb.count[cls], 1);
         lb.dense_items[(int64_t)cls * lb.ncl + idx] = (int32_t)c;
       } else {
         flist[atomicAdd(flist_count, 1)] = (int32_t)c;
       }
     }
-    if (lane < K) capw[p0 + lane + 1] = cls >= 0 ? min64((int64_t)h_pos[p0 + lane], (int64_t)ncap) : 0;
+    if (lane < K) capw[p0 + lane + 1] = take ? min64((int64_t)h_pos[p0 + lane], (int64_t)ncap) : 0;
   }
 }
 
@@ -311,7 +314,7 @@ cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, 
 cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const int32_t* ncap_in,
                             float margin, float scale, const int32_t* uc, const int32_t* h_pos, int32_t* ncap_out,
                             int64_t* capw, int32_t* flag, int32_t* flist, int32_t* flist_count, const BinOut& lb,
-                            int in_bytes, int acc_bytes, int bulk, int cl_load, int sms, cudaStream_t s) {
+                            int in_bytes, int acc_bytes, int bulk, int cl_load, int lean, int sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(lb.count, 0, sizeof(int32_t) * NBIN_ALL, s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(flist_count, 0, sizeof(int32_t), s);
@@ -321,7 +324,7 @@ cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* 
   if (A.ncl <= 0) return cudaSuccess;
   k_learned_bin<<<grid_for(A.ncl, 8, sms, 8), 256, 0, s>>>(A, B, yhat, ncap_in, margin, scale, uc, h_pos, ncap_out,
                                                             capw, flag, flist, flist_count, lb, in_bytes, acc_bytes,
-                                                            bulk, cl_load);
+                                                            bulk, cl_load, lean);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -100,17 +100,25 @@ __device__ __forceinline__ int64_t item_row(const AClusterView& Acl, int64_t ite
 // rank_of(x) for x in [0, n) is valid after the call, via the returned lambda
 // inputs (bst, bcur, srt).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int interp_bucket(int32_t key, int32_t kmin, int n, uint64_t range) {
-  return (int)(((uint64_t)(uint32_t)(key - kmin) * (uint64_t)n) / range);
+// Bucket of a key among n buckets spread over [kmin, kmax]: about
+// (key - kmin) * n / (kmax - kmin + 1), evaluated in FP32.  Every step is
+// monotone non-decreasing in the key, so a smaller key never lands in a later
+// bucket; the result is clamped to [0, n).
+struct Interp {
+  int32_t kmin;
+  int n;
+  float scale;
+};
+__device__ __forceinline__ Interp interp_make(int32_t kmin, int32_t kmax, int n) {
+  return Interp{kmin, n, (float)n / (float)((int64_t)kmax - (int64_t)kmin + 1)};
+}
+__device__ __forceinline__ int interp_bucket(const Interp& ip, int32_t key) {
+  const int b = (int)(__uint2float_rz((uint32_t)(key - ip.kmin)) * ip.scale);
+  return b < ip.n - 1 ? b : ip.n - 1;
 }
 
-struct RankCtx {
-  int32_t kmin;
-  uint64_t range;
-};
-
-__device__ __forceinline__ RankCtx warp_rank_prepare(const int32_t* keys, int n, int32_t* bst, int32_t* bcur,
-                                                     int32_t* srt) {
+__device__ __forceinline__ Interp warp_rank_prepare(const int32_t* keys, int n, int32_t* bst, int32_t* bcur,
+                                                    int32_t* srt) {
   const int lane = lane_id();
   int32_t kmin = PAD_KEY, kmax = -1;
   for (int x = lane; x < n; x += 32) {
@@ -120,9 +128,9 @@ __device__ __forceinline__ RankCtx warp_rank_prepare(const int32_t* keys, int n,
   }
   kmin = warp_min(kmin);
   kmax = warp_max(kmax);
-  const uint64_t range = (uint64_t)((int64_t)kmax - (int64_t)kmin + 1);
+  const Interp ip = interp_make(kmin, kmax, n);
   __syncwarp();
-  for (int x = lane; x < n; x += 32) atomicAdd(&bst[interp_bucket(keys[x], kmin, n, range)], 1);
+  for (int x = lane; x < n; x += 32) atomicAdd(&bst[interp_bucket(ip, keys[x])], 1);
   __syncwarp();
   int carry = 0;
   for (int x0 = 0; x0 < n; x0 += 32) {
@@ -136,18 +144,26 @@ __device__ __forceinline__ RankCtx warp_rank_prepare(const int32_t* keys, int n,
     carry += __shfl_sync(FULL, ex + v, 31);
   }
   __syncwarp();
-  for (int x = lane; x < n; x += 32) srt[atomicAdd(&bcur[interp_bucket(keys[x], kmin, n, range)], 1)] = keys[x];
+  for (int x = lane; x < n; x += 32) srt[atomicAdd(&bcur[interp_bucket(ip, keys[x])], 1)] = keys[x];
   __syncwarp();
-  return RankCtx{kmin, range};
+  return ip;
 }
 
-__device__ __forceinline__ int warp_rank_of(int32_t key, int n, const RankCtx& rc, const int32_t* bst,
-                                            const int32_t* bcur, const int32_t* srt) {
-  const int b = interp_bucket(key, rc.kmin, n, rc.range);
+__device__ __forceinline__ int warp_rank_of(int32_t key, const Interp& ip, const int32_t* bst, const int32_t* bcur,
+                                            const int32_t* srt) {
+  const int b = interp_bucket(ip, key);
   const int bs = bst[b], be = bcur[b];
   int r = bs;
   for (int y = bs; y < be; ++y) r += srt[y] < key;
   return r;
+}
+
+// Hint: bring the 16-byte window around elements [s, s + len) of an array of
+// `elem`-byte values (16-byte aligned base, nnz elements) into L2.
+__device__ __forceinline__ void bulk_prefetch_row(const void* base, int64_t s, int64_t len, int elem, int64_t nnz) {
+  const int64_t per = 16 / elem;
+  const int64_t ws = s & ~(per - 1), we = min64((s + len + per - 1) & ~(per - 1), nnz & ~(per - 1));
+  if (we > ws) bulk_prefetch_l2((const char*)base + ws * elem, (uint32_t)((we - ws) * elem));
 }
 
 // ---------------------------------------------------------------------------
@@ -161,7 +177,8 @@ __device__ __forceinline__ int warp_rank_of(int32_t key, int n, const RankCtx& r
 template <bool SYM, int DT, int SRC>
 __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl, BView B, CView C,
                                                   int64_t* c_rp_sym, const int64_t* items,
-                                                  const int32_t* count_ptr, int log2T, int fused, void* status) {
+                                                  const int32_t* count_ptr, int log2T, int fused, int pf,
+                                                  void* status) {
   using In = typename VT<DT>::In;
   using Acc = typename VT<DT>::Acc;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -188,21 +205,57 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
     __syncwarp();
     int64_t cnt = 0;
     bool full = false;
-    auto apply = [&](int64_t s, int64_t e, In a) {
-      for (int64_t q = s + lane; q < e; q += 32) {
-        bool nw;
-        const int slot = hash_find_or_insert(keys, log2T, B.col[q], &nw);
-        if (slot < 0) {
-          full = true;
-          continue;
-        }
-        if constexpr (SYM) {
-          cnt += nw;
-        } else {
-          vals[slot] = VT<DT>::madd(vals[slot], a, ((const In*)B.val)[q], fused != 0);
-        }
+    auto process = [&](int32_t j, In v, In a) {
+      bool nw;
+      const int slot = hash_find_or_insert(keys, log2T, j, &nw);
+      if (slot < 0) {
+        full = true;
+      } else if constexpr (SYM) {
+        cnt += nw;
+      } else {
+        vals[slot] = VT<DT>::madd(vals[slot], a, v, fused != 0);
       }
-      __syncwarp();
+    };
+    // One chunk of up to 32 entries (k, a_ik) of the row, one per lane, B row
+    // [s, e).  The chunk's B rows are prefetched into L2 at once; the entries are
+    // then applied in order, the next entry's first 32 elements in flight while
+    // the current one is hashed.
+    auto run_chunk = [&](bool valid, int64_t s, int64_t e, In a) {
+      const bool has = valid && e > s;
+      if (pf && has) {
+        bulk_prefetch_row(B.col, s, e - s, 4, B.nnz);
+        if (!SYM) bulk_prefetch_row(B.val, s, e - s, (int)sizeof(In), B.nnz);
+      }
+      unsigned bits = __ballot_sync(FULL, has);
+      if (!bits) return;
+      int src = __ffs(bits) - 1;
+      int64_t sn = __shfl_sync(FULL, s, src), en = __shfl_sync(FULL, e, src);
+      int32_t jn = 0;
+      In vn{};
+      if (sn + lane < en) {
+        jn = B.col[sn + lane];
+        if (!SYM) vn = ((const In*)B.val)[sn + lane];
+      }
+      while (true) {
+        const int64_t si = sn, ei = en;
+        const In ai = __shfl_sync(FULL, a, src);
+        const int32_t j = jn;
+        const In v = vn;
+        bits &= bits - 1;
+        if (bits) {
+          src = __ffs(bits) - 1;
+          sn = __shfl_sync(FULL, s, src);
+          en = __shfl_sync(FULL, e, src);
+          if (sn + lane < en) {
+            jn = B.col[sn + lane];
+            if (!SYM) vn = ((const In*)B.val)[sn + lane];
+          }
+        }
+        if (si + lane < ei) process(j, v, ai);
+        for (int64_t q = si + 32 + lane; q < ei; q += 32) process(B.col[q], SYM ? In{} : ((const In*)B.val)[q], ai);
+        __syncwarp();
+        if (!bits) break;
+      }
     };
     if constexpr (SRC == SRC_CSR) {
       const int64_t rs = Ac.rp[row], re = Ac.rp[row + 1];
@@ -216,12 +269,38 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
           s = B.rp[k];
           e = B.rp[k + 1];
         }
-        const int n = (int)min64(32, re - pb);
-        for (int i = 0; i < n; ++i)
-          apply(__shfl_sync(FULL, s, i), __shfl_sync(FULL, e, i), __shfl_sync(FULL, a, i));
+        run_chunk(p < re, s, e, a);
       }
     } else {
-      for_row_entries_cluster<DT>(Acl, item, [&](int32_t k, In a) { apply(B.rp[k], B.rp[k + 1], a); });
+      const int64_t c = item >> 5;
+      const int l = (int)(item & 31);
+      const int K = (int)(Acl.cptr[c + 1] - Acl.cptr[c]);
+      const int64_t u0 = Acl.uptr[c], u1 = Acl.uptr[c + 1], v0 = Acl.vptr[c];
+      const uint32_t below = (1u << l) - 1u;
+      int64_t run = 0;  // MASKED: value slots before this chunk of union columns
+      for (int64_t tb = u0; tb < u1; tb += 32) {
+        const int64_t t = tb + lane;
+        uint32_t m = 0;
+        int32_t k = 0;
+        if (t < u1) {
+          m = Acl.mask[t];
+          k = Acl.ucol[t];
+        }
+        const int pc = __popc(m);
+        const int excl = warp_incl_scan(pc) - pc;
+        const bool mine = (m >> l) & 1u;
+        In a{};
+        int64_t s = 0, e = 0;
+        if (mine) {
+          const int64_t vi = Acl.layout == SGC_LAYOUT_PADDED ? v0 + (t - u0) * K + l
+                                                             : v0 + run + excl + __popc(m & below);
+          if (Acl.val) a = ((const In*)Acl.val)[vi];
+          s = B.rp[k];
+          e = B.rp[k + 1];
+        }
+        run += __shfl_sync(FULL, excl + pc, 31);
+        run_chunk(mine, s, e, a);
+      }
     }
     if (__any_sync(FULL, full)) {
       if (lane == 0) raise(st, DEV_TABLE_FULL, 10, row);
@@ -239,9 +318,9 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
       int32_t* bst = scr;
       int32_t* bcur = scr + T;
       int32_t* srt = scr + 2 * T;
-      const RankCtx rc = warp_rank_prepare(keys, n, bst, bcur, srt);
+      const Interp ip = warp_rank_prepare(keys, n, bst, bcur, srt);
       for (int x = lane; x < n; x += 32) {
-        const int r = warp_rank_of(keys[x], n, rc, bst, bcur, srt);
+        const int r = warp_rank_of(keys[x], ip, bst, bcur, srt);
         C.col[out0 + r] = keys[x];
         ((In*)C.val)[out0 + r] = VT<DT>::out(vals[x]);
       }
@@ -457,12 +536,12 @@ __global__ void __launch_bounds__(BLOCK_ROW_THREADS, 2) k_row_block(ACsrView Ac,
       }
       kmin = s_misc[2];
       kmax = s_misc[3];
-      const uint64_t range = (uint64_t)((int64_t)kmax - (int64_t)kmin + 1);
+      const Interp ip = interp_make(kmin, kmax, n);
       for (int x = tid; x < n; x += nt) bst[x] = 0;
       __syncthreads();
       for (int i = tid; i < T; i += nt) {
         const int32_t k = keys[i];
-        if (k != EMPTY_KEY) atomicAdd(&bst[interp_bucket(k, kmin, n, range)], 1);
+        if (k != EMPTY_KEY) atomicAdd(&bst[interp_bucket(ip, k)], 1);
       }
       __syncthreads();
       // exclusive scan of the n bucket sizes: each thread a contiguous segment
@@ -481,7 +560,7 @@ __global__ void __launch_bounds__(BLOCK_ROW_THREADS, 2) k_row_block(ACsrView Ac,
       __syncthreads();
       for (int i = tid; i < T; i += nt) {
         const int32_t k = keys[i];
-        if (k != EMPTY_KEY) srt[atomicAdd(&bcur[interp_bucket(k, kmin, n, range)], 1)] = k;
+        if (k != EMPTY_KEY) srt[atomicAdd(&bcur[interp_bucket(ip, k)], 1)] = k;
       }
       __syncthreads();
       int rk[BLOCK_ROW_SPT];
@@ -492,7 +571,7 @@ __global__ void __launch_bounds__(BLOCK_ROW_THREADS, 2) k_row_block(ACsrView Ac,
         if (i < T) {
           const int32_t k = keys[i];
           if (k != EMPTY_KEY) {
-            const int b = interp_bucket(k, kmin, n, range);
+            const int b = interp_bucket(ip, k);
             int r = bst[b];
             for (int y = bst[b], ye = bcur[b]; y < ye; ++y) r += srt[y] < k;
             rk[j] = r;

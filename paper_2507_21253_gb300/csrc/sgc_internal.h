@@ -65,6 +65,7 @@ struct ResolvedOptions {
   int load_pct;
   int fused;
   int cl_load;  // numeric cluster-table fill limit, percent
+  int lean;     // numeric: 1 = warp-per-cluster kernel where it fits
 };
 ResolvedOptions resolve(const sgc_options* opt);
 

@@ -43,14 +43,17 @@ struct CView {
 
 // Work bins (k_bins.cuh): NDB dense-kernel budget classes, NRB row-hash table
 // sizes (log2 T = LOG2T_MIN..LOG2T_MAX), one heavy-row list.
-constexpr int NDB = 13;  // per-warp shared-memory classes of the cluster kernel
+constexpr int NDB = 13;  // per-group shared-memory classes of the cluster kernel
 constexpr int NRB = LOG2T_MAX - LOG2T_MIN + 1;
 constexpr int BIN_HEAVY = NDB + NRB;
-constexpr int NBIN_ALL = NDB + NRB + 1;
+constexpr int NLB = 6;   // per-warp classes of the warp-per-cluster numeric kernel
+constexpr int BIN_LEAN0 = NDB + NRB + 1;
+constexpr int NBIN_ALL = NDB + NRB + 1 + NLB;
 
 struct BinOut {
   int32_t* count;        // NBIN_ALL
   int32_t* dense_items;  // NDB * ncl
+  int32_t* lean_items;   // NLB * ncl (numeric phase; may be NULL: no warp-per-cluster kernel)
   int64_t* row_items;    // NRB * nrows
   int64_t* heavy_items;  // nrows
   int32_t* uc_rec;       // ncl: staged B elements per cluster
@@ -122,7 +125,7 @@ cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, 
 cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const int32_t* ncap_in,
                             float margin, float scale, const int32_t* uc, const int32_t* h_pos, int32_t* ncap_out,
                             int64_t* capw, int32_t* flag, int32_t* flist, int32_t* flist_count, const BinOut& lb,
-                            int in_bytes, int acc_bytes, int bulk, int cl_load, int sms, cudaStream_t s);
+                            int in_bytes, int acc_bytes, int bulk, int cl_load, int lean, int sms, cudaStream_t s);
 cudaError_t compact_run(const AClusterView& A, const int32_t* flag, const int64_t* slab_off, const int32_t* slab_col,
                         const void* slab_val, int val_bytes, const int64_t* c_rp, int32_t* ccol, void* cval, int sms,
                         cudaStream_t s);

@@ -63,6 +63,24 @@ def test_clusterwise(sgc, name, A, clus, staging, layout):
     compare(C, A, A, exact_f64=(A.val.dtype == np.float64))
 
 
+KERNEL_CASES = [c for c in CASES if c[0] in ("laplacian64", "rand_f32", "rand_i64", "rmat12_f32", "planted",
+                                             "stencil14")]
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+@pytest.mark.parametrize("kernel", [1, 0], ids=["warp_per_cluster", "warp_groups"])
+@pytest.mark.parametrize("name,A", KERNEL_CASES, ids=[c[0] for c in KERNEL_CASES])
+def test_cluster_kernels(sgc, name, A, kernel, fused):
+    """The numeric phase with one warp per (small) cluster and with warp groups for
+    every cluster give the same C (FP64 bit-identical to the oracle unless fused)."""
+    perm, cptr = synth.random_clusters(A.nrows, 13, kmax=8)
+    Ad = dev(sgc, A)
+    for layout in (0, 1):
+        Acl = sgc.csr_cluster_build(Ad, perm, cptr, layout)
+        C = sgc.spgemm(Acl, Ad, sgc.options(cluster_kernel=kernel, fused_fma=fused))
+        compare(C, A, A, exact_f64=(A.val.dtype == np.float64 and not fused))
+
+
 def test_cluster_format_matches_oracle(sgc):
     from oracle import csr_cluster as occ
     A = random_sparse(200, 120, 0.06, 3, "f64")
