@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import re
 import os
 import subprocess
 import sys
@@ -182,15 +183,39 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_from_profiles(kernel_key: str, workload: str):
-    """Per-launch DRAM bytes recorded by an ncu capture summarised under profiles/."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+NUMERIC_KERNEL_SOURCES = ("k_cluster.cuh", "k_lean.cuh", "k_rows.cuh", "k_bins.cuh", "k_launch.cuh",
+                          "sgc_device.cuh", "sgc_kernels.h", "sgc_internal.h", "k_phase_f32.cu", "k_phase_f64.cu",
+                          "k_phase_i64.cu", "k_phase_sym.cu", "capi.cu")
+
+
+def numeric_sources_digest() -> str:
+    """sha256 over the sources that define the numeric phase's kernels and launches."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in NUMERIC_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2507_21253_gb300", "csrc", f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(workload: str):
+    """Per-launch DRAM bytes of the numeric phase from the ncu summary under profiles/,
+    or None when the summary has no figure for the workload or the kernels changed since."""
+    p = os.path.join(ROOT, "profiles", "traffic_cluster_numeric_stencil27.md")
     if not os.path.exists(p):
         return None
+    digest, value = None, None
     with open(p) as fh:
-        d = json.load(fh)
-    e = d.get(workload, {}).get(kernel_key)
-    return e
+        for line in fh:
+            m = re.match(r"\s*sources digest:\s*(\w+)", line)
+            if m:
+                digest = m.group(1)
+            m = re.match(r"\s*traffic per launch, %s:\s*([0-9]+)" % re.escape(workload), line)
+            if m:
+                value = int(m.group(1))
+    if value is None or digest != numeric_sources_digest():
+        return None
+    return value
 
 
 # ---------------------------------------------------------------------------
@@ -373,7 +398,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     num_avg = float(np.mean(num_ms))
     peak, peak_kind = measured_peaks()
     achieved = num_bytes / (num_avg * 1e-3) / 1e9
-    traffic = traffic_from_profiles("cluster_numeric", args.workload)
+    traffic = traffic_from_profiles(args.workload)
     compulsory = 2 * csr_bytes(A) + c_bytes
 
     # ---- end to end through the public API, host buffers -----------------------

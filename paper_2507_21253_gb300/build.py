@@ -40,7 +40,8 @@ def _stale(target: str, deps) -> bool:
 
 def _compile(src: str, extra) -> str:
     obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
-    cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+    host = ["-Xcompiler", "-fopenmp"] if src.endswith(".cpp") else []
+    cmd = [NVCC, *ARCH, *FLAGS, *host, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -59,7 +60,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lgomp"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -10,6 +10,8 @@
 //  * heap order: higher score first (exact, cross-multiplied), then smaller i,
 //    then smaller j; pairs are stored once with i < j;
 //  * clusters are ordered by their smallest row (the root), rows ascending.
+#include <parallel/algorithm>
+
 #include <algorithm>
 #include <cstdint>
 #include <queue>
@@ -63,38 +65,63 @@ inline uint64_t pkey(int32_t i, int32_t j) { return ((uint64_t)(uint32_t)i << 32
 
 // n rows; rp/col: host copy of A's pattern; cand arrays: n*topk (j = -1: none).
 // Writes perm[n] and cluster_ptr[ncl+1]; returns ncl.
+//
+// The candidate pairs are popped in priority order from two sources: the
+// original candidates, sorted once (in parallel), and a heap that holds only
+// the pairs re-scored during the merge.  "Was (a, b) ever a candidate" is a
+// scan of the two rows' candidate lists plus a set of the re-scored pairs.
 int64_t hc_merge_host(int64_t n, const int64_t* rp, const int32_t* col, const int32_t* cj, const int32_t* cc,
                       const int32_t* cu, int topk, double th, int max_cluster, int32_t* perm, int64_t* cluster_ptr) {
-  // unique candidate pairs (i < j)
-  std::vector<HPair> pairs;
-  pairs.reserve((size_t)n * (size_t)topk / 2 + 16);
-  for (int64_t i = 0; i < n; ++i)
+  auto in_list = [&](int64_t row, int32_t x) {
+    const int32_t* L = cj + row * topk;
+    for (int s = 0; s < topk && L[s] >= 0; ++s)
+      if (L[s] == x) return true;
+    return false;
+  };
+  // unique candidate pairs (i < j): a pair in both rows' lists is taken from the smaller row
+  std::vector<int64_t> start((size_t)n + 1, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t c = 0;
     for (int s = 0; s < topk; ++s) {
       const int32_t j = cj[i * topk + s];
       if (j < 0) break;
-      const int32_t a = (int32_t)std::min<int64_t>(i, j), b = (int32_t)std::max<int64_t>(i, j);
-      pairs.push_back(HPair{cc[i * topk + s], cu[i * topk + s], a, b});
+      c += (i < j || !in_list(j, (int32_t)i)) ? 1 : 0;
     }
-  std::sort(pairs.begin(), pairs.end(), [](const HPair& x, const HPair& y) {
-    return x.i != y.i ? x.i < y.i : x.j < y.j;
-  });
-  pairs.erase(std::unique(pairs.begin(), pairs.end(),
-                          [](const HPair& x, const HPair& y) { return x.i == y.i && x.j == y.j; }),
-              pairs.end());
-  // sorted keys of the original candidates, plus pairs added by rescoring
-  std::vector<uint64_t> orig(pairs.size());
-  for (size_t q = 0; q < pairs.size(); ++q) orig[q] = pkey(pairs[q].i, pairs[q].j);
+    start[(size_t)i + 1] = c;
+  }
+  for (int64_t i = 0; i < n; ++i) start[(size_t)i + 1] += start[(size_t)i];
+  std::vector<HPair> pairs((size_t)start[(size_t)n]);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t o = start[(size_t)i];
+    for (int s = 0; s < topk; ++s) {
+      const int32_t j = cj[i * topk + s];
+      if (j < 0) break;
+      if (i < j || !in_list(j, (int32_t)i))
+        pairs[(size_t)o++] = HPair{cc[i * topk + s], cu[i * topk + s], (int32_t)std::min<int64_t>(i, j),
+                                   (int32_t)std::max<int64_t>(i, j)};
+    }
+  }
+  const Lower lower;
+  // highest priority first
+  __gnu_parallel::sort(pairs.begin(), pairs.end(), [&](const HPair& x, const HPair& y) { return lower(y, x); });
   std::unordered_set<uint64_t> added;
   auto is_cand = [&](int32_t a, int32_t b) {
-    const uint64_t k = pkey(a, b);
-    return std::binary_search(orig.begin(), orig.end(), k) || added.count(k) != 0;
+    return in_list(a, b) || in_list(b, a) || added.count(pkey(a, b)) != 0;
   };
-  std::priority_queue<HPair, std::vector<HPair>, Lower> heap(Lower(), std::move(pairs));
+  std::priority_queue<HPair, std::vector<HPair>, Lower> heap;  // re-scored pairs only
+  size_t next = 0;
   std::vector<int32_t> parent((size_t)n), size((size_t)n, 1);
   for (int64_t r = 0; r < n; ++r) parent[(size_t)r] = (int32_t)r;
-  while (!heap.empty()) {
-    const HPair t = heap.top();
-    heap.pop();
+  while (next < pairs.size() || !heap.empty()) {
+    HPair t;
+    if (!heap.empty() && (next == pairs.size() || lower(pairs[next], heap.top()))) {
+      t = heap.top();
+      heap.pop();
+    } else {
+      t = pairs[next++];
+    }
     if (parent[t.i] == t.i && parent[t.j] == t.j) {
       if (size[t.i] + size[t.j] <= max_cluster) {
         const int32_t lo = std::min(t.i, t.j), hi = std::max(t.i, t.j);
