@@ -114,7 +114,15 @@ int64_t hc_merge_host(int64_t n, const int64_t* rp, const int32_t* col, const in
   size_t next = 0;
   std::vector<int32_t> parent((size_t)n), size((size_t)n, 1);
   for (int64_t r = 0; r < n; ++r) parent[(size_t)r] = (int32_t)r;
+  constexpr size_t AHEAD = 48;  // pairs whose union-find and candidate-list entries are fetched ahead
   while (next < pairs.size() || !heap.empty()) {
+    if (next + AHEAD < pairs.size()) {
+      const HPair& f = pairs[next + AHEAD];
+      __builtin_prefetch(&parent[(size_t)f.i]);
+      __builtin_prefetch(&parent[(size_t)f.j]);
+      __builtin_prefetch(cj + (int64_t)f.i * topk);
+      __builtin_prefetch(cj + (int64_t)f.j * topk);
+    }
     HPair t;
     if (!heap.empty() && (next == pairs.size() || lower(pairs[next], heap.top()))) {
       t = heap.top();
@@ -133,6 +141,9 @@ int64_t hc_merge_host(int64_t n, const int64_t* rp, const int32_t* col, const in
     const int32_t ri = find_root(parent, t.i), rj = find_root(parent, t.j);
     if (ri == rj) continue;
     const int32_t a = std::min(ri, rj), b = std::max(ri, rj);
+    // roots whose clusters can never merge (sizes only grow): scoring them could only
+    // push pairs that are popped without effect, so the clustering is the same
+    if (size[a] + size[b] > max_cluster) continue;
     if (is_cand(a, b)) continue;
     int64_t inter, uni;
     overlap(rp, col, a, b, &inter, &uni);
