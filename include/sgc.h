@@ -271,6 +271,23 @@ int spgemm_rowwise_numeric(const sgc_csr* A, const sgc_csr* B, sgc_csr* C, void*
  * the host (A's pattern is copied to the host).  Synchronises.
  * ------------------------------------------------------------------------- */
 int hcluster_workspace_size(const sgc_csr* A, int32_t max_cluster, size_t* bytes);
+
+/* Cluster sources over A's own row order (Sec. 3.2), for comparison with
+ * hierarchical clustering.  Both give perm = identity (position -> row),
+ * cluster_ptr (device, int64, nclusters + 1 entries; at most nrows + 1) and
+ * *nclusters_host.
+ * cluster_fixed_length: clusters of K consecutive rows (1 <= K <= 32), the
+ *   last one shorter.  Asynchronous.
+ * cluster_variable_length: Algorithm 2.  A cluster's first row is its
+ *   representative; the following row joins while Jaccard(representative,
+ *   row) >= jacc_th (tested as inter >= jacc_th * union in FP64; an empty
+ *   union ends the cluster) and the cluster has fewer than max_cluster rows
+ *   (1..32).  The per-row run lengths are computed on the device; the chain of
+ *   cluster starts is followed on the host.  Synchronises the stream. */
+int cluster_fixed_length(int64_t nrows, int32_t K, int32_t* perm, int64_t* cluster_ptr, int64_t* nclusters_host,
+                         void* stream);
+int cluster_variable_length(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm,
+                            int64_t* cluster_ptr, int64_t* nclusters_host, void* stream);
 int hcluster_candidates(const sgc_csr* A, float jacc_th, int32_t topk, int32_t* cand_j, int32_t* cand_inter,
                         int32_t* cand_union, void* ws, size_t ws_bytes, void* stream);
 int hcluster_reorder(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm, int64_t* cluster_ptr,

@@ -483,6 +483,39 @@ int hcluster_candidates(const sgc_csr* A, float jacc_th, int32_t topk, int32_t* 
   return SGC_OK;
 }
 
+int cluster_fixed_length(int64_t nrows, int32_t K, int32_t* perm, int64_t* cluster_ptr, int64_t* nclusters_host,
+                         void* stream) {
+  if (nrows < 0 || K < 1 || K > 32) SGC_FAIL(SGC_INVALID_ARG, "nrows >= 0 and K in 1..32 required");
+  if (!nclusters_host || !cluster_ptr || (nrows > 0 && !perm)) SGC_FAIL(SGC_INVALID_ARG, "NULL output");
+  const int64_t ncl = (nrows + K - 1) / K;
+  *nclusters_host = ncl;
+  SGC_CUDA(fixed_clusters_run(nrows, K, perm, cluster_ptr, num_sms(), (cudaStream_t)stream));
+  return SGC_OK;
+}
+
+int cluster_variable_length(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm,
+                            int64_t* cluster_ptr, int64_t* nclusters_host, void* stream) {
+  int rc = check_csr(A, "A", false);
+  if (rc) return rc;
+  if (max_cluster < 1 || max_cluster > 32) SGC_FAIL(SGC_INVALID_ARG, "max_cluster must be in 1..32");
+  if (!nclusters_host || !cluster_ptr || (A->nrows > 0 && !perm)) SGC_FAIL(SGC_INVALID_ARG, "NULL output");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->nrows;
+  std::vector<uint8_t> run((size_t)(n > 0 ? n : 1));
+  std::vector<int64_t> hcp((size_t)n + 1);
+  if (n > 0) {  // perm's memory holds the per-row run lengths until the clusters are known
+    SGC_CUDA(vlen_runs_run(A->row_ptr, A->col, n, (double)jacc_th, max_cluster, (uint8_t*)perm, num_sms(), s));
+    SGC_CUDA(cudaMemcpyAsync(run.data(), perm, (size_t)n, cudaMemcpyDeviceToHost, s));
+    SGC_CUDA(cudaStreamSynchronize(s));
+  }
+  const int64_t ncl = vlen_chain_host(run.data(), n, max_cluster, hcp.data());
+  SGC_CUDA(cudaMemcpyAsync(cluster_ptr, hcp.data(), sizeof(int64_t) * (ncl + 1), cudaMemcpyHostToDevice, s));
+  if (n > 0) SGC_CUDA(fixed_clusters_run(n, 1, perm, nullptr, num_sms(), s));
+  SGC_CUDA(cudaStreamSynchronize(s));  // hcp is host memory of this call
+  *nclusters_host = ncl;
+  return SGC_OK;
+}
+
 int hcluster_reorder(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm, int64_t* cluster_ptr,
                      int64_t* nclusters_host, void* ws, size_t ws_bytes, void* stream) {
   int rc = check_csr(A, "A", false);

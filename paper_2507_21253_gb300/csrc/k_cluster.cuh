@@ -358,21 +358,25 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
         const uint32_t m = d.mask[i];
         const int n = d.len[i];
         const int dc = d.off_c[i] & 0x7fffffff;
-        for (int q = lane; q < n; q += 32) {
-          bool nwk;
-          const int slot = hash_find_or_insert(table, LH, stage_c[dc + q], &nwk);
-          if (slot < 0) {
-            full = true;
-            continue;
+        for (int qb = 0; qb < n; qb += 32) {  // all lanes take every step
+          const int q = qb + lane;
+          int slot = -1;
+          bool nwk = false;
+          if (q < n) {
+            slot = hash_find_or_insert(table, LH, stage_c[dc + q], &nwk);
+            if (slot < 0) full = true;
           }
-          newk += nwk;
-          const uint32_t bit = 1u << (slot & 31);
-          uint32_t* w0 = rb + (slot >> 5);
-          uint32_t mm = m;
-          while (mm) {
-            const int l = __ffs(mm) - 1;
-            mm &= mm - 1;
-            atomicOr(w0 + (size_t)l * WPR, bit);
+          __syncwarp();  // reconverge after the probes: the bitmap updates issue once
+          if (slot >= 0) {
+            newk += nwk;
+            const uint32_t bit = 1u << (slot & 31);
+            uint32_t* w0 = rb + (slot >> 5);
+            uint32_t mm = m;
+            while (mm) {
+              const int l = __ffs(mm) - 1;
+              mm &= mm - 1;
+              atomicOr(w0 + (size_t)l * WPR, bit);
+            }
           }
         }
       }
@@ -394,15 +398,19 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       for (int64_t i = wg; i < T; i += gw) {
         const int n = d.len[i];
         const int dc = d.off_c[i] & 0x7fffffff;
-        for (int q = lane; q < n; q += 32) {
-          bool nwk;
-          const int slot = hash_find_or_insert(table, LH, stage_c[dc + q], &nwk);
-          if (slot < 0) {
-            full = true;
-            continue;
+        for (int qb = 0; qb < n; qb += 32) {  // all lanes take every step
+          const int q = qb + lane;
+          int slot = -1;
+          bool nwk = false;
+          if (q < n) {
+            slot = hash_find_or_insert(table, LH, stage_c[dc + q], &nwk);
+            if (slot < 0) full = true;
           }
-          newk += nwk;
-          stage_c[dc + q] = slot;
+          __syncwarp();
+          if (slot >= 0) {
+            newk += nwk;
+            stage_c[dc + q] = slot;
+          }
         }
       }
       newk = warp_sum(newk);

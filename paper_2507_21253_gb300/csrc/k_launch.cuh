@@ -34,11 +34,12 @@ template <bool SYM, int DT, int SRC>
 cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const BView& B, const CView& C,
                             int64_t* c_rp, const BinOut& bins, void* status, const Launch& L) {
   using Acc = typename VT<DT>::Acc;
-  auto kh = k_row_hash<SYM, DT, SRC>;
+  auto kh = L.o.fused ? k_row_hash<SYM, DT, SRC, true> : k_row_hash<SYM, DT, SRC, false>;
   auto kb = k_row_block<SYM, DT, SRC>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = allow_smem(kh);
+    cudaError_t e = allow_smem(k_row_hash<SYM, DT, SRC, true>);
+    if (e == cudaSuccess) e = allow_smem(k_row_hash<SYM, DT, SRC, false>);
     if (e == cudaSuccess) e = allow_smem(kb);
     if (e != cudaSuccess) return e;
   }

@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(256) k_cluster_lean(AClusterView A, BView B, C
       }
       cp_async_commit();
     };
-    // f(t, q, j, v) for every element in (t, q) order; lanes hold one segment at a time
+    // f(ok, t, j, v) for every segment in (t, q) order, called by all lanes (ok: the
+    // lane holds an element); lanes hold one segment at a time
     auto stream = [&](bool with_val, auto&& f) {
       int pt = 0, ps = 0;
       normalize(pt, ps);
@@ -208,7 +209,8 @@ __global__ void __launch_bounds__(256) k_cluster_lean(AClusterView A, BView B, C
       while (ct < T) {
         cp_async_wait<RING - 1>();
         const int q = cs * 32 + lane;
-        if (q < dl[ct]) f(ct, q, ring_j[slot * 32 + lane], with_val ? ring_v[slot * 32 + lane] : In{});
+        const bool ok = q < dl[ct];
+        f(ok, ct, ok ? ring_j[slot * 32 + lane] : 0, (ok && with_val) ? ring_v[slot * 32 + lane] : In{});
         __syncwarp();  // the next item's lanes read what these lanes wrote
         issue(pt, ps, slot, with_val);
         ++ps;
@@ -225,7 +227,8 @@ __global__ void __launch_bounds__(256) k_cluster_lean(AClusterView A, BView B, C
     bool full = false;
     int newk = 0;
     int32_t kmin = PAD_KEY, kmax = -1;
-    stream(false, [&](int, int, int32_t j, In) {
+    stream(false, [&](bool ok, int, int32_t j, In) {
+      if (!ok) return;
       bool nw;
       const int slot = hash_find_or_insert(table, LH, j, &nw);
       if (slot < 0) {
@@ -334,12 +337,11 @@ __global__ void __launch_bounds__(256) k_cluster_lean(AClusterView A, BView B, C
       return -1;
     };
     bool lost = false;
-    stream(true, [&](int t, int, int32_t j, In v) {
-      const int r = rank_of(j);
-      if (r < 0) {
-        lost = true;
-        return;
-      }
+    stream(true, [&](bool ok, int t, int32_t j, In v) {
+      const int r = ok ? rank_of(j) : -1;
+      if (ok && r < 0) lost = true;
+      __syncwarp();  // reconverge after the probes: the FP64 updates issue once for the warp
+      if (r < 0) return;
       const uint32_t m = dm[t];
       const int ao = da[t];
       uint32_t mm = m;

@@ -174,7 +174,7 @@ __device__ __forceinline__ void bulk_prefetch_row(const void* base, int64_t s, i
 // Shared memory per warp: keys[T], and for numeric vals[T] plus 3*T ints of
 // ranking scratch.
 // ---------------------------------------------------------------------------
-template <bool SYM, int DT, int SRC>
+template <bool SYM, int DT, int SRC, bool FUSED>
 __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl, BView B, CView C,
                                                   int64_t* c_rp_sym, const int64_t* items,
                                                   const int32_t* count_ptr, int log2T, int fused, int pf,
@@ -205,15 +205,21 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
     __syncwarp();
     int64_t cnt = 0;
     bool full = false;
-    auto process = [&](int32_t j, In v, In a) {
-      bool nw;
-      const int slot = hash_find_or_insert(keys, log2T, j, &nw);
-      if (slot < 0) {
-        full = true;
-      } else if constexpr (SYM) {
-        cnt += nw;
+    // One 32-element step, called by all lanes (ok: this lane has an element).
+    // The lanes reconverge after the hash probes, so the FP64 update of the
+    // step issues once for the warp, not once per divergent probe path.
+    auto process = [&](bool ok, int32_t j, In v, In a) {
+      int slot = -1;
+      bool nw = false;
+      if (ok) {
+        slot = hash_find_or_insert(keys, log2T, j, &nw);
+        if (slot < 0) full = true;
+      }
+      if constexpr (SYM) {
+        cnt += (slot >= 0 && nw);
       } else {
-        vals[slot] = VT<DT>::madd(vals[slot], a, v, fused != 0);
+        __syncwarp();
+        if (slot >= 0) vals[slot] = VT<DT>::madd(vals[slot], a, v, FUSED);
       }
     };
     // One chunk of up to 32 entries (k, a_ik) of the row, one per lane, B row
@@ -251,8 +257,12 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
             if (!SYM) vn = ((const In*)B.val)[sn + lane];
           }
         }
-        if (si + lane < ei) process(j, v, ai);
-        for (int64_t q = si + 32 + lane; q < ei; q += 32) process(B.col[q], SYM ? In{} : ((const In*)B.val)[q], ai);
+        process(si + lane < ei, j, v, ai);
+        for (int64_t qb = si + 32; qb < ei; qb += 32) {
+          const int64_t q = qb + lane;
+          const bool ok = q < ei;
+          process(ok, ok ? B.col[q] : 0, (ok && !SYM) ? ((const In*)B.val)[q] : In{}, ai);
+        }
         __syncwarp();
         if (!bits) break;
       }
@@ -476,23 +486,28 @@ __global__ void __launch_bounds__(BLOCK_ROW_THREADS, 2) k_row_block(ACsrView Ac,
       }
       __syncthreads();
       int e0 = 0;  // entry of the previous product: the search starts there
-      for (int64_t p = tid; p < P && !full; p += nt) {
-        int hi = n - 1;
-        while (e0 < hi) {
-          const int mid = (e0 + hi + 1) >> 1;
-          if (s_pre[mid] <= p) e0 = mid; else hi = mid - 1;
-        }
-        const int64_t q = s_off[e0] + p;
-        bool nw;
-        const int slot = hash_find_or_insert(keys, log2T, B.col[q], &nw);
-        if (slot < 0) {
-          full = true;
-          break;
+      // every lane of a warp runs the same number of steps, so the lanes
+      // reconverge after the hash probes and the FP64 update issues once a step
+      for (int64_t pb = 0; pb < P && !__any_sync(FULL, full); pb += nt) {
+        const int64_t p = pb + tid;
+        int slot = -1;
+        bool nw = false;
+        int64_t q = 0;
+        if (p < P) {
+          int hi = n - 1;
+          while (e0 < hi) {
+            const int mid = (e0 + hi + 1) >> 1;
+            if (s_pre[mid] <= p) e0 = mid; else hi = mid - 1;
+          }
+          q = s_off[e0] + p;
+          slot = hash_find_or_insert(keys, log2T, B.col[q], &nw);
+          if (slot < 0) full = true;
         }
         if constexpr (SYM) {
-          cnt += nw;
+          cnt += (slot >= 0 && nw);
         } else {
-          VT<DT>::atomic_add(&vals[slot], VT<DT>::mul(s_a[e0], ((const In*)B.val)[q]));
+          __syncwarp();
+          if (slot >= 0) VT<DT>::atomic_add(&vals[slot], VT<DT>::mul(s_a[e0], ((const In*)B.val)[q]));
         }
       }
       __syncthreads();

@@ -130,6 +130,12 @@ cudaError_t compact_run(const AClusterView& A, const int32_t* flag, const int64_
                         const void* slab_val, int val_bytes, const int64_t* c_rp, int32_t* ccol, void* cval, int sms,
                         cudaStream_t s);
 
+// k_vlen.cu
+cudaError_t vlen_runs_run(const int64_t* rp, const int32_t* col, int64_t n, double th, int max_cluster, uint8_t* run,
+                          int sms, cudaStream_t s);
+int64_t vlen_chain_host(const uint8_t* run, int64_t n, int max_cluster, int64_t* cluster_ptr);
+cudaError_t fixed_clusters_run(int64_t n, int K, int32_t* perm, int64_t* cluster_ptr, int sms, cudaStream_t s);
+
 // k_hc.cu / hc_merge.cpp
 cudaError_t hc_candidates_run(const int64_t* arp, const int32_t* acol, int64_t nrows, int64_t ncols, int64_t nnz,
                               double th, int topk, int64_t* trp, int32_t* tcol, int32_t* cursor, int64_t* dummy_rp,

@@ -97,6 +97,9 @@ _c = {
                                 ctypes.c_size_t, vp),
     "hcluster_reorder": _sig("hcluster_reorder", P(CsrStruct), ctypes.c_float, i32, vp, vp, P(i64), vp,
                              ctypes.c_size_t, vp),
+    "cluster_fixed_length": _sig("cluster_fixed_length", i64, i32, vp, vp, P(i64), vp),
+    "cluster_variable_length": _sig("cluster_variable_length", P(CsrStruct), ctypes.c_float, i32, vp, vp, P(i64),
+                                    vp),
     "cluster_features": _sig("cluster_features", P(ClusterStruct), P(CsrStruct), vp, vp),
     "nnz_predictor_targets": _sig("nnz_predictor_targets", P(ClusterStruct), P(CsrStruct), vp, ctypes.c_size_t, vp,
                                   vp),
@@ -380,6 +383,27 @@ def hcluster_reorder(A: DeviceCsr, jacc_th: float = JACC_TH, max_cluster: int = 
     a = A.struct()
     _call("hcluster_reorder", ctypes.byref(a), float(jacc_th), max_cluster, _ptr(perm), _ptr(cptr),
           ctypes.byref(ncl), ws.ptr, ws.nbytes, _stream())
+    return perm[:A.nrows], cptr[:ncl.value + 1]
+
+
+def cluster_fixed_length(nrows: int, K: int, device="cuda"):
+    """Clusters of K consecutive rows: (perm = identity, cluster_ptr) on the device."""
+    perm = torch.empty(max(nrows, 1), dtype=torch.int32, device=device)
+    cptr = torch.empty(nrows + 1, dtype=torch.int64, device=device)
+    ncl = i64()
+    _call("cluster_fixed_length", nrows, K, _ptr(perm), _ptr(cptr), ctypes.byref(ncl), _stream())
+    return perm[:nrows], cptr[:ncl.value + 1]
+
+
+def cluster_variable_length(A: DeviceCsr, jacc_th: float = JACC_TH, max_cluster: int = MAX_CLUSTER):
+    """Algorithm 2 clusters over A's row order: (perm = identity, cluster_ptr) on the device."""
+    dev = A.row_ptr.device
+    perm = torch.empty(max(A.nrows, 1), dtype=torch.int32, device=dev)
+    cptr = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
+    ncl = i64()
+    a = A.struct()
+    _call("cluster_variable_length", ctypes.byref(a), float(jacc_th), max_cluster, _ptr(perm), _ptr(cptr),
+          ctypes.byref(ncl), _stream())
     return perm[:A.nrows], cptr[:ncl.value + 1]
 
 

@@ -92,3 +92,53 @@ def test_max_cluster_one(sgc):
     perm, cptr = sgc.hcluster_reorder(sgc.DeviceCsr.from_host(A), TH, 1)
     assert np.array_equal(perm.cpu().numpy(), np.arange(256))
     assert np.array_equal(cptr.cpu().numpy(), np.arange(257))
+
+
+def golden_alg2_matrix():
+    """The six rows of the Algorithm 2 worked example (tests/golden)."""
+    import os
+    rows, cols = [], []
+    path = os.path.join(os.path.dirname(__file__), "golden", "alg2_worked_example.txt")
+    for line in open(path):
+        if line.startswith("row "):
+            r, cs = line[4:].split(":")
+            for c in cs.split():
+                rows.append(int(r))
+                cols.append(int(c))
+    A = synth.csr_from_pattern(6, 12, np.array(rows), np.array(cols))
+    return A.with_values(np.ones(A.nnz))
+
+
+VLEN_CASES = [("golden", golden_alg2_matrix()),
+              ("stencil_natural", synth.stencil27_3d(12, 11, 10, seed=5, permute=False)),
+              ("laplacian64", synth.workload_laplacian(1)),
+              ("planted", synth.planted_groups(2048, 4002, permute=False)),
+              ("rand", random_sparse(300, 200, 0.03, 5, "f64"))]
+
+
+@pytest.mark.parametrize("max_cluster", [1, 2, 8, 32])
+@pytest.mark.parametrize("name,A", VLEN_CASES, ids=[c[0] for c in VLEN_CASES])
+def test_variable_length_matches_oracle(sgc, name, A, max_cluster):
+    perm, cptr = sgc.cluster_variable_length(sgc.DeviceCsr.from_host(A), TH, max_cluster)
+    rperm, rcptr = oh.variable_length(A, TH, max_cluster)
+    assert np.array_equal(perm.cpu().numpy(), rperm)
+    assert np.array_equal(cptr.cpu().numpy(), rcptr)
+    if name == "golden" and max_cluster == 8:
+        assert list(rcptr) == [0, 3, 5, 6]            # clusters {0,1,2}, {3,4}, {5} as printed
+
+
+@pytest.mark.parametrize("K", [1, 3, 8, 32])
+def test_fixed_length_clusters(sgc, K):
+    for n in (0, 1, 100, 1001):
+        perm, cptr = sgc.cluster_fixed_length(n, K)
+        rperm, rcptr = synth.fixed_clusters(n, K)
+        assert np.array_equal(perm.cpu().numpy(), rperm)
+        assert np.array_equal(cptr.cpu().numpy(), rcptr)
+
+
+def test_variable_length_product_exact(sgc):
+    A = synth.planted_groups(2048, 4002, permute=False)
+    Ad = sgc.DeviceCsr.from_host(A)
+    perm, cptr = sgc.cluster_variable_length(Ad, TH, 8)
+    C = sgc.spgemm(sgc.csr_cluster_build(Ad, perm, cptr), Ad)
+    compare(C, A, A, exact_f64=True)
