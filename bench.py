@@ -58,6 +58,10 @@ WORKLOADS = {
     "batched256": ("256 independent products A_i*A_i: n_i log-uniform in [1e3, 2e5], row lengths floor of a "
                    "power law (pdf ~ x^-2.1, mean 12, max 2000), uniform columns, FP64 N(0,1); packed "
                    "block-diagonally, one launch sequence captured in one CUDA graph, autotuned", None),
+    "tallskinny_rmat18": ("C = A*B, A = R-MAT scale 18 graph (edge factor 16, (0.57,0.19,0.19,0.05), unit FP64 "
+                          "weights), B = BFS frontiers at distance 2 from 512 seeded sources valued by shortest-path "
+                          "counts (square x tall-skinny, the forward sweep of betweenness centrality); hierarchical "
+                          "clustering of A + CSR_Cluster", lambda: synth.workload_tallskinny(6)),
     "planted1m": ("C = A*A, A = planted groups of 8 rows (n = 1,000,000, 11 of 16 shared columns + 5 random), "
                   "FP64, seeded symmetric permutation; hierarchical clustering + CSR_Cluster",
                   lambda: synth.workload_planted(4000)),
@@ -165,28 +169,36 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample of rows)
 # ---------------------------------------------------------------------------
-def row_flops(A) -> np.ndarray:
-    """Multiply-adds of each row of A*A (sum over a_ik of nnz(A_k))."""
-    per = np.diff(A.row_ptr)[A.col].astype(np.int64)
+def operands(make):
+    """(A, B) of a workload: generators return A (for C = A*A) or the pair."""
+    x = make()
+    return x if isinstance(x, tuple) else (x, x)
+
+
+def row_flops(A, B=None) -> np.ndarray:
+    """Multiply-adds of each row of A*B (sum over a_ik of nnz(B_k))."""
+    B = A if B is None else B
+    per = np.diff(B.row_ptr)[A.col].astype(np.int64)
     cs = np.concatenate([[0], np.cumsum(per)])
     return cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]
 
 
-def oracle_sample_rate(A, target_s: float, seed: int = 9, rf=None):
+def oracle_sample_rate(A, target_s: float, seed: int = 9, rf=None, B=None):
     """GFLOP/s of the CPU oracle (all host cores, rows over OpenMP threads) on a
     seeded random row sample sized to take about target_s seconds."""
     from oracle import gustavson as og
     og.build()
     threads = os.cpu_count() or 1
-    rf = row_flops(A) if rf is None else rf
+    B = A if B is None else B
+    rf = row_flops(A, B) if rf is None else rf
     probe = np.sort(synth.Stream(seed, 1).randint(A.nrows, 512)).astype(np.int64)
     t = time.perf_counter()
-    og.spgemm(A, A, rows=probe, want_mag=False, nthreads=threads)
+    og.spgemm(A, B, rows=probe, want_mag=False, nthreads=threads)
     dt = max(time.perf_counter() - t, 1e-4)
     want = max(512, min(A.nrows, int(512 * target_s / dt)))
     rows = np.sort(synth.Stream(seed, 2).randint(A.nrows, want)).astype(np.int64)
     t = time.perf_counter()
-    og.spgemm(A, A, rows=rows, want_mag=False, nthreads=threads)
+    og.spgemm(A, B, rows=rows, want_mag=False, nthreads=threads)
     dt = time.perf_counter() - t
     return 2.0 * float(rf[rows].sum()) / dt / 1e9, threads, int(rows.size), dt
 
@@ -242,17 +254,18 @@ def run_reference(args, rank: int):
     desc, make = WORKLOADS[args.workload]
     if make is None:   # the batch as one block-diagonal matrix (same products, same rows)
         A = synth.block_diag([synth.powerlaw_matrix(3000 + i) for i in range(args.batch)])
+        B = A
     else:
-        A = make()
-    flops = flops_of(A, A)
+        A, B = operands(make)
+    flops = flops_of(A, B)
     steps = []
     per_step_s = 8.0
-    rf = row_flops(A)
+    rf = row_flops(A, B)
     cores = os.cpu_count() or 1
     sample_rows = 0
     for s in range(args.warmup + args.steps):
         gf, cores, sample_rows, dt = oracle_sample_rate(A, per_step_s if s >= args.warmup else 1.0, seed=100 + s,
-                                                        rf=rf)
+                                                        rf=rf, B=B)
         if s >= args.warmup:
             steps.append(gf)
     value = float(np.mean(steps))
@@ -278,9 +291,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     desc, make = WORKLOADS[args.workload]
-    A = make()
-    flops = flops_of(A, A)
+    A, B = operands(make)
+    square = B is A
+    flops = flops_of(A, B)
     Ad = sgc.DeviceCsr.from_host(A, dev)
+    Bd = Ad if square else sgc.DeviceCsr.from_host(B, dev)
     torch.cuda.synchronize()
 
     def barrier():
@@ -299,16 +314,29 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     opt = sgc.options(fused_fma=args.fused_fma, cluster_load_pct=args.cluster_load,
                       cluster_kernel=args.cluster_kernel)
-    ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad, opt), dev)
-    rp, nnz = sgc.spgemm_symbolic(Acl, Ad, ws, opt)
-    C = sgc.spgemm_numeric(Acl, Ad, rp, nnz, ws, opt)
+    ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Bd, opt), dev)
+    rp, nnz = sgc.spgemm_symbolic(Acl, Bd, ws, opt)
+    C = sgc.spgemm_numeric(Acl, Bd, rp, nnz, ws, opt)
     sgc.workspace_status(ws)
     stream = torch.cuda.current_stream()
+
+    # inputs below twice the L2 (129 MB): overwrite a 258 MB buffer before each timed step
+    l2_bytes = 129 * 2**20
+    in_bytes = csr_bytes(A) + (0 if square else csr_bytes(B))
+    flush_buf = torch.empty(2 * l2_bytes // 4, dtype=torch.float32, device=dev) if in_bytes < 2 * l2_bytes else None
+
+    def flush():
+        if flush_buf is not None:
+            flush_buf.zero_()
+
+    l2_note = (f"inputs {in_bytes / 1e6:.0f} MB < 2x L2: a 258 MB buffer is written before each timed step"
+               if flush_buf is not None else f"inputs {in_bytes / 1e9:.2f} GB > 2x L2 (129 MB): no flush")
 
     def timed_loop(sym_fn, num_fn, steps):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
                torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for e0, e1, e2 in ev:
+            flush()
             e0.record(stream)
             sym_fn()
             e1.record(stream)
@@ -319,8 +347,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         num = [b.elapsed_time(c) for _, b, c in ev]
         return sym, num
 
-    sym_c = lambda: sgc.spgemm_symbolic(Acl, Ad, ws, opt, c_row_ptr=rp, sync=False)  # noqa: E731
-    num_c = lambda: sgc.spgemm_numeric(Acl, Ad, rp, nnz, ws, opt, C=C)  # noqa: E731
+    sym_c = lambda: sgc.spgemm_symbolic(Acl, Bd, ws, opt, c_row_ptr=rp, sync=False)  # noqa: E731
+    num_c = lambda: sgc.spgemm_numeric(Acl, Bd, rp, nnz, ws, opt, C=C)  # noqa: E731
     timed_loop(sym_c, num_c, args.warmup)
     barrier()
     torch.cuda.synchronize()
@@ -336,14 +364,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     exact_value = job_gflops(flops, world, step_ms)
 
     # ---- plain row-wise method, same GPU ---------------------------------------
-    wsr = sgc.Workspace(sgc.spgemm_rowwise_workspace_size(Ad, Ad, opt), dev)
-    rpr, nnzr = sgc.spgemm_rowwise_symbolic(Ad, Ad, wsr, opt)
+    wsr = sgc.Workspace(sgc.spgemm_rowwise_workspace_size(Ad, Bd, opt), dev)
+    rpr, nnzr = sgc.spgemm_rowwise_symbolic(Ad, Bd, wsr, opt)
     del C
     torch.cuda.empty_cache()
-    Cr = sgc.spgemm_rowwise_numeric(Ad, Ad, rpr, nnzr, wsr, opt)
+    Cr = sgc.spgemm_rowwise_numeric(Ad, Bd, rpr, nnzr, wsr, opt)
     sgc.workspace_status(wsr)
-    sym_r = lambda: sgc.spgemm_rowwise_symbolic(Ad, Ad, wsr, opt, c_row_ptr=rpr, sync=False)  # noqa: E731
-    num_r = lambda: sgc.spgemm_rowwise_numeric(Ad, Ad, rpr, nnzr, wsr, opt, C=Cr)  # noqa: E731
+    sym_r = lambda: sgc.spgemm_rowwise_symbolic(Ad, Bd, wsr, opt, c_row_ptr=rpr, sync=False)  # noqa: E731
+    num_r = lambda: sgc.spgemm_rowwise_numeric(Ad, Bd, rpr, nnzr, wsr, opt, C=Cr)  # noqa: E731
     timed_loop(sym_r, num_r, args.warmup)
     rsym, rnum = timed_loop(sym_r, num_r, args.steps)
     sgc.workspace_status(wsr)
@@ -353,14 +381,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # ---- clustered + learned: predictor trained on the GPU, symbolic-free path ---
     learned_out = None
-    if not args.no_learned:
+    if not args.no_learned and args.workload in TRAINING:
         from paper_2507_21253_gb300 import learned as lrn
         gen_name, ntrain = TRAINING[args.workload]
         t0 = time.perf_counter()
         params, tloss = lrn.train(getattr(lrn, gen_name), range(1000, 1000 + ntrain), epochs=4, device=dev)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
-        Lrn = sgc.LearnedSpgemm(Acl, Ad, params=params, margin=1.25, opt=opt)
+        Lrn = sgc.LearnedSpgemm(Acl, Bd, params=params, margin=1.25, opt=opt)
         Lrn.phase1()
         Cl = Lrn.phase2()
         sgc.workspace_status(Lrn.ws)
@@ -379,6 +407,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         l0 = sgc.kernel_launches()
         with ClockSampler(local_rank) as clk:      # the headline's timed region
             for e0, e1 in lev:
+                flush()
                 e0.record(stream)
                 learned_step()
                 e1.record(stream)
@@ -398,7 +427,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # ---- algorithmic bytes ----------------------------------------------------
     ucol = Acl.ucol.cpu().numpy()
-    staged = int(np.sum(np.diff(A.row_ptr)[ucol]))      # sum over clusters of the B elements staged
+    staged = int(np.sum(np.diff(B.row_ptr)[ucol]))      # sum over clusters of the B elements staged
     ncl = Acl.nclusters
     a_cl_bytes = 8 * 3 * (ncl + 1) + 4 * A.nrows + 8 * ucol.size + A.val.itemsize * Acl.val.numel()
     c_bytes = 8 * (A.nrows + 1) + nnz * (4 + A.val.itemsize)
@@ -408,13 +437,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     peak, peak_kind = measured_peaks()
     achieved = num_bytes / (num_avg * 1e-3) / 1e9
     traffic = traffic_from_profiles(args.workload)
-    compulsory = 2 * csr_bytes(A) + c_bytes
+    compulsory = csr_bytes(A) + csr_bytes(B) + c_bytes
 
     # ---- end to end through the public API, host buffers -----------------------
     e2e = None
     if not args.no_e2e:
         pin = lambda x: torch.from_numpy(x).pin_memory()  # noqa: E731
         h_rp, h_col, h_val = pin(A.row_ptr), pin(A.col), pin(A.val)
+        if not square:
+            h_brp, h_bcol, h_bval = pin(B.row_ptr), pin(B.col), pin(B.val)
         e_steps = max(1, min(args.steps, 3))
         h_out = None
         times = []
@@ -424,8 +455,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             Ad.row_ptr.copy_(h_rp, non_blocking=True)
             Ad.col.copy_(h_col, non_blocking=True)
             Ad.val.copy_(h_val, non_blocking=True)
+            if not square:
+                Bd.row_ptr.copy_(h_brp, non_blocking=True)
+                Bd.col.copy_(h_bcol, non_blocking=True)
+                Bd.val.copy_(h_bval, non_blocking=True)
             Acl2 = sgc.csr_cluster_build(Ad, perm, cptr, sgc.LAYOUT_MASKED)
-            C2 = sgc.spgemm(Acl2, Ad, opt)
+            C2 = sgc.spgemm(Acl2, Bd, opt)
             if h_out is None:
                 h_out = (torch.empty(C2.row_ptr.shape, dtype=torch.int64, pin_memory=True),
                          torch.empty(C2.col.shape, dtype=torch.int32, pin_memory=True),
@@ -439,6 +474,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             del C2, Acl2
         e_s = max_over_ranks(float(np.mean(times)), world, dev)
         h2d = int(h_rp.numel() * 8 + h_col.numel() * 4 + h_val.numel() * h_val.element_size())
+        if not square:
+            h2d += int(h_brp.numel() * 8 + h_bcol.numel() * 4 + h_bval.numel() * h_bval.element_size())
         d2h = int(h_out[0].numel() * 8 + h_out[1].numel() * 4 + h_out[2].numel() * h_out[2].element_size())
         e2e = {"value": round(job_gflops(flops, world, e_s * 1e3), 3), "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
@@ -447,7 +484,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        gf, cores, nrows_s, dt = oracle_sample_rate(A, 12.0)
+        gf, cores, nrows_s, dt = oracle_sample_rate(A, 12.0, B=B)
         cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                "sample": f"{nrows_s} random rows of C ({dt:.1f} s; serial std::map Gustavson per row, rows "
                          f"over {cores} OpenMP threads), rate scaled to GFLOP/s"}
@@ -463,7 +500,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "vs_baseline": None, "dtype": A.val.dtype.name.replace("float", "f").replace("int", "i"),
             "data": "synthetic",
             "config": {"workload": desc, "n": A.nrows, "nnz_A": A.nnz, "flops": flops, "nnz_C": nnz,
-                       "nclusters": ncl, "l2": "inputs larger than L2 (A and B = 1.3 GB each); no flush",
+                       "nclusters": ncl, "l2": l2_note,
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "method": "clustered+learned" if learned_out else "clustered (exact symbolic + numeric)",
             "clustered_exact": {"value": round(exact_value, 3), "unit": "GFLOP/s", "ms_per_step": round(step_ms, 4),

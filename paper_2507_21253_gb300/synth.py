@@ -229,6 +229,58 @@ def rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int,
 
 
 # --------------------------------------------------------------------------
+# Square x tall-skinny: BFS frontiers (the forward sweep of betweenness
+# centrality multiplies the graph by a block of frontiers, Sec. 4 workloads)
+# --------------------------------------------------------------------------
+def bfs_frontiers(A: Csr, nsrc: int, level: int, seed: int) -> Csr:
+    """n x nsrc matrix whose column s is the BFS frontier at distance `level`
+    (following A's rows) from a seeded random source, valued by the number of
+    shortest paths from the source (FP64).  Columns whose BFS dies out early
+    are empty."""
+    n = A.nrows
+    src = Stream(seed, 88).randint(n, nsrc)
+    rows, cols, vals = [], [], []
+    rp, ci = A.row_ptr, A.col
+    for s_idx, s in enumerate(src.tolist()):
+        dist = np.full(n, -1, dtype=np.int32)
+        sigma = np.zeros(n, dtype=np.float64)
+        dist[s], sigma[s] = 0, 1.0
+        frontier = np.array([s], dtype=np.int64)
+        for L in range(1, level + 1):
+            starts, lens = rp[frontier], rp[frontier + 1] - rp[frontier]
+            tot = int(lens.sum())
+            if tot == 0:
+                frontier = frontier[:0]
+                break
+            offs = np.repeat(starts - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens) + np.arange(tot)
+            nb = ci[offs].astype(np.int64)
+            w = np.repeat(sigma[frontier], lens)
+            new = dist[nb] == -1                      # first reached at this level
+            v, w = nb[new], w[new]
+            np.add.at(sigma, v, w)
+            dist[v] = L
+            frontier = _sorted_unique(v)
+        rows.append(frontier)
+        cols.append(np.full(frontier.size, s_idx, dtype=np.int64))
+        vals.append(sigma[frontier])
+    r = np.concatenate(rows) if rows else np.zeros(0, dtype=np.int64)
+    c = np.concatenate(cols) if cols else np.zeros(0, dtype=np.int64)
+    v = np.concatenate(vals) if vals else np.zeros(0)
+    order = np.lexsort((c, r))
+    B = Csr(n, nsrc, np.zeros(n + 1, dtype=np.int64), c[order].astype(np.int32), v[order])
+    np.cumsum(np.bincount(r, minlength=n), out=B.row_ptr[1:])
+    return B
+
+
+def workload_tallskinny(seed: int = 6, scale: int = 18, nsrc: int = 512, level: int = 2):
+    """(A, B): A = R-MAT graph (scale, edge factor 16, (.57,.19,.19,.05)) with unit
+    FP64 weights, B = its BFS frontiers at `level` from nsrc sources."""
+    G = rmat(scale, 16, 0.57, 0.19, 0.19, seed, "f64")
+    A = G.with_values(np.ones(G.nnz))
+    return A, bfs_frontiers(A, nsrc, level, seed)
+
+
+# --------------------------------------------------------------------------
 # Workload 3: batches of power-law row-length matrices
 # --------------------------------------------------------------------------
 POWERLAW_EXPONENT = 2.1     # density exponent: pdf(x) ~ x^-2.1 on [x_min, x_max]

@@ -106,6 +106,20 @@ def test_rmat16(sgc, dtype):
     run_all(sgc, A, learned_gen="rmat_instance", exact_f64=False)
 
 
+def test_tallskinny_rmat18(sgc):
+    """Square x tall-skinny at the benchmark's size: R-MAT scale 18 times 512 BFS frontiers."""
+    A, B = synth.workload_tallskinny(6)
+    Ad, Bd = sgc.DeviceCsr.from_host(A), sgc.DeviceCsr.from_host(B)
+    rows = sample(A)
+    Cr = sgc.spgemm_rowwise(Ad, Bd)
+    well_formed(Cr, B.ncols)
+    compare(Cr, A, B, rows=rows)
+    Cc = sgc.spgemm(clustered(sgc, Ad), Bd)
+    well_formed(Cc, B.ncols)
+    compare(Cc, A, B, rows=rows)
+    same_result(Cc, Cr, exact_values=False)
+
+
 def test_batched_256(sgc):
     """The batch as the benchmark runs it: block-diagonal packing, hierarchical
     clustering, one CUDA graph; each product's block on sampled rows."""

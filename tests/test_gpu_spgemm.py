@@ -173,6 +173,20 @@ def test_row_tiers(sgc, dtype, load):
     compare(sgc.spgemm(sgc.csr_cluster_build(Ad, perm, cptr, 1), Bd, opt), A, B)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "i64"])
+def test_square_times_tall_skinny(sgc, dtype):
+    """A (R-MAT graph) times B (its BFS frontiers, 96 columns, path counts)."""
+    A, B = synth.workload_tallskinny(7, scale=11, nsrc=96, level=2)
+    if dtype == "i64":
+        A = A.with_values(np.ones(A.nnz, dtype=np.int64))
+        B = B.with_values(np.rint(B.val).astype(np.int64))
+    Ad, Bd = dev(sgc, A), dev(sgc, B)
+    compare(sgc.spgemm_rowwise(Ad, Bd), A, B, exact_f64=True)
+    perm, cptr = sgc.hcluster_reorder(Ad)
+    for layout in (0, 1):
+        compare(sgc.spgemm(sgc.csr_cluster_build(Ad, perm, cptr, layout), Bd), A, B, exact_f64=True)
+
+
 def test_rectangular_and_empty_rows(sgc):
     A = random_sparse(90, 70, 0.05, 31, "f64")
     B = random_sparse(70, 300, 0.02, 32, "f64")
