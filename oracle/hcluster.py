@@ -132,6 +132,70 @@ def hierarchical(A, th: float, max_cluster: int):
     return np.array(perm, dtype=np.int32), np.array(cluster_ptr, dtype=np.int64)
 
 
+def handshake(A, th: float, max_cluster: int):
+    """Round-parallel variant of Algorithm 3's merge (not in the paper; the
+    library's GPU-parallel hierarchical clustering).  The candidate edges are
+    those of Algorithm 3 (candidate_pairs with topk = max_cluster - 1), ranked
+    by the same total order as its heap: score inter/union descending, then
+    smaller i, then smaller j.  Each round, every edge whose endpoints lie in
+    two different clusters with sizes summing to at most max_cluster is a
+    proposal for both clusters; each cluster keeps its highest-ranked proposal,
+    and every edge that is the kept proposal of both its clusters merges them
+    (the smaller root row becomes the root).  Rounds repeat until one merges
+    nothing.  Scores stay those of the original row pairs (no re-scoring).
+    Output as hierarchical(): clusters by smallest row, rows ascending."""
+    n = A.nrows
+    cand = candidate_pairs(A, th, max_cluster - 1)
+    edges = sorted(cand.items(), key=lambda kv: (-Fraction(kv[1][0], kv[1][1]), kv[0][0], kv[0][1]))
+    parent = list(range(n))
+    size = [1] * n
+
+    def find(x):
+        while parent[x] != x:
+            x = parent[x]
+        return x
+
+    while True:
+        best = {}
+        for rank, ((i, j), _) in enumerate(edges):
+            ri, rj = find(i), find(j)
+            if ri == rj or size[ri] + size[rj] > max_cluster:
+                continue
+            for r in (ri, rj):
+                if r not in best:           # edges are in rank order: the first is the best
+                    best[r] = rank
+        merges = []
+        for rank, ((i, j), _) in enumerate(edges):
+            ri, rj = find(i), find(j)
+            if ri != rj and best.get(ri) == rank and best.get(rj) == rank:
+                merges.append((min(ri, rj), max(ri, rj)))
+        if not merges:
+            break
+        for lo, hi in merges:
+            parent[hi] = lo
+            size[lo] += size[hi]
+    groups: dict = {}
+    for r in range(n):
+        groups.setdefault(find(r), []).append(r)
+    perm, cluster_ptr = [], [0]
+    for root in sorted(groups):
+        perm.extend(sorted(groups[root]))
+        cluster_ptr.append(len(perm))
+    return np.array(perm, dtype=np.int32), np.array(cluster_ptr, dtype=np.int64)
+
+
+def greedy_matching(A, th: float):
+    """Pairs by the global greedy rule (edges in rank order, taken when both rows
+    are still unmatched); the clusters of handshake(A, th, 2) must equal these."""
+    cand = candidate_pairs(A, th, 1)
+    edges = sorted(cand.items(), key=lambda kv: (-Fraction(kv[1][0], kv[1][1]), kv[0][0], kv[0][1]))
+    mate = {}
+    for (i, j), _ in edges:
+        if i not in mate and j not in mate:
+            mate[i], mate[j] = j, i
+    return mate
+
+
 def variable_length(A, th: float, max_cluster: int):
     """Algorithm 2 (variable-length clusters over the given row order)."""
     rows = _rows(A)

@@ -147,3 +147,66 @@ def test_exact_score_order():
     assert not oh.jaccard_gt(2, 7, TH)
     assert oh.jaccard_gt(1, 3, TH)
     assert Fraction(1, 3) == Fraction(2, 6)
+
+
+# ---- round-parallel merge (handshake) ----------------------------------------
+def handshake_example():
+    """Rows 0..5: J(0,1) = 3/5, J(0,2) = J(1,2) = 2/6, J(3,4) = 2/3, row 5 alone."""
+    rows = {0: [0, 1, 2, 3], 1: [0, 1, 2, 4], 2: [0, 1, 5, 6], 3: [7, 8], 4: [7, 8, 9], 5: [20]}
+    rr = np.concatenate([[r] * len(rows[r]) for r in range(6)])
+    cc = np.concatenate([rows[r] for r in range(6)])
+    return synth.csr_from_pattern(6, 21, rr, cc).with_values(np.ones(len(cc)))
+
+
+def test_handshake_hand_traced():
+    A = handshake_example()
+    # max 2: round 1 merges (3,4) (rank 0) and (0,1) (rank 1); (0,2) would make 3 rows
+    perm, cptr = oh.handshake(A, TH, 2)
+    assert list(perm) == [0, 1, 2, 3, 4, 5] and list(cptr) == [0, 2, 3, 5, 6]
+    # max 3: round 2 merges (0,2) into {0,1}: its best proposal is (0,2), rank 2 < (1,2)
+    perm, cptr = oh.handshake(A, TH, 3)
+    assert list(perm) == [0, 1, 2, 3, 4, 5] and list(cptr) == [0, 3, 5, 6]
+
+
+def clusters_of(perm, cptr):
+    return [frozenset(int(x) for x in perm[cptr[c]:cptr[c + 1]]) for c in range(len(cptr) - 1)]
+
+
+def test_handshake_max2_is_greedy_matching():
+    """With clusters of at most 2 rows the rounds pick locally dominant edges, which
+    give exactly the global greedy matching (edges in rank order)."""
+    for seed in range(6):
+        A = random_sparse(120, 40, 0.12, 100 + seed, "f64")
+        perm, cptr = oh.handshake(A, TH, 2)
+        mate = oh.greedy_matching(A, TH)
+        want = {frozenset((i, mate[i])) if i in mate else frozenset((i,)) for i in range(A.nrows)}
+        assert set(clusters_of(perm, cptr)) == want
+
+
+def test_handshake_invariants():
+    """Clusters within the size cap, every cluster joined by candidate edges, and no
+    candidate edge left between two clusters that could still merge (maximality)."""
+    for seed, mc in ((1, 3), (2, 8), (3, 8), (4, 32)):
+        A = random_sparse(150, 50, 0.1, 200 + seed, "f64")
+        perm, cptr = oh.handshake(A, TH, mc)
+        assert sorted(perm.tolist()) == list(range(A.nrows))
+        cl = clusters_of(perm, cptr)
+        where = {r: k for k, c in enumerate(cl) for r in c}
+        assert all(len(c) <= mc for c in cl)
+        cand = oh.candidate_pairs(A, TH, mc - 1)
+        for (i, j) in cand:
+            if where[i] != where[j]:
+                assert len(cl[where[i]]) + len(cl[where[j]]) > mc
+        for c in cl:                      # connected through candidate edges
+            c = sorted(c)
+            seen, todo = {c[0]}, [c[0]]
+            while todo:
+                x = todo.pop()
+                for (i, j) in cand:
+                    for a, b in ((i, j), (j, i)):
+                        if a == x and b in c and b not in seen:
+                            seen.add(b)
+                            todo.append(b)
+            assert seen == set(c)
+        roots = [min(c) for c in cl]
+        assert roots == sorted(roots)     # clusters ordered by their smallest row
