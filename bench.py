@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-parallel-hc", action="store_true", help="skip the round-parallel clustering line")
     ap.add_argument("--fused-fma", type=int, default=0, help="FP64: accumulate with fused multiply-add")
     ap.add_argument("--cluster-load", type=int, default=0, help="numeric cluster-table fill limit, percent (0: default)")
     ap.add_argument("--cluster-kernel", type=int, default=0,
@@ -213,12 +214,12 @@ def measured_peaks():
 
 
 NUMERIC_KERNEL_SOURCES = ("k_cluster.cuh", "k_lean.cuh", "k_rows.cuh", "k_bins.cuh", "k_launch.cuh",
-                          "sgc_device.cuh", "sgc_kernels.h", "sgc_internal.h", "k_phase_f32.cu", "k_phase_f64.cu",
-                          "k_phase_i64.cu", "k_phase_sym.cu", "capi.cu")
+                          "sgc_device.cuh", "sgc_internal.h", "k_phase_f32.cu", "k_phase_f64.cu", "k_phase_i64.cu",
+                          "k_phase_sym.cu")
 
 
 def numeric_sources_digest() -> str:
-    """sha256 over the sources that define the numeric phase's kernels and launches."""
+    """sha256 over the device sources of the numeric phase's kernels and their launches."""
     import hashlib
     h = hashlib.sha256()
     for f in NUMERIC_KERNEL_SOURCES:
@@ -425,6 +426,30 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         del Cl, Lrn
         torch.cuda.empty_cache()
 
+    # ---- round-parallel hierarchical merge: preprocessing time and the exact step on its clusters
+    par = None
+    if not args.no_parallel_hc:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        perm_p, cptr_p = sgc.hcluster_reorder_parallel(Ad, sgc.JACC_TH, sgc.MAX_CLUSTER)
+        torch.cuda.synchronize()
+        t_hcp = time.perf_counter() - t0
+        Acl_p = sgc.csr_cluster_build(Ad, perm_p, cptr_p, sgc.LAYOUT_MASKED)
+        ws_p = sgc.Workspace(sgc.spgemm_workspace_size(Acl_p, Bd, opt), dev)
+        rp_p, nnz_p = sgc.spgemm_symbolic(Acl_p, Bd, ws_p, opt)
+        C_p = sgc.spgemm_numeric(Acl_p, Bd, rp_p, nnz_p, ws_p, opt)
+        sym_p = lambda: sgc.spgemm_symbolic(Acl_p, Bd, ws_p, opt, c_row_ptr=rp_p, sync=False)  # noqa: E731
+        num_p = lambda: sgc.spgemm_numeric(Acl_p, Bd, rp_p, nnz_p, ws_p, opt, C=C_p)  # noqa: E731
+        timed_loop(sym_p, num_p, args.warmup)
+        psym, pnum = timed_loop(sym_p, num_p, args.steps)
+        sgc.workspace_status(ws_p)
+        p_ms = max_over_ranks(float(np.mean([a + b for a, b in zip(psym, pnum)])), world, dev)
+        par = {"hcluster_s": round(t_hcp, 3), "nclusters": int(Acl_p.nclusters),
+               "in_spgemm_units": round(t_hcp / (p_ms * 1e-3), 1),
+               "clustered_exact": {"value": round(job_gflops(flops, world, p_ms), 3), "ms_per_step": round(p_ms, 4)}}
+        del C_p, Acl_p, ws_p
+        torch.cuda.empty_cache()
+
     # ---- algorithmic bytes ----------------------------------------------------
     ucol = Acl.ucol.cpu().numpy()
     staged = int(np.sum(np.diff(B.row_ptr)[ucol]))      # sum over clusters of the B elements staged
@@ -521,6 +546,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                          "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": num_bytes},
+            "preprocess_parallel_merge": par,
             "preprocess": {"hcluster_s": round(t_hc, 3), "csr_cluster_build_s": round(t_build, 4),
                            "in_spgemm_units": round((t_hc + t_build) / (step_ms * 1e-3), 1)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,

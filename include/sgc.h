@@ -272,6 +272,19 @@ int spgemm_rowwise_numeric(const sgc_csr* A, const sgc_csr* B, sgc_csr* C, void*
  * ------------------------------------------------------------------------- */
 int hcluster_workspace_size(const sgc_csr* A, int32_t max_cluster, size_t* bytes);
 
+/* hcluster_reorder_parallel: a round-parallel variant of Algorithm 3's merge
+ * (not in the paper), same candidate edges, same priority order, same
+ * workspace and output conventions as hcluster_reorder.  Each round, every
+ * candidate edge joining two clusters whose sizes sum to at most max_cluster
+ * proposes to both; a cluster keeps its highest-priority proposal; edges kept
+ * by both of their clusters merge them (the smaller root survives).  Rounds
+ * run on the device until one merges nothing.  Scores are those of the
+ * original row pairs (no re-scoring of root rows), so the clusters can differ
+ * from hcluster_reorder's; C does not depend on the clustering.  Synchronises. */
+int hcluster_reorder_parallel(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm,
+                              int64_t* cluster_ptr, int64_t* nclusters_host, void* ws, size_t ws_bytes,
+                              void* stream);
+
 /* Cluster sources over A's own row order (Sec. 3.2), for comparison with
  * hierarchical clustering.  Both give perm = identity (position -> row),
  * cluster_ptr (device, int64, nclusters + 1 entries; at most nrows + 1) and

@@ -516,6 +516,60 @@ int cluster_variable_length(const sgc_csr* A, float jacc_th, int32_t max_cluster
   return SGC_OK;
 }
 
+int hcluster_reorder_parallel(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm,
+                              int64_t* cluster_ptr, int64_t* nclusters_host, void* ws, size_t ws_bytes,
+                              void* stream) {
+  int rc = check_csr(A, "A", false);
+  if (rc) return rc;
+  if (max_cluster < 1 || max_cluster > 32) SGC_FAIL(SGC_INVALID_ARG, "max_cluster must be in 1..32");
+  if (!nclusters_host || (A->nrows > 0 && (!perm || !cluster_ptr))) SGC_FAIL(SGC_INVALID_ARG, "NULL output");
+  HcWs w = carve_hc(ws, ws_bytes, A, 31);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->nrows;
+  const int topk = max_cluster - 1;
+  SGC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+  std::vector<int32_t> hroot((size_t)(n > 0 ? n : 1));
+  for (int64_t r = 0; r < n; ++r) hroot[(size_t)r] = (int32_t)r;
+  if (topk > 0 && n > 0) {
+    SGC_CUDA(hc_candidates_run(A->row_ptr, A->col, n, A->ncols, A->nnz, (double)jacc_th, topk, w.trp, w.tcol,
+                               w.cursor, w.dummy_rp, w.bins, w.scan_tmp, w.cj, w.cc, w.cu, w.status, num_sms(), s));
+    std::vector<int32_t> cj((size_t)(n * topk)), cc(cj.size()), cu(cj.size());
+    SGC_CUDA(cudaMemcpyAsync(cj.data(), w.cj, sizeof(int32_t) * cj.size(), cudaMemcpyDeviceToHost, s));
+    SGC_CUDA(cudaMemcpyAsync(cc.data(), w.cc, sizeof(int32_t) * cj.size(), cudaMemcpyDeviceToHost, s));
+    SGC_CUDA(cudaMemcpyAsync(cu.data(), w.cu, sizeof(int32_t) * cj.size(), cudaMemcpyDeviceToHost, s));
+    rc = sync_status(w.status, s);
+    if (rc) return rc;
+    // edges in rank order on the host; rounds on the device (candidate arrays reused as scratch)
+    std::vector<int32_t> eu(cj.size()), ev(cj.size());
+    const int64_t E = hc_rank_edges(n, cj.data(), cc.data(), cu.data(), topk, eu.data(), ev.data());
+    int32_t *du = w.cj, *dv = w.cc, *root = w.cu, *size = w.cu + n, *best = w.cu + 2 * n, *link = w.cu + 3 * n;
+    if (E > 0) {
+      SGC_CUDA(cudaMemcpyAsync(du, eu.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice, s));
+      SGC_CUDA(cudaMemcpyAsync(dv, ev.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice, s));
+    }
+    cudaError_t err;
+    if (hc_merge_parallel_run(n, E, du, dv, max_cluster, root, size, best, link, w.cursor, num_sms(), s, &err) < 0 ||
+        err != cudaSuccess)
+      SGC_FAIL(SGC_CUDA_ERROR, cudaGetErrorString(err));
+    SGC_CUDA(cudaMemcpyAsync(hroot.data(), root, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    SGC_CUDA(cudaStreamSynchronize(s));
+  }
+  std::vector<int32_t> hperm((size_t)(n > 0 ? n : 1));
+  std::vector<int64_t> hcp((size_t)n + 1);
+  const int64_t ncl = hc_order_by_root(n, hroot.data(), hperm.data(), hcp.data());
+  if (n > 0) {
+    SGC_CUDA(cudaMemcpyAsync(perm, hperm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    SGC_CUDA(cudaMemcpyAsync(cluster_ptr, hcp.data(), sizeof(int64_t) * (ncl + 1), cudaMemcpyHostToDevice, s));
+    SGC_CUDA(cudaStreamSynchronize(s));
+  } else {
+    SGC_CUDA(cudaMemcpyAsync(cluster_ptr, hcp.data(), sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    SGC_CUDA(cudaStreamSynchronize(s));
+  }
+  *nclusters_host = ncl;
+  return SGC_OK;
+}
+
 int hcluster_reorder(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm, int64_t* cluster_ptr,
                      int64_t* nclusters_host, void* ws, size_t ws_bytes, void* stream) {
   int rc = check_csr(A, "A", false);

@@ -63,6 +63,65 @@ inline uint64_t pkey(int32_t i, int32_t j) { return ((uint64_t)(uint32_t)i << 32
 
 }  // namespace
 
+// Unique candidate pairs (i < j) of the per-row lists, in the heap's priority
+// order (score descending, then i, then j): u[e], v[e] for rank e; returns the count.
+int64_t hc_rank_edges(int64_t n, const int32_t* cj, const int32_t* cc, const int32_t* cu, int topk, int32_t* u,
+                      int32_t* v) {
+  auto in_list = [&](int64_t row, int32_t x) {
+    const int32_t* L = cj + row * topk;
+    for (int s = 0; s < topk && L[s] >= 0; ++s)
+      if (L[s] == x) return true;
+    return false;
+  };
+  std::vector<int64_t> start((size_t)n + 1, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t c = 0;
+    for (int s = 0; s < topk; ++s) {
+      const int32_t j = cj[i * topk + s];
+      if (j < 0) break;
+      c += (i < j || !in_list(j, (int32_t)i)) ? 1 : 0;
+    }
+    start[(size_t)i + 1] = c;
+  }
+  for (int64_t i = 0; i < n; ++i) start[(size_t)i + 1] += start[(size_t)i];
+  std::vector<HPair> pairs((size_t)start[(size_t)n]);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t o = start[(size_t)i];
+    for (int s = 0; s < topk; ++s) {
+      const int32_t j = cj[i * topk + s];
+      if (j < 0) break;
+      if (i < j || !in_list(j, (int32_t)i))
+        pairs[(size_t)o++] = HPair{cc[i * topk + s], cu[i * topk + s], (int32_t)std::min<int64_t>(i, j),
+                                   (int32_t)std::max<int64_t>(i, j)};
+    }
+  }
+  const Lower lower;
+  __gnu_parallel::sort(pairs.begin(), pairs.end(), [&](const HPair& x, const HPair& y) { return lower(y, x); });
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < (int64_t)pairs.size(); ++e) {
+    u[e] = pairs[(size_t)e].i;
+    v[e] = pairs[(size_t)e].j;
+  }
+  return (int64_t)pairs.size();
+}
+
+// Clusters from a root per row (root = smallest row of its cluster): ordered by
+// root, rows ascending.  Returns ncl.
+int64_t hc_order_by_root(int64_t n, const int32_t* root, int32_t* perm, int64_t* cluster_ptr) {
+  std::vector<int64_t> cnt((size_t)n + 1, 0);
+  for (int64_t r = 0; r < n; ++r) ++cnt[(size_t)root[r] + 1];
+  for (int64_t r = 0; r < n; ++r) cnt[(size_t)r + 1] += cnt[(size_t)r];
+  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+  for (int64_t r = 0; r < n; ++r) perm[fill[(size_t)root[r]]++] = (int32_t)r;
+  int64_t ncl = 0;
+  cluster_ptr[0] = 0;
+  for (int64_t r = 0; r < n; ++r)
+    if (root[r] == r) cluster_ptr[++ncl] = cnt[(size_t)r + 1];
+  return ncl;
+}
+
 // n rows; rp/col: host copy of A's pattern; cand arrays: n*topk (j = -1: none).
 // Writes perm[n] and cluster_ptr[ncl+1]; returns ncl.
 //

@@ -141,6 +141,12 @@ cudaError_t hc_candidates_run(const int64_t* arp, const int32_t* acol, int64_t n
                               double th, int topk, int64_t* trp, int32_t* tcol, int32_t* cursor, int64_t* dummy_rp,
                               const BinOut& bins, int64_t* scan_tmp, int32_t* cj, int32_t* cc, int32_t* cu,
                               void* status, int sms, cudaStream_t s);
+int64_t hc_rank_edges(int64_t n, const int32_t* cj, const int32_t* cc, const int32_t* cu, int topk, int32_t* u,
+                      int32_t* v);
+int64_t hc_order_by_root(int64_t n, const int32_t* root, int32_t* perm, int64_t* cluster_ptr);
+int hc_merge_parallel_run(int64_t n, int64_t E, const int32_t* u, const int32_t* v, int max_cluster, int32_t* root,
+                          int32_t* size, int32_t* best, int32_t* link, int32_t* merged, int sms, cudaStream_t s,
+                          cudaError_t* err);
 int64_t hc_merge_host(int64_t n, const int64_t* rp, const int32_t* col, const int32_t* cj, const int32_t* cc,
                       const int32_t* cu, int topk, double th, int max_cluster, int32_t* perm, int64_t* cluster_ptr);
 

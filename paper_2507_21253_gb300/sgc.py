@@ -97,6 +97,8 @@ _c = {
                                 ctypes.c_size_t, vp),
     "hcluster_reorder": _sig("hcluster_reorder", P(CsrStruct), ctypes.c_float, i32, vp, vp, P(i64), vp,
                              ctypes.c_size_t, vp),
+    "hcluster_reorder_parallel": _sig("hcluster_reorder_parallel", P(CsrStruct), ctypes.c_float, i32, vp, vp,
+                                      P(i64), vp, ctypes.c_size_t, vp),
     "cluster_fixed_length": _sig("cluster_fixed_length", i64, i32, vp, vp, P(i64), vp),
     "cluster_variable_length": _sig("cluster_variable_length", P(CsrStruct), ctypes.c_float, i32, vp, vp, P(i64),
                                     vp),
@@ -382,6 +384,19 @@ def hcluster_reorder(A: DeviceCsr, jacc_th: float = JACC_TH, max_cluster: int = 
     ncl = i64()
     a = A.struct()
     _call("hcluster_reorder", ctypes.byref(a), float(jacc_th), max_cluster, _ptr(perm), _ptr(cptr),
+          ctypes.byref(ncl), ws.ptr, ws.nbytes, _stream())
+    return perm[:A.nrows], cptr[:ncl.value + 1]
+
+
+def hcluster_reorder_parallel(A: DeviceCsr, jacc_th: float = JACC_TH, max_cluster: int = MAX_CLUSTER):
+    """Round-parallel variant of Algorithm 3's merge: (perm, cluster_ptr) on the device."""
+    dev = A.row_ptr.device
+    ws = _hc_ws(A, max_cluster)
+    perm = torch.empty(max(A.nrows, 1), dtype=torch.int32, device=dev)
+    cptr = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
+    ncl = i64()
+    a = A.struct()
+    _call("hcluster_reorder_parallel", ctypes.byref(a), float(jacc_th), max_cluster, _ptr(perm), _ptr(cptr),
           ctypes.byref(ncl), ws.ptr, ws.nbytes, _stream())
     return perm[:A.nrows], cptr[:ncl.value + 1]
 

@@ -142,3 +142,23 @@ def test_variable_length_product_exact(sgc):
     perm, cptr = sgc.cluster_variable_length(Ad, TH, 8)
     C = sgc.spgemm(sgc.csr_cluster_build(Ad, perm, cptr), Ad)
     compare(C, A, A, exact_f64=True)
+
+
+@pytest.mark.parametrize("max_cluster", [2, 3, 8, 32])
+@pytest.mark.parametrize("name,A", CASES, ids=[c[0] for c in CASES])
+def test_parallel_merge_matches_oracle(sgc, name, A, max_cluster):
+    """Round-parallel merge on the GPU equals the oracle's handshake() exactly."""
+    if A.nrows > 4096 and max_cluster == 32:
+        pytest.skip("oracle time")
+    perm, cptr = sgc.hcluster_reorder_parallel(sgc.DeviceCsr.from_host(A), TH, max_cluster)
+    rperm, rcptr = oh.handshake(A, TH, max_cluster)
+    assert np.array_equal(perm.cpu().numpy(), rperm)
+    assert np.array_equal(cptr.cpu().numpy(), rcptr)
+
+
+def test_parallel_merge_product_exact(sgc):
+    A = synth.stencil27_3d(14, 13, 12, seed=5)
+    Ad = sgc.DeviceCsr.from_host(A)
+    perm, cptr = sgc.hcluster_reorder_parallel(Ad, TH, 8)
+    C = sgc.spgemm(sgc.csr_cluster_build(Ad, perm, cptr), Ad)
+    compare(C, A, A, exact_f64=True)
