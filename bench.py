@@ -44,7 +44,7 @@ TRAINING = {"stencil27_160": ("stencil_instance", 24), "stencil27_80": ("stencil
 WORKLOADS = {
     "stencil27_160": ("C = A*A, A = 27-point stencil on a 160^3 grid (n = 4,096,000, nnz = 109,215,352), "
                       "FP64 N(0,1) values, seeded random symmetric permutation; hierarchical clustering "
-                      "(jacc_th 0.3, max 8) + CSR_Cluster (masked layout)",
+                      "(jacc_th 0.3, max 8; merge as in 'clustering') + CSR_Cluster (masked layout)",
                       lambda: synth.workload_stencil(5, nx=160)),
     "stencil27_80": ("C = A*A, A = 27-point stencil on an 80^3 grid, FP64 N(0,1), seeded symmetric permutation; "
                      "hierarchical clustering + CSR_Cluster",
@@ -78,7 +78,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--no-parallel-hc", action="store_true", help="skip the round-parallel clustering line")
+    ap.add_argument("--clustering", default="parallel", choices=["parallel", "serial"],
+                    help="merge of the hierarchical clustering: round-parallel on the GPU (default) or the serial heap")
+    ap.add_argument("--no-alt-clustering", action="store_true", help="skip timing the other merge")
     ap.add_argument("--fused-fma", type=int, default=0, help="FP64: accumulate with fused multiply-add")
     ap.add_argument("--cluster-load", type=int, default=0, help="numeric cluster-table fill limit, percent (0: default)")
     ap.add_argument("--cluster-kernel", type=int, default=0,
@@ -304,8 +306,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             dist.barrier()
 
     # ---- preprocessing: hierarchical clustering + CSR_Cluster build ----------
+    parallel = args.clustering == "parallel"
+    hc_main = sgc.hcluster_reorder_parallel if parallel else sgc.hcluster_reorder
+    hc_alt = sgc.hcluster_reorder if parallel else sgc.hcluster_reorder_parallel
     t0 = time.perf_counter()
-    perm, cptr = sgc.hcluster_reorder(Ad, sgc.JACC_TH, sgc.MAX_CLUSTER)
+    perm, cptr = hc_main(Ad, sgc.JACC_TH, sgc.MAX_CLUSTER)
     torch.cuda.synchronize()
     t_hc = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -386,7 +391,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         from paper_2507_21253_gb300 import learned as lrn
         gen_name, ntrain = TRAINING[args.workload]
         t0 = time.perf_counter()
-        params, tloss = lrn.train(getattr(lrn, gen_name), range(1000, 1000 + ntrain), epochs=4, device=dev)
+        params, tloss = lrn.train(getattr(lrn, gen_name), range(1000, 1000 + ntrain), epochs=4, device=dev,
+                                  parallel=parallel)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         Lrn = sgc.LearnedSpgemm(Acl, Bd, params=params, margin=1.25, opt=opt)
@@ -426,12 +432,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         del Cl, Lrn
         torch.cuda.empty_cache()
 
-    # ---- round-parallel hierarchical merge: preprocessing time and the exact step on its clusters
+    # ---- the other merge of the hierarchical clustering: its preprocessing time and exact step
     par = None
-    if not args.no_parallel_hc:
+    if not args.no_alt_clustering:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        perm_p, cptr_p = sgc.hcluster_reorder_parallel(Ad, sgc.JACC_TH, sgc.MAX_CLUSTER)
+        perm_p, cptr_p = hc_alt(Ad, sgc.JACC_TH, sgc.MAX_CLUSTER)
         torch.cuda.synchronize()
         t_hcp = time.perf_counter() - t0
         Acl_p = sgc.csr_cluster_build(Ad, perm_p, cptr_p, sgc.LAYOUT_MASKED)
@@ -444,7 +450,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         psym, pnum = timed_loop(sym_p, num_p, args.steps)
         sgc.workspace_status(ws_p)
         p_ms = max_over_ranks(float(np.mean([a + b for a, b in zip(psym, pnum)])), world, dev)
-        par = {"hcluster_s": round(t_hcp, 3), "nclusters": int(Acl_p.nclusters),
+        par = {"clustering": ("serial heap merge (Algorithm 3)" if parallel else "round-parallel merge"),
+               "hcluster_s": round(t_hcp, 3), "nclusters": int(Acl_p.nclusters),
                "in_spgemm_units": round(t_hcp / (p_ms * 1e-3), 1),
                "clustered_exact": {"value": round(job_gflops(flops, world, p_ms), 3), "ms_per_step": round(p_ms, 4)}}
         del C_p, Acl_p, ws_p
@@ -546,7 +553,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                          "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": num_bytes},
-            "preprocess_parallel_merge": par,
+            "clustering": ("hierarchical, round-parallel merge on the GPU (jacc_th 0.3, max 8)" if parallel else
+                           "hierarchical, serial heap merge (Algorithm 3; jacc_th 0.3, max 8)"),
+            "alternative_clustering": par,
             "preprocess": {"hcluster_s": round(t_hc, 3), "csr_cluster_build_s": round(t_build, 4),
                            "in_spgemm_units": round((t_hc + t_build) / (step_ms * 1e-3), 1)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,

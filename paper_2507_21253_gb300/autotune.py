@@ -4,8 +4,9 @@ A batch A_i * B_i runs as one product of block-diagonal matrices (see
 ``csr_batch_pack`` in include/sgc.h), captured in one CUDA graph.  The tuner
 times each candidate configuration on the batch itself and keeps the fastest:
 
-* clustering: hierarchical (Algorithm 3, max cluster 8 or 4) or fixed-length
-  clusters of width K in {1, 4, 8} (Sec. 3.2) -- the "cluster width";
+* clustering: hierarchical (Algorithm 3's serial merge, max cluster 8 or 4, or
+  the round-parallel merge, max 8) or fixed-length clusters of width K in
+  {1, 4, 8} (Sec. 3.2) -- the "cluster width";
 * staging of B rows: 1D bulk async copies or cooperative loads;
 * row-hash table fill limit (the size threshold that bins rows into table
   classes) 50% or 75%.
@@ -26,7 +27,7 @@ import torch
 
 from . import sgc, synth
 
-CLUSTERINGS = ("hc8", "hc4", "fixed1", "fixed4", "fixed8")
+CLUSTERINGS = ("phc8", "hc8", "hc4", "fixed1", "fixed4", "fixed8")
 STAGINGS = (sgc.STAGING_BULK, sgc.STAGING_LDG)
 LOADS = (50, 75)
 
@@ -42,6 +43,8 @@ def device_key() -> str:
 
 
 def cluster(packed: sgc.DeviceCsr, how: str):
+    if how.startswith("phc"):
+        return sgc.hcluster_reorder_parallel(packed, sgc.JACC_TH, int(how[3:]))
     if how.startswith("hc"):
         return sgc.hcluster_reorder(packed, sgc.JACC_TH, int(how[2:]))
     perm, cptr = synth.fixed_clusters(packed.nrows, int(how[5:]))

@@ -19,10 +19,13 @@ from . import sgc, synth
 MAGIC = b"SGCNNZP1"
 
 
-def instance_data(A, jacc_th: float = sgc.JACC_TH, max_cluster: int = sgc.MAX_CLUSTER, device="cuda"):
-    """(features [ncl, 8], targets [ncl]) of one instance, clustered hierarchically."""
+def instance_data(A, jacc_th: float = sgc.JACC_TH, max_cluster: int = sgc.MAX_CLUSTER, device="cuda",
+                  parallel: bool = False):
+    """(features [ncl, 8], targets [ncl]) of one instance, clustered hierarchically
+    (the serial merge, or the round-parallel one if `parallel`)."""
     Ad = sgc.DeviceCsr.from_host(A, device)
-    perm, cptr = sgc.hcluster_reorder(Ad, jacc_th, max_cluster)
+    hc = sgc.hcluster_reorder_parallel if parallel else sgc.hcluster_reorder
+    perm, cptr = hc(Ad, jacc_th, max_cluster)
     Acl = sgc.csr_cluster_build(Ad, perm, cptr, sgc.LAYOUT_MASKED)
     ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad), device)
     sgc.spgemm_symbolic(Acl, Ad, ws)
@@ -32,11 +35,11 @@ def instance_data(A, jacc_th: float = sgc.JACC_TH, max_cluster: int = sgc.MAX_CL
 
 
 def train(make_instance, seeds, epochs: int = 4, batch: int = 256, lr: float = 2e-3, init_seed: int = 1,
-          device="cuda"):
+          device="cuda", parallel: bool = False):
     """Trains on instances make_instance(seed) for seed in seeds; returns (params, per-step loss)."""
     feats, ys = [], []
     for s in seeds:
-        X, y = instance_data(make_instance(s), device=device)
+        X, y = instance_data(make_instance(s), device=device, parallel=parallel)
         feats.append(X)
         ys.append(y)
     X = torch.cat(feats)
