@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--clustering", default="parallel", choices=["parallel", "serial"],
                     help="merge of the hierarchical clustering: round-parallel on the GPU (default) or the serial heap")
     ap.add_argument("--no-alt-clustering", action="store_true", help="skip timing the other merge")
+    ap.add_argument("--epochs", type=int, default=20, help="predictor training epochs")
+    ap.add_argument("--margin", type=float, default=1.1, help="capacity margin over the predicted output columns")
     ap.add_argument("--fused-fma", type=int, default=0, help="FP64: accumulate with fused multiply-add")
     ap.add_argument("--cluster-load", type=int, default=0, help="numeric cluster-table fill limit, percent (0: default)")
     ap.add_argument("--cluster-kernel", type=int, default=0,
@@ -230,9 +232,10 @@ def numeric_sources_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profiles(workload: str):
+def traffic_from_profiles(workload: str, clustering: str):
     """Per-launch DRAM bytes of the numeric phase from the ncu summary under profiles/,
-    or None when the summary has no figure for the workload or the kernels changed since."""
+    or None when the summary has no figure for the workload and clustering or the
+    kernels changed since."""
     p = os.path.join(ROOT, "profiles", "traffic_cluster_numeric_stencil27.md")
     if not os.path.exists(p):
         return None
@@ -242,7 +245,8 @@ def traffic_from_profiles(workload: str):
             m = re.match(r"\s*sources digest:\s*(\w+)", line)
             if m:
                 digest = m.group(1)
-            m = re.match(r"\s*traffic per launch, %s:\s*([0-9]+)" % re.escape(workload), line)
+            m = re.match(r"\s*traffic per launch, %s, %s merge:\s*([0-9]+)" % (re.escape(workload), clustering),
+                         line)
             if m:
                 value = int(m.group(1))
     if value is None or digest != numeric_sources_digest():
@@ -391,11 +395,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         from paper_2507_21253_gb300 import learned as lrn
         gen_name, ntrain = TRAINING[args.workload]
         t0 = time.perf_counter()
-        params, tloss = lrn.train(getattr(lrn, gen_name), range(1000, 1000 + ntrain), epochs=4, device=dev,
-                                  parallel=parallel)
+        params, tloss = lrn.train(getattr(lrn, gen_name), range(1000, 1000 + ntrain), epochs=args.epochs,
+                                  device=dev, parallel=parallel)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
-        Lrn = sgc.LearnedSpgemm(Acl, Bd, params=params, margin=1.25, opt=opt)
+        Lrn = sgc.LearnedSpgemm(Acl, Bd, params=params, margin=args.margin, opt=opt)
         Lrn.phase1()
         Cl = Lrn.phase2()
         sgc.workspace_status(Lrn.ws)
@@ -426,7 +430,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         learned_out = {"value": round(job_gflops(flops, world, l_ms), 3), "unit": "GFLOP/s",
                        "ms_per_step": round(l_ms, 4), "overflow_clusters": int(Lrn.n_overflow),
                        "slab_over_nnzC": round(Lrn.slab_elems / max(nnz, 1), 4),
-                       "train": {"instances": ntrain, "generator": gen_name, "seconds": round(t_train, 2),
+                       "margin": args.margin,
+                       "train": {"instances": ntrain, "generator": gen_name, "epochs": args.epochs,
+                                 "seconds": round(t_train, 2),
                                  "final_loss": round(float(tloss[-50:].mean().item()), 5)},
                        "step": "plan (features, MLP, capacities) + slab pass + exact fallback + compaction"}
         del Cl, Lrn
@@ -468,7 +474,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     num_avg = float(np.mean(num_ms))
     peak, peak_kind = measured_peaks()
     achieved = num_bytes / (num_avg * 1e-3) / 1e9
-    traffic = traffic_from_profiles(args.workload)
+    traffic = traffic_from_profiles(args.workload, args.clustering)
     compulsory = csr_bytes(A) + csr_bytes(B) + c_bytes
 
     # ---- end to end through the public API, host buffers -----------------------

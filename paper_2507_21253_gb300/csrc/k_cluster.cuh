@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
   const int ngroups = (blockDim.x >> 5) / gw;
   unsigned char* my = sm + (size_t)gid * region_bytes;
   uint64_t* bar = (uint64_t*)my;
-  // group header: [0,8) mbarrier; [8,72) ints: [0] distinct count, [1..8] copy flags;
+  // group header: [0,8) mbarrier; [8,72) ints: [0] distinct count, [1..8] per-warp flags, [9] cursor;
   // [72,104) / [104,136) per-warp key min / max; [136,200) per-warp 64-bit scan partials
   int* hdr = (int*)(my + 8);
   int* wmin = (int*)(my + 72);
@@ -236,7 +236,6 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
 
     // ---- 1. descriptors and staging ---------------------------------------
     int64_t run_c = 0, run_v = 0, run_a = 0;
-    bool issued = false;
     if (bulk) fence_proxy_async_smem();  // earlier generic accesses to the region precede async writes
     for (int64_t tb = 0; tb < T; tb += GT) {
       const int64_t i = tb + gt;
@@ -282,7 +281,6 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
           mbar_expect_tx(bar, (uint32_t)wc * 4u + (uint32_t)wv * (uint32_t)sizeof(In));
           bulk_g2s(stage_c + run_c + oc, B.col + (s - shc), (uint32_t)wc * 4u, bar);
           if (!SYM) bulk_g2s(stage_v + run_v + ov, (const In*)B.val + (s - shv), (uint32_t)wv * sizeof(In), bar);
-          issued = true;
         }
       }
       run_c += tc;
@@ -300,7 +298,6 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
         if (gt == 0) {
           mbar_expect_tx(bar, (uint32_t)((ae - as) * (int64_t)sizeof(In)));
           bulk_g2s(stage_a, (const In*)A.val + as, (uint32_t)((ae - as) * (int64_t)sizeof(In)), bar);
-          issued = true;
         }
       } else {
         for (int64_t q = gt; q < nva; q += GT) stage_a[q] = ((const In*)A.val)[v0 + q];
@@ -308,8 +305,13 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
     }
     // table init overlaps the copies in flight
     for (int x = gt; x < TH; x += GT) table[x] = EMPTY_KEY;
-    if (gt == 0) hdr[0] = 0;
-    group_sync(gw, gid);  // descriptors visible to the group
+    if (gt == 0) {
+      hdr[0] = 0;  // distinct output columns
+      hdr[9] = 0;  // compaction cursor (numeric)
+    }
+    group_sync(gw, gid);  // descriptors visible to the group; every expect_tx of the group is issued
+    // one arrival per phase (a cluster without copies completes its phase at once)
+    if (bulk && gt == 0) mbar_arrive(bar);
     // rows copied with loads: all of them in LDG mode, window-overflow rows in bulk mode
     for (int64_t i = wg; i < T; i += gw) {
       const int32_t oc = d.off_c[i];
@@ -325,20 +327,11 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       }
     }
     if (bulk) {
-      // one arrival per phase, after every expect_tx of the group
-      const int any = __any_sync(FULL, issued);
-      if (lane == 0) hdr[1 + wg] = any;
-      group_sync(gw, gid);
-      int grp_any = 0;
-      for (int q = 0; q < gw; ++q) grp_any |= hdr[1 + q];
-      if (grp_any) {
-        if (gt == 0) mbar_arrive(bar);
-        const bool ok = mbar_wait_bounded(bar, phase, WAIT_LIMIT);
-        phase ^= 1u;
-        if (!__all_sync(FULL, ok)) {
-          if (lane == 0) raise(st, DEV_TIMEOUT, 30, c);
-          return;  // timeouts are not expected; the group's other warps time out alike
-        }
+      const bool ok = mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+      phase ^= 1u;
+      if (!__all_sync(FULL, ok)) {
+        if (lane == 0) raise(st, DEV_TIMEOUT, 30, c);
+        return;  // timeouts are not expected; the group's other warps time out alike
       }
     }
     group_sync(gw, gid);
@@ -395,6 +388,7 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       // ---- 2. map staged column ids to slots ---------------------------------
       bool full = false;
       int newk = 0;
+      int32_t kmin = PAD_KEY, kmax = -1;  // range of the cluster's output columns
       for (int64_t i = wg; i < T; i += gw) {
         const int n = d.len[i];
         const int dc = d.off_c[i] & 0x7fffffff;
@@ -402,19 +396,29 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
           const int q = qb + lane;
           int slot = -1;
           bool nwk = false;
+          int32_t j = 0;
           if (q < n) {
-            slot = hash_find_or_insert(table, LH, stage_c[dc + q], &nwk);
+            j = stage_c[dc + q];
+            slot = hash_find_or_insert(table, LH, j, &nwk);
             if (slot < 0) full = true;
           }
           __syncwarp();
           if (slot >= 0) {
             newk += nwk;
+            kmin = min(kmin, j);
+            kmax = max(kmax, j);
             stage_c[dc + q] = slot;
           }
         }
       }
       newk = warp_sum(newk);
       if (lane == 0 && newk) atomicAdd(&hdr[0], newk);
+      kmin = warp_min(kmin);
+      kmax = warp_max(kmax);
+      if (lane == 0) {
+        wmin[wg] = kmin;
+        wmax[wg] = kmax;
+      }
       const bool anyfull = __any_sync(FULL, full);
       if (anyfull && lane == 0) {
         if (lo.active)
@@ -453,47 +457,26 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       int32_t* bkey = bcur + nb;
       int32_t* kslot = bkey + nb;
       {
-        // compaction: warp wg owns slots [s0, s1)
-        const int per = (TH + gw - 1) / gw;
-        const int s0 = min(wg * per, TH), s1 = min(s0 + per, TH);
-        int mine = 0;
-        for (int x0 = s0; x0 < s1; x0 += 32) {
+        // compaction of the occupied slots, in any order (the ranking sorts them):
+        // one cursor advance a warp step; the key range comes from the map phase
+        for (int x0 = wg * 32; x0 < TH; x0 += GT) {
           const int x = x0 + lane;
-          mine += __popc(__ballot_sync(FULL, x < s1 && table[x] != EMPTY_KEY));
-        }
-        int32_t kmin = PAD_KEY, kmax = -1;
-        for (int x = gt; x < TH; x += GT) {
           const int32_t key = table[x];
-          if (key != EMPTY_KEY) {
-            kmin = min(kmin, key);
-            kmax = max(kmax, key);
-          }
-        }
-        kmin = warp_min(kmin);
-        kmax = warp_max(kmax);
-        if (lane == 0) {
-          red64[wg] = (uint64_t)mine;
-          wmin[wg] = kmin;
-          wmax[wg] = kmax;
-        }
-        group_sync(gw, gid);
-        int base = 0;
-        for (int q = 0; q < gw; ++q) {
-          if (q < wg) base += (int)red64[q];
-          kmin = min(kmin, wmin[q]);
-          kmax = max(kmax, wmax[q]);
-        }
-        for (int x0 = s0; x0 < s1; x0 += 32) {
-          const int x = x0 + lane;
-          const int32_t key = x < s1 ? table[x] : EMPTY_KEY;
           const bool occ = key != EMPTY_KEY;
           const unsigned bal = __ballot_sync(FULL, occ);
+          int base = 0;
+          if (lane == 0 && bal) base = atomicAdd(&hdr[9], __popc(bal));
+          base = __shfl_sync(FULL, base, 0);
           if (occ) {
             const int pos = base + __popc(bal & lt);
             bkey[pos] = key;
             kslot[pos] = x;
           }
-          base += __popc(bal);
+        }
+        int32_t kmin = PAD_KEY, kmax = -1;
+        for (int q = 0; q < gw; ++q) {
+          kmin = min(kmin, wmin[q]);
+          kmax = max(kmax, wmax[q]);
         }
         for (int x = gt; x < n_out; x += GT) bst[x] = 0;
         group_sync(gw, gid);
