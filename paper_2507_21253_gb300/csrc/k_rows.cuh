@@ -354,6 +354,8 @@ inline size_t row_hash_smem(int warps, int log2T, bool sym, int acc_bytes) {
 constexpr int HEAVY_THREADS = 512;
 constexpr int HEAVY_SYM_WORDS = 16384;  // 64 KB bitmap: 524288 columns per pass
 constexpr int HEAVY_NUM_W = 16384;      // columns per numeric pass (128 KB of FP64)
+constexpr int HEAVY_CACHE = 2048;       // numeric: a row with at most this many entries keeps them in shared
+                                        // memory with a cursor per B row across the column windows
 
 template <int DT>
 __device__ __forceinline__ void gather_chunk(const ACsrView& Ac, const AClusterView& Acl, int src, int64_t item,
@@ -636,6 +638,10 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
   constexpr int WCOLS = SYM ? HEAVY_SYM_WORDS * 32 : HEAVY_NUM_W;
   constexpr int WWORDS = WCOLS / 32;
   Acc* acc = (Acc*)(win + (SYM ? 0 : 4 * WWORDS));
+  // numeric entry cache: a_ik, cursor into B row k, end of B row k
+  In* c_a = (In*)(win + (SYM ? 0 : 4 * WWORDS + sizeof(Acc) * WCOLS));
+  int64_t* c_pos = (int64_t*)((unsigned char*)c_a + 8 * HEAVY_CACHE);
+  int64_t* c_end = c_pos + HEAVY_CACHE;
   DevStatus* st = (DevStatus*)status;
   const int32_t count = *count_ptr;
   for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
@@ -648,8 +654,10 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
       const int64_t c = item >> 5;
       nent = Acl.uptr[c + 1] - Acl.uptr[c];
     }
-    // ---- pass 0: column range of the row's products
+    const bool cached = !SYM && nent <= HEAVY_CACHE;
+    // ---- pass 0: column range of the row's products (and the entry cache)
     int32_t lo = PAD_KEY, hi = -1;
+    int ncache = 0;
     if (tid == 0) *s_run = 0;
     __syncthreads();
     for (int64_t cb = 0; cb < nent; cb += blockDim.x) {
@@ -662,7 +670,13 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
           lo = min(lo, B.col[s]);
           hi = max(hi, B.col[e - 1]);
         }
+        if (cached) {
+          c_a[ncache + i] = s_a[i];
+          c_pos[ncache + i] = s;
+          c_end[ncache + i] = e;
+        }
       }
+      ncache += n;
       __syncthreads();
     }
     lo = warp_min(lo);
@@ -695,7 +709,24 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
         for (int i = tid; i < WCOLS; i += blockDim.x) acc[i] = Acc(0);
       if (tid == 0) *s_run = 0;
       __syncthreads();
-      for (int64_t cb = 0; cb < nent; cb += blockDim.x) {
+      if (cached) {
+        // thread per cached entry: its B row from the cursor to the window's end
+        for (int i = tid; i < ncache; i += blockDim.x) {
+          int64_t q = c_pos[i];
+          const int64_t e = c_end[i];
+          const In a = c_a[i];
+          for (; q < e; ++q) {
+            const int32_t j = B.col[q];
+            if (j >= wend) break;
+            const int o = (int)(j - base);
+            atomicOr(&bits[o >> 5], 1u << (o & 31));
+            VT<DT>::atomic_add(&acc[o], VT<DT>::mul(a, ((const In*)B.val)[q]));
+          }
+          c_pos[i] = q;
+        }
+        __syncthreads();
+      }
+      for (int64_t cb = 0; cb < (cached ? 0 : nent); cb += blockDim.x) {
         gather_chunk<DT>(Ac, Acl, SRC, item, cb, s_k, s_a, tmp, s_n, s_run);
         const int n = *s_n;
         for (int i = w; i < n; i += nw) {
@@ -764,7 +795,7 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
 inline size_t row_heavy_smem(bool sym, int acc_bytes) {
   const size_t head = 512 + 4 * HEAVY_THREADS + 8 * HEAVY_THREADS;
   return sym ? head + 4 * (size_t)HEAVY_SYM_WORDS
-             : head + 4 * (size_t)(HEAVY_NUM_W / 32) + (size_t)acc_bytes * HEAVY_NUM_W;
+             : head + 4 * (size_t)(HEAVY_NUM_W / 32) + (size_t)acc_bytes * HEAVY_NUM_W + 24 * (size_t)HEAVY_CACHE;
 }
 
 }  // namespace sgc
