@@ -31,7 +31,7 @@ constexpr int CL_THREADS = 256;  // 8 independent warps per CTA at most
 
 // Per-warp shared-memory budget classes (bytes), NDB of them.
 __host__ __device__ inline int warp_class_bytes(int b) {
-  const int kb[NDB] = {4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 160, 227};
+  const int kb[NDB] = {4, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 56, 64, 80, 96, 128, 160, 227};
   return kb[b] * 1024;
 }
 

@@ -43,7 +43,7 @@ struct CView {
 
 // Work bins (k_bins.cuh): NDB dense-kernel budget classes, NRB row-hash table
 // sizes (log2 T = LOG2T_MIN..LOG2T_MAX), one heavy-row list.
-constexpr int NDB = 13;  // per-group shared-memory classes of the cluster kernel
+constexpr int NDB = 18;  // per-group shared-memory classes of the cluster kernel
 constexpr int NRB = LOG2T_MAX - LOG2T_MIN + 1;
 constexpr int BIN_HEAVY = NDB + NRB;
 constexpr int NLB = 6;   // per-warp classes of the warp-per-cluster numeric kernel
