@@ -486,10 +486,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             h_brp, h_bcol, h_bval = pin(B.row_ptr), pin(B.col), pin(B.val)
         e_steps = max(1, min(args.steps, 3))
         h_out = None
-        times = []
+        times, stages = [], []
         for s in range(e_steps + 1):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
             torch.cuda.synchronize()
             t = time.perf_counter()
+            ev[0].record(stream)
             Ad.row_ptr.copy_(h_rp, non_blocking=True)
             Ad.col.copy_(h_col, non_blocking=True)
             Ad.val.copy_(h_val, non_blocking=True)
@@ -497,8 +499,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 Bd.row_ptr.copy_(h_brp, non_blocking=True)
                 Bd.col.copy_(h_bcol, non_blocking=True)
                 Bd.val.copy_(h_bval, non_blocking=True)
+            ev[1].record(stream)
             Acl2 = sgc.csr_cluster_build(Ad, perm, cptr, sgc.LAYOUT_MASKED)
+            ev[2].record(stream)
             C2 = sgc.spgemm(Acl2, Bd, opt)
+            ev[3].record(stream)
             if h_out is None:
                 h_out = (torch.empty(C2.row_ptr.shape, dtype=torch.int64, pin_memory=True),
                          torch.empty(C2.col.shape, dtype=torch.int32, pin_memory=True),
@@ -506,17 +511,22 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             h_out[0].copy_(C2.row_ptr, non_blocking=True)
             h_out[1].copy_(C2.col, non_blocking=True)
             h_out[2].copy_(C2.val, non_blocking=True)
+            ev[4].record(stream)
             torch.cuda.synchronize()
             if s > 0:
                 times.append(time.perf_counter() - t)
+                stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
             del C2, Acl2
         e_s = max_over_ranks(float(np.mean(times)), world, dev)
         h2d = int(h_rp.numel() * 8 + h_col.numel() * 4 + h_val.numel() * h_val.element_size())
         if not square:
             h2d += int(h_brp.numel() * 8 + h_bcol.numel() * 4 + h_bval.numel() * h_bval.element_size())
         d2h = int(h_out[0].numel() * 8 + h_out[1].numel() * 4 + h_out[2].numel() * h_out[2].element_size())
+        st_ms = np.mean(np.array(stages), axis=0)
         e2e = {"value": round(job_gflops(flops, world, e_s * 1e3), 3), "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h,
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(e_s * 1e3, 2),
+               "stages_ms": {"h2d": round(float(st_ms[0]), 2), "csr_cluster_build": round(float(st_ms[1]), 2),
+                             "spgemm": round(float(st_ms[2]), 2), "d2h": round(float(st_ms[3]), 2)},
                "step": "H2D of A (CSR) from pinned host memory, csr_cluster_build, spgemm_symbolic + "
                        "spgemm_numeric, D2H of C (CSR) to pinned host memory"}
 
