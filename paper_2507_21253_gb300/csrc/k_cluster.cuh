@@ -519,9 +519,14 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       group_sync(gw, gid);  // the ranking scratch is read up to here; the accumulators alias it
       Acc* acc = (Acc*)(my + Ly.acc);
       uint8_t* flg = (uint8_t*)(my + Ly.flags);
-      for (int64_t x = gt; x < (int64_t)K * n_out; x += GT) {
-        acc[x] = Acc(0);
-        flg[x] = 0;
+      {  // zero with wide stores: accumulators 16-byte aligned, flags 8-byte aligned
+        const int nacc = K * n_out;
+        uint4* za = (uint4*)acc;
+        for (int x = gt; x < (nacc >> 1); x += GT) za[x] = make_uint4(0u, 0u, 0u, 0u);
+        if ((nacc & 1) && gt == 0) acc[nacc - 1] = Acc(0);
+        uint2* zf = (uint2*)flg;
+        for (int x = gt; x < (nacc >> 3); x += GT) zf[x] = make_uint2(0u, 0u);
+        for (int x = (nacc & ~7) + gt; x < nacc; x += GT) flg[x] = 0;
       }
       group_sync(gw, gid);
       const In* av = stage_a + ashift;
