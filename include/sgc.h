@@ -227,6 +227,28 @@ int spgemm_symbolic(const sgc_csr_cluster* A, const sgc_csr* B, int64_t* c_row_p
 int spgemm_numeric(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, void* ws,
                    size_t ws_bytes, const sgc_options* opt, void* stream);
 
+/* spgemm_numeric_to_host: spgemm_numeric (same preconditions, same device C)
+ * that also copies C into host memory while the product is still being
+ * computed.  The clusters are taken in nchunks consecutive ranges of cluster
+ * ids (1..SGC_MAX_STREAM_CHUNKS; fewer when there are fewer clusters).  After
+ * range g, every original row below the smallest row of the clusters of the
+ * later ranges is final; those rows' C->col / C->val segments are copied to
+ * host_col / host_val (nnz(C) elements each, at the same offsets as on the
+ * device) on copy_stream while range g + 1 computes on stream.  host_row_ptr
+ * (nrows + 1 elements) receives C->row_ptr when it is not NULL.  The overlap
+ * is largest when clusters are ordered by their smallest row (as the
+ * hcluster_reorder* calls order them); any order gives the same result.
+ * Host buffers should be page-locked for the copies to run asynchronously.
+ * copy_stream: a stream of the caller's other than stream (not NULL).
+ * Synchronises stream once, before the first range, to read the range
+ * boundaries; on return every copy is ordered before the work enqueued on
+ * stream afterwards, so the host buffers are complete once stream is.
+ * Device-side failures are reported by sgc_workspace_status. */
+#define SGC_MAX_STREAM_CHUNKS 64
+int spgemm_numeric_to_host(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, int64_t* host_row_ptr,
+                           int32_t* host_col, void* host_val, int32_t nchunks, void* ws, size_t ws_bytes,
+                           const sgc_options* opt, void* stream, void* copy_stream);
+
 /* ---------------------------------------------------------------------------
  * Plain row-wise Gustavson SpGEMM C = A * B with A in CSR (Sec. 2.2, Fig. 1):
  * the comparison method.  Same binning, hash accumulators, sort and copy-out

@@ -52,6 +52,10 @@ struct SpWs {
   DevStatus* status;
   BinOut bins;
   int64_t* scan_tmp;
+  int32_t* range_ids;     // ncl: ids 0..ncl-1, the cluster list of a range
+  int32_t* range_count;   // SGC_MAX_STREAM_CHUNKS: clusters per range
+  int32_t* range_min;     // SGC_MAX_STREAM_CHUNKS
+  int64_t* range_bounds;  // 2 (SGC_MAX_STREAM_CHUNKS + 1)
   size_t bytes;
 };
 
@@ -69,6 +73,10 @@ SpWs carve_sp(void* base, size_t cap, int64_t nrows, int64_t ncl) {
   w.bins.ncl = ncl;
   w.bins.nrows = nrows;
   w.scan_tmp = cv.take<int64_t>(scan_tmp_elems(nrows));
+  w.range_ids = cv.take<int32_t>(ncl > 0 ? ncl : 1);
+  w.range_count = cv.take<int32_t>(SGC_MAX_STREAM_CHUNKS);
+  w.range_min = cv.take<int32_t>(SGC_MAX_STREAM_CHUNKS);
+  w.range_bounds = cv.take<int64_t>(2 * (SGC_MAX_STREAM_CHUNKS + 1));
   w.bytes = cv.off + 256;
   return w;
 }
@@ -338,6 +346,86 @@ int spgemm_numeric(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, void*
     case SGC_F32: SGC_CUDA((run_cluster_phase<false, SGC_F32>(av, bv, cv, C->row_ptr, w.bins, w.status, L))); break;
     case SGC_F64: SGC_CUDA((run_cluster_phase<false, SGC_F64>(av, bv, cv, C->row_ptr, w.bins, w.status, L))); break;
     default: SGC_CUDA((run_cluster_phase<false, SGC_I64>(av, bv, cv, C->row_ptr, w.bins, w.status, L))); break;
+  }
+  return SGC_OK;
+}
+
+int spgemm_numeric_to_host(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, int64_t* host_row_ptr,
+                           int32_t* host_col, void* host_val, int32_t nchunks, void* ws, size_t ws_bytes,
+                           const sgc_options* opt, void* stream, void* copy_stream) {
+  int rc = check_product(A, B, true);
+  if (rc) return rc;
+  rc = check_csr(C, "C", true);
+  if (rc) return rc;
+  if (C->nrows != A->nrows || C->ncols != B->ncols || C->dtype != A->dtype)
+    SGC_FAIL(SGC_INVALID_ARG, "C shape or dtype inconsistent with A*B");
+  if (nchunks < 1 || nchunks > SGC_MAX_STREAM_CHUNKS) SGC_FAIL(SGC_INVALID_ARG, "nchunks out of range");
+  if (!copy_stream || copy_stream == stream) SGC_FAIL(SGC_INVALID_ARG, "copy_stream must be a second stream");
+  if (C->nnz > 0 && (!host_col || !host_val)) SGC_FAIL(SGC_INVALID_ARG, "NULL host_col / host_val");
+  SpWs w = carve_sp(ws, ws_bytes, A->nrows, A->nclusters);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream, cs = (cudaStream_t)copy_stream;
+  const ResolvedOptions o = resolve(opt);
+  Launch L{s, o, num_sms(), 0};
+  rc = resolve_mode(o, B, true, &L.mode);
+  if (rc) return rc;
+  const size_t vb = dtype_bytes(A->dtype);
+  SGC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+  const int G = (int)(A->nclusters < nchunks ? A->nclusters : nchunks);
+  int64_t hb[2 * (SGC_MAX_STREAM_CHUNKS + 1)];
+  if (A->nrows > 0 && C->nnz > 0)
+    SGC_CUDA(stream_ranges_run(A->perm, A->cluster_ptr, A->nclusters, A->nrows, G, C->row_ptr, w.range_ids,
+                               w.range_count, w.range_min, w.range_bounds, L.sms, s));
+  if (A->nrows > 0 && C->nnz > 0)
+    SGC_CUDA(cudaMemcpyAsync(hb, w.range_bounds, sizeof(int64_t) * (2 * G + 2), cudaMemcpyDeviceToHost, s));
+  SGC_CUDA(cudaStreamSynchronize(s));  // the symbolic row pointer and the boundaries are final
+  if (host_row_ptr)
+    SGC_CUDA(cudaMemcpyAsync(host_row_ptr, C->row_ptr, sizeof(int64_t) * (A->nrows + 1), cudaMemcpyDeviceToHost,
+                             cs));
+  if (A->nrows > 0 && C->nnz > 0) {
+    const AClusterView av = cview(A, true);
+    const BView bv = bview(B, true);
+    const CView cv{C->row_ptr, C->col, C->val};
+    std::vector<cudaEvent_t> ev(G, nullptr);
+    cudaError_t e = cudaSuccess;
+    int64_t done = hb[G + 1];
+    for (int g = 0; g < G && e == cudaSuccess; ++g) {
+      BinOut b = w.bins;
+      b.clist = w.range_ids + (int64_t)g * A->nclusters / G;
+      b.clist_count = w.range_count + g;
+      switch (A->dtype) {
+        case SGC_F32: e = run_cluster_phase<false, SGC_F32>(av, bv, cv, C->row_ptr, b, w.status, L); break;
+        case SGC_F64: e = run_cluster_phase<false, SGC_F64>(av, bv, cv, C->row_ptr, b, w.status, L); break;
+        default: e = run_cluster_phase<false, SGC_I64>(av, bv, cv, C->row_ptr, b, w.status, L); break;
+      }
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[g], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[g], s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[g], 0);
+      const int64_t upto = hb[G + 2 + g];  // c_rp[r_{g+1}]: entries of the rows now final
+      if (e == cudaSuccess && upto > done) {
+        e = cudaMemcpyAsync(host_col + done, (const int32_t*)C->col + done, sizeof(int32_t) * (upto - done),
+                            cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync((char*)host_val + done * vb, (const char*)C->val + done * vb, vb * (upto - done),
+                              cudaMemcpyDeviceToHost, cs);
+        done = upto;
+      }
+    }
+    cudaEvent_t fin = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fin, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(fin, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fin, 0);  // later work on stream follows the copies
+    for (cudaEvent_t x : ev)
+      if (x) cudaEventDestroy(x);
+    if (fin) cudaEventDestroy(fin);
+    SGC_CUDA(e);
+  } else if (host_row_ptr) {
+    cudaEvent_t fin = nullptr;
+    SGC_CUDA(cudaEventCreateWithFlags(&fin, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(fin, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fin, 0);
+    cudaEventDestroy(fin);
+    SGC_CUDA(e);
   }
   return SGC_OK;
 }

@@ -135,6 +135,12 @@ cudaError_t vlen_runs_run(const int64_t* rp, const int32_t* col, int64_t n, doub
                           int sms, cudaStream_t s);
 int64_t vlen_chain_host(const uint8_t* run, int64_t n, int max_cluster, int64_t* cluster_ptr);
 cudaError_t fixed_clusters_run(int64_t n, int K, int32_t* perm, int64_t* cluster_ptr, int sms, cudaStream_t s);
+// Range boundaries of the streamed numeric phase (k_stream.cu): ids[c] = c,
+// counts[g] = clusters of range g, bounds[0..G] = first non-final row after
+// each range, bounds[G+1..2G+1] = c_rp at those rows.  mins: G scratch ints.
+cudaError_t stream_ranges_run(const int32_t* perm, const int64_t* cptr, int64_t ncl, int64_t nrows, int G,
+                              const int64_t* c_rp, int32_t* ids, int32_t* counts, int32_t* mins, int64_t* bounds,
+                              int sms, cudaStream_t s);
 
 // k_hc.cu / hc_merge.cpp
 cudaError_t hc_candidates_run(const int64_t* arp, const int32_t* acol, int64_t nrows, int64_t ncols, int64_t nnz,

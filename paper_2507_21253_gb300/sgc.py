@@ -88,6 +88,8 @@ _c = {
                             P(Options), vp),
     "spgemm_numeric": _sig("spgemm_numeric", P(ClusterStruct), P(CsrStruct), P(CsrStruct), vp, ctypes.c_size_t,
                            P(Options), vp),
+    "spgemm_numeric_to_host": _sig("spgemm_numeric_to_host", P(ClusterStruct), P(CsrStruct), P(CsrStruct), vp, vp,
+                                   vp, i32, vp, ctypes.c_size_t, P(Options), vp, vp),
     "spgemm_rowwise_workspace_size": _sig("spgemm_rowwise_workspace_size", P(CsrStruct), P(CsrStruct),
                                           P(Options), P(ctypes.c_size_t)),
     "spgemm_rowwise_symbolic": _sig("spgemm_rowwise_symbolic", P(CsrStruct), P(CsrStruct), vp, P(i64), vp,
@@ -298,6 +300,43 @@ def spgemm_numeric(A: DeviceCsrCluster, B: DeviceCsr, c_row_ptr: torch.Tensor, n
     a, b, c = A.struct(), B.struct(), C.struct()
     _call("spgemm_numeric", ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ws.ptr, ws.nbytes,
           ctypes.byref(opt) if opt else None, _stream())
+    return C
+
+
+_copy_streams: dict = {}
+
+
+def _copy_stream(dev):
+    dev = torch.device(dev)
+    if dev not in _copy_streams:
+        _copy_streams[dev] = torch.cuda.Stream(device=dev)
+    return _copy_streams[dev]
+
+
+def spgemm_numeric_to_host(A: DeviceCsrCluster, B: DeviceCsr, c_row_ptr: torch.Tensor, nnz: int, ws: Workspace,
+                           host_col: torch.Tensor, host_val: torch.Tensor, host_row_ptr: torch.Tensor | None = None,
+                           nchunks: int = 8, opt: Options | None = None, C: DeviceCsr | None = None,
+                           copy_stream: torch.cuda.Stream | None = None) -> DeviceCsr:
+    """spgemm_numeric that also copies C into the (pinned) host tensors while it computes.
+
+    The host tensors are complete once the current stream has finished (for
+    instance after torch.cuda.synchronize())."""
+    dev = B.row_ptr.device
+    if host_col.dtype != torch.int32 or host_col.numel() < nnz or host_col.device.type != "cpu":
+        raise ValueError("host_col: int32 host tensor of nnz(C) elements")
+    if host_val.dtype != B.val.dtype or host_val.numel() < nnz or host_val.device.type != "cpu":
+        raise ValueError("host_val: host tensor of nnz(C) elements of B's value type")
+    if host_row_ptr is not None and (host_row_ptr.dtype != torch.int64 or host_row_ptr.numel() < A.nrows + 1
+                                     or host_row_ptr.device.type != "cpu"):
+        raise ValueError("host_row_ptr: int64 host tensor of nrows + 1 elements")
+    if C is None:
+        C = DeviceCsr(A.nrows, B.ncols, c_row_ptr, torch.empty(nnz, dtype=torch.int32, device=dev),
+                      torch.empty(nnz, dtype=B.val.dtype, device=dev))
+    cs = copy_stream if copy_stream is not None else _copy_stream(dev)
+    a, b, c = A.struct(), B.struct(), C.struct()
+    _call("spgemm_numeric_to_host", ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+          vp(host_row_ptr.data_ptr()) if host_row_ptr is not None else vp(0), _ptr(host_col), _ptr(host_val),
+          int(nchunks), ws.ptr, ws.nbytes, ctypes.byref(opt) if opt else None, _stream(), vp(cs.cuda_stream))
     return C
 
 
