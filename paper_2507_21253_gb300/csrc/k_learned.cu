@@ -248,20 +248,31 @@ __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, co
 
 // copy the slab rows of clusters that did not overflow into C (warp per cluster)
 template <class V>
-__global__ void __launch_bounds__(256) k_compact(AClusterView A, const int32_t* flag, const int64_t* slab_off,
-                                                 const int32_t* slab_col, const V* slab_val, const int64_t* c_rp,
-                                                 int32_t* ccol, V* cval) {
+__global__ void __launch_bounds__(256) k_compact(AClusterView A, const int32_t* __restrict__ flag,
+                                                 const int64_t* __restrict__ slab_off,
+                                                 const int32_t* __restrict__ slab_col, const V* __restrict__ slab_val,
+                                                 const int64_t* __restrict__ c_rp, int32_t* __restrict__ ccol,
+                                                 V* __restrict__ cval) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   for (int64_t c = gw; c < A.ncl; c += nwarps) {
     if (flag[c]) continue;
-    const int64_t p0 = A.cptr[c], p1 = A.cptr[c + 1];
-    for (int64_t p = p0; p < p1; ++p) {
-      const int64_t r = A.perm[p];
-      const int64_t dst = c_rp[r], n = c_rp[r + 1] - dst, src = slab_off[p];
-      for (int64_t q = lane; q < n; q += 32) {
-        ccol[dst + q] = slab_col[src + q];
-        cval[dst + q] = slab_val[src + q];
+    const int64_t p0 = A.cptr[c];
+    const int K = (int)(A.cptr[c + 1] - p0);  // at most 32
+    // lane l holds row l's destination, length and slab offset (one round of loads for the cluster)
+    int64_t dst = 0, n = 0, src = 0;
+    if (lane < K) {
+      const int64_t r = A.perm[p0 + lane];
+      dst = c_rp[r];
+      n = c_rp[r + 1] - dst;
+      src = slab_off[p0 + lane];
+    }
+    for (int l = 0; l < K; ++l) {
+      const int64_t d = __shfl_sync(FULL, dst, l), m = __shfl_sync(FULL, n, l), sp = __shfl_sync(FULL, src, l);
+#pragma unroll 4
+      for (int64_t q = lane; q < m; q += 32) {
+        ccol[d + q] = slab_col[sp + q];
+        cval[d + q] = slab_val[sp + q];
       }
     }
   }

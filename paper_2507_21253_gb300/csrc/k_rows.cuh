@@ -642,6 +642,7 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
   In* c_a = (In*)(win + (SYM ? 0 : 4 * WWORDS + sizeof(Acc) * WCOLS));
   int64_t* c_pos = (int64_t*)((unsigned char*)c_a + 8 * HEAVY_CACHE);
   int64_t* c_end = c_pos + HEAVY_CACHE;
+  int32_t* c_next = (int32_t*)(c_end + HEAVY_CACHE);  // B.col at the cursor, -1 past the row's end
   DevStatus* st = (DevStatus*)status;
   const int32_t count = *count_ptr;
   for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
@@ -655,6 +656,7 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
       nent = Acl.uptr[c + 1] - Acl.uptr[c];
     }
     const bool cached = !SYM && nent <= HEAVY_CACHE;
+    const bool pf = ((reinterpret_cast<uintptr_t>(B.col) | reinterpret_cast<uintptr_t>(B.val)) & 15u) == 0;
     // ---- pass 0: column range of the row's products (and the entry cache)
     int32_t lo = PAD_KEY, hi = -1;
     int ncache = 0;
@@ -674,6 +676,11 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
           c_a[ncache + i] = s_a[i];
           c_pos[ncache + i] = s;
           c_end[ncache + i] = e;
+          c_next[ncache + i] = e > s ? B.col[s] : -1;
+          if (pf && e > s) {  // the windows walk these B rows: bring them into L2 now
+            bulk_prefetch_row(B.col, s, e - s, 4, B.nnz);
+            bulk_prefetch_row(B.val, s, e - s, (int)sizeof(In), B.nnz);
+          }
         }
       }
       ncache += n;
@@ -710,19 +717,28 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
       if (tid == 0) *s_run = 0;
       __syncthreads();
       if (cached) {
-        // thread per cached entry: its B row from the cursor to the window's end
+        // thread per cached entry: its B row from the cursor to the window's end.  The
+        // column at the cursor is kept in shared memory, so an entry with nothing in
+        // this window costs no global load; the value of the current column and the
+        // next column id are loaded together.
         for (int i = tid; i < ncache; i += blockDim.x) {
+          int32_t j = c_next[i];
+          if (j < 0 || j >= wend) continue;
           int64_t q = c_pos[i];
           const int64_t e = c_end[i];
           const In a = c_a[i];
-          for (; q < e; ++q) {
-            const int32_t j = B.col[q];
-            if (j >= wend) break;
+          for (;;) {
+            const In b = ((const In*)B.val)[q];
+            const int32_t jn = q + 1 < e ? B.col[q + 1] : -1;
             const int o = (int)(j - base);
             atomicOr(&bits[o >> 5], 1u << (o & 31));
-            VT<DT>::atomic_add(&acc[o], VT<DT>::mul(a, ((const In*)B.val)[q]));
+            VT<DT>::atomic_add(&acc[o], VT<DT>::mul(a, b));
+            ++q;
+            j = jn;
+            if (j < 0 || j >= wend) break;
           }
           c_pos[i] = q;
+          c_next[i] = j;
         }
         __syncthreads();
       }
@@ -795,7 +811,7 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
 inline size_t row_heavy_smem(bool sym, int acc_bytes) {
   const size_t head = 512 + 4 * HEAVY_THREADS + 8 * HEAVY_THREADS;
   return sym ? head + 4 * (size_t)HEAVY_SYM_WORDS
-             : head + 4 * (size_t)(HEAVY_NUM_W / 32) + (size_t)acc_bytes * HEAVY_NUM_W + 24 * (size_t)HEAVY_CACHE;
+             : head + 4 * (size_t)(HEAVY_NUM_W / 32) + (size_t)acc_bytes * HEAVY_NUM_W + 28 * (size_t)HEAVY_CACHE;
 }
 
 }  // namespace sgc
