@@ -76,8 +76,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="stencil27_160", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-chunks", type=int, default=8,
-                    help="cluster ranges of the streamed numeric phase in the e2e step (0: copy C after it)")
+    ap.add_argument("--e2e-chunks", type=int, default=0,
+                    help="e2e numeric call: 0 = kernels store C straight into pinned host memory; k > 0 = k cluster "
+                         "ranges, each followed by a copy of the rows it finished; -1 = numeric, then one copy of C")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--clustering", default="parallel", choices=["parallel", "serial"],
@@ -512,7 +513,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 h_out = (torch.empty(A.nrows + 1, dtype=torch.int64, pin_memory=True),
                          torch.empty(nnz2, dtype=torch.int32, pin_memory=True),
                          torch.empty(nnz2, dtype=Ad.val.dtype, pin_memory=True))
-            if chunks > 0:   # numeric with C streamed to the host buffers as rows become final
+            if chunks >= 0:  # numeric with C streamed to the host buffers while it computes
                 C2 = sgc.spgemm_numeric_to_host(Acl2, Bd, rp2, nnz2, ws2, h_out[1], h_out[2], h_out[0],
                                                 nchunks=chunks, opt=opt)
                 ev[4].record(stream)
@@ -535,13 +536,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             h2d += int(h_brp.numel() * 8 + h_bcol.numel() * 4 + h_bval.numel() * h_bval.element_size())
         d2h = int(h_out[0].numel() * 8 + h_out[1].numel() * 4 + h_out[2].numel() * h_out[2].element_size())
         st_ms = np.mean(np.array(stages), axis=0)
-        if chunks > 0:
+        if chunks >= 0:
             stage_ms = {"h2d": round(float(st_ms[0]), 2), "csr_cluster_build": round(float(st_ms[1]), 2),
                         "symbolic": round(float(st_ms[2]), 2),
                         "numeric_with_d2h_overlapped": round(float(st_ms[3] + st_ms[4]), 2)}
+            how = ("the numeric kernels store C straight into pinned host memory" if chunks == 0 else
+                   f"{chunks} cluster ranges, C copied to pinned host memory as its rows become final")
             what = (f"H2D of A (CSR) from pinned host memory, csr_cluster_build, spgemm_symbolic, "
-                    f"spgemm_numeric_to_host ({chunks} cluster ranges; C copied to pinned host memory as its rows "
-                    f"become final, overlapping the numeric phase)")
+                    f"spgemm_numeric_to_host ({how})")
         else:
             stage_ms = {"h2d": round(float(st_ms[0]), 2), "csr_cluster_build": round(float(st_ms[1]), 2),
                         "symbolic": round(float(st_ms[2]), 2), "numeric": round(float(st_ms[3]), 2),

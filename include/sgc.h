@@ -239,6 +239,12 @@ int spgemm_numeric(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, void*
  * is largest when clusters are ordered by their smallest row (as the
  * hcluster_reorder* calls order them); any order gives the same result.
  * Host buffers should be page-locked for the copies to run asynchronously.
+ * nchunks = 0 selects the direct mode: the numeric kernels store C's entries
+ * straight into host_col / host_val through their device-mapped addresses
+ * (page-locked memory from cudaHostAlloc or cudaHostRegister, mapped for the
+ * device; anything else is rejected with SGC_INVALID_ARG), so the transfer
+ * overlaps the whole numeric phase whatever the cluster order; C->col and
+ * C->val are not written and may be NULL.
  * copy_stream: a stream of the caller's other than stream (not NULL).
  * Synchronises stream once, before the first range, to read the range
  * boundaries; on return every copy is ordered before the work enqueued on

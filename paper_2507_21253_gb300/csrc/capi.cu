@@ -350,18 +350,75 @@ int spgemm_numeric(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, void*
   return SGC_OK;
 }
 
+// Direct mode of spgemm_numeric_to_host: the numeric kernels store C's
+// entries straight into the caller's page-locked host buffers (through their
+// device-mapped addresses), so the copy to the host runs inside the kernels.
+static int numeric_host_direct(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, int64_t* host_row_ptr,
+                               int32_t* host_col, void* host_val, void* ws, size_t ws_bytes, const sgc_options* opt,
+                               cudaStream_t s, cudaStream_t cs) {
+  SpWs w = carve_sp(ws, ws_bytes, A->nrows, A->nclusters);
+  if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  const ResolvedOptions o = resolve(opt);
+  Launch L{s, o, num_sms(), 0};
+  int rc = resolve_mode(o, B, true, &L.mode);
+  if (rc) return rc;
+  void* dcol = nullptr;
+  void* dval = nullptr;
+  if (C->nnz > 0) {
+    for (int x = 0; x < 2; ++x) {
+      void* hp = x == 0 ? (void*)host_col : host_val;
+      cudaPointerAttributes pa{};
+      if (cudaPointerGetAttributes(&pa, hp) != cudaSuccess || pa.type != cudaMemoryTypeHost || !pa.devicePointer) {
+        cudaGetLastError();
+        SGC_FAIL(SGC_INVALID_ARG, "direct mode (nchunks 0) needs page-locked, device-mapped host_col / host_val");
+      }
+      (x == 0 ? dcol : dval) = pa.devicePointer;
+    }
+  }
+  SGC_CUDA(cudaMemsetAsync(w.status, 0, sizeof(DevStatus), s));
+  cudaEvent_t ready = nullptr, fin = nullptr;
+  SGC_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  cudaError_t e = cudaEventCreateWithFlags(&fin, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ready, s);  // the symbolic row pointer is final here
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
+  if (e == cudaSuccess && host_row_ptr)
+    e = cudaMemcpyAsync(host_row_ptr, C->row_ptr, sizeof(int64_t) * (A->nrows + 1), cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess && A->nrows > 0 && C->nnz > 0) {
+    const CView cv{C->row_ptr, (int32_t*)dcol, dval};
+    const AClusterView av = cview(A, true);
+    const BView bv = bview(B, true);
+    switch (A->dtype) {
+      case SGC_F32: e = run_cluster_phase<false, SGC_F32>(av, bv, cv, C->row_ptr, w.bins, w.status, L); break;
+      case SGC_F64: e = run_cluster_phase<false, SGC_F64>(av, bv, cv, C->row_ptr, w.bins, w.status, L); break;
+      default: e = run_cluster_phase<false, SGC_I64>(av, bv, cv, C->row_ptr, w.bins, w.status, L); break;
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(fin, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fin, 0);
+  if (ready) cudaEventDestroy(ready);
+  if (fin) cudaEventDestroy(fin);
+  SGC_CUDA(e);
+  return SGC_OK;
+}
+
 int spgemm_numeric_to_host(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, int64_t* host_row_ptr,
                            int32_t* host_col, void* host_val, int32_t nchunks, void* ws, size_t ws_bytes,
                            const sgc_options* opt, void* stream, void* copy_stream) {
   int rc = check_product(A, B, true);
   if (rc) return rc;
-  rc = check_csr(C, "C", true);
-  if (rc) return rc;
+  if (nchunks != 0) {
+    rc = check_csr(C, "C", true);
+    if (rc) return rc;
+  } else if (!C || !C->row_ptr || C->nrows < 0 || C->nnz < 0) {  // direct mode: C's col / val may be NULL
+    SGC_FAIL(SGC_INVALID_ARG, "C or C.row_ptr is NULL");
+  }
   if (C->nrows != A->nrows || C->ncols != B->ncols || C->dtype != A->dtype)
     SGC_FAIL(SGC_INVALID_ARG, "C shape or dtype inconsistent with A*B");
-  if (nchunks < 1 || nchunks > SGC_MAX_STREAM_CHUNKS) SGC_FAIL(SGC_INVALID_ARG, "nchunks out of range");
+  if (nchunks < 0 || nchunks > SGC_MAX_STREAM_CHUNKS) SGC_FAIL(SGC_INVALID_ARG, "nchunks out of range");
   if (!copy_stream || copy_stream == stream) SGC_FAIL(SGC_INVALID_ARG, "copy_stream must be a second stream");
   if (C->nnz > 0 && (!host_col || !host_val)) SGC_FAIL(SGC_INVALID_ARG, "NULL host_col / host_val");
+  if (nchunks == 0) return numeric_host_direct(A, B, C, host_row_ptr, host_col, host_val, ws, ws_bytes, opt,
+                                               (cudaStream_t)stream, (cudaStream_t)copy_stream);
   SpWs w = carve_sp(ws, ws_bytes, A->nrows, A->nclusters);
   if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
   cudaStream_t s = (cudaStream_t)stream, cs = (cudaStream_t)copy_stream;

@@ -319,8 +319,9 @@ def spgemm_numeric_to_host(A: DeviceCsrCluster, B: DeviceCsr, c_row_ptr: torch.T
                            copy_stream: torch.cuda.Stream | None = None) -> DeviceCsr:
     """spgemm_numeric that also copies C into the (pinned) host tensors while it computes.
 
-    The host tensors are complete once the current stream has finished (for
-    instance after torch.cuda.synchronize())."""
+    nchunks = 0: the kernels store C straight into the pinned host tensors and the
+    returned C has no device col / val.  The host tensors are complete once the
+    current stream has finished (for instance after torch.cuda.synchronize())."""
     dev = B.row_ptr.device
     if host_col.dtype != torch.int32 or host_col.numel() < nnz or host_col.device.type != "cpu":
         raise ValueError("host_col: int32 host tensor of nnz(C) elements")
@@ -329,11 +330,20 @@ def spgemm_numeric_to_host(A: DeviceCsrCluster, B: DeviceCsr, c_row_ptr: torch.T
     if host_row_ptr is not None and (host_row_ptr.dtype != torch.int64 or host_row_ptr.numel() < A.nrows + 1
                                      or host_row_ptr.device.type != "cpu"):
         raise ValueError("host_row_ptr: int64 host tensor of nrows + 1 elements")
-    if C is None:
-        C = DeviceCsr(A.nrows, B.ncols, c_row_ptr, torch.empty(nnz, dtype=torch.int32, device=dev),
-                      torch.empty(nnz, dtype=B.val.dtype, device=dev))
+    if nchunks == 0:   # direct mode: the kernels write the host buffers; no device copy of C
+        if nnz > 0 and not (host_col.is_pinned() and host_val.is_pinned()):
+            raise ValueError("direct mode (nchunks=0) needs pinned host_col / host_val")
+        if C is None:
+            C = DeviceCsr(A.nrows, B.ncols, c_row_ptr, torch.empty(0, dtype=torch.int32, device=dev),
+                          torch.empty(0, dtype=B.val.dtype, device=dev))
+        c = CsrStruct(A.nrows, B.ncols, int(nnz), _ptr(c_row_ptr), vp(0), vp(0), _DT[B.val.dtype], 0)
+    else:
+        if C is None:
+            C = DeviceCsr(A.nrows, B.ncols, c_row_ptr, torch.empty(nnz, dtype=torch.int32, device=dev),
+                          torch.empty(nnz, dtype=B.val.dtype, device=dev))
+        c = C.struct()
     cs = copy_stream if copy_stream is not None else _copy_stream(dev)
-    a, b, c = A.struct(), B.struct(), C.struct()
+    a, b = A.struct(), B.struct()
     _call("spgemm_numeric_to_host", ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
           vp(host_row_ptr.data_ptr()) if host_row_ptr is not None else vp(0), _ptr(host_col), _ptr(host_val),
           int(nchunks), ws.ptr, ws.nbytes, ctypes.byref(opt) if opt else None, _stream(), vp(cs.cuda_stream))
