@@ -58,17 +58,18 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
     const int64_t u0 = A.uptr[c], u1 = A.uptr[c + 1];
     s_ub[w][lane] = 0;
     __syncwarp();
-    int64_t U = 0;
-    for (int64_t t = u0 + lane; t < u1; t += 32) {
-      const int32_t k = A.ucol[t];
-      const int64_t len = B.rp[k + 1] - B.rp[k];
-      U += len;
-      uint32_t m = A.mask[t];
-      while (m) {
-        const int l = __ffs(m) - 1;
-        m &= m - 1;
-        atomicAdd(&s_ub[w][l], (unsigned long long)len);
+    int64_t U = 0, ubr = 0;
+    for (int64_t tb = u0; tb < u1; tb += 32) {  // warp-uniform trip count
+      const int64_t t = tb + lane;
+      int64_t len = 0;
+      uint32_t m = 0;
+      if (t < u1) {
+        const int32_t k = A.ucol[t];
+        len = B.rp[k + 1] - B.rp[k];
+        m = A.mask[t];
       }
+      U += len;
+      if (K > 1) add_row_bounds(m, len, K, lane, &ubr, s_ub[w]);  // one row: its bound is U
     }
     U = warp_sum(U);
     __syncwarp();
@@ -86,7 +87,7 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
       if (cls >= 0) push_dense(o, cls, (int32_t)c);
     }
     if (cls < 0 && lane < K) {
-      const int64_t ub = (int64_t)s_ub[w][lane];
+      const int64_t ub = K == 1 ? U : ubr + (int64_t)s_ub[w][lane];
       const int64_t row = A.perm[p0 + lane];
       if (ub == 0)
         c_rp[row + 1] = 0;

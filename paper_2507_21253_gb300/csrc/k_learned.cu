@@ -32,38 +32,45 @@ __global__ void __launch_bounds__(256) k_features(AClusterView A, BView B, float
     const int64_t u0 = A.uptr[c], u1 = A.uptr[c + 1], T = u1 - u0;
     s_ub[w][lane] = 0;
     __syncwarp();
-    int64_t U = 0, nA = 0;
-    for (int64_t t = u0 + lane; t < u1; t += 32) {
-      const int32_t k = A.ucol[t];
-      const int64_t len = B.rp[k + 1] - B.rp[k];
-      uint32_t m = A.mask[t];
+    int64_t U = 0, nA = 0, ubr = 0;
+    int32_t first = 0, last = 0;
+    for (int64_t tb = u0; tb < u1; tb += 32) {  // warp-uniform trip count
+      const int64_t t = tb + lane;
+      int32_t k = 0;
+      int64_t len = 0;
+      uint32_t m = 0;
+      if (t < u1) {
+        k = A.ucol[t];
+        len = B.rp[k + 1] - B.rp[k];
+        m = A.mask[t];
+      }
       U += len;
       nA += __popc(m);
-      while (m) {
-        const int l = __ffs(m) - 1;
-        m &= m - 1;
-        atomicAdd(&s_ub[w][l], (unsigned long long)len);
-      }
+      if (tb == u0) first = __shfl_sync(FULL, k, 0);
+      if (u1 - tb <= 32) last = __shfl_sync(FULL, k, (int)(u1 - tb - 1));
+      if (K > 1) add_row_bounds(m, len, K, lane, &ubr, s_ub[w]);  // one row: its bound is U
     }
     U = warp_sum(U);
     nA = warp_sum(nA);
     __syncwarp();
-    const int64_t ub = lane < K ? (int64_t)s_ub[w][lane] : 0;
+    const int64_t ub = lane < K ? (K == 1 ? U : ubr + (int64_t)s_ub[w][lane]) : 0;
     const int64_t sub = warp_sum(ub), mub = warp_max(ub);
     if (lane < K && h_pos) h_pos[p0 + lane] = (int32_t)min64(ub, B.ncols);
-    if (lane == 0) {
-      float* x = X + c * NFEAT;
-      const float span = T > 0 ? (float)(A.ucol[u1 - 1] - A.ucol[u0] + 1) / (float)B.ncols : 0.0f;
-      x[0] = (float)K / 32.0f;
-      x[1] = log1pf((float)T) / 8.0f;
-      x[2] = log1pf((float)nA) / 8.0f;
-      x[3] = log1pf((float)U) / 8.0f;
-      x[4] = log1pf((float)sub) / 8.0f;
-      x[5] = log1pf((float)mub) / 8.0f;
-      x[6] = log1pf((float)B.ncols) / 16.0f;
-      x[7] = span;
-      if (uc_out) uc_out[c] = (int32_t)min64(U, 0x7fffffff);
+    if (lane < NFEAT) {  // one feature a lane
+      float v;
+      switch (lane) {
+        case 0: v = (float)K / 32.0f; break;
+        case 1: v = log1pf((float)T) / 8.0f; break;
+        case 2: v = log1pf((float)nA) / 8.0f; break;
+        case 3: v = log1pf((float)U) / 8.0f; break;
+        case 4: v = log1pf((float)sub) / 8.0f; break;
+        case 5: v = log1pf((float)mub) / 8.0f; break;
+        case 6: v = log1pf((float)B.ncols) / 16.0f; break;
+        default: v = T > 0 ? (float)(last - first + 1) / (float)B.ncols : 0.0f; break;
+      }
+      X[c * NFEAT + lane] = v;
     }
+    if (lane == 0 && uc_out) uc_out[c] = (int32_t)min64(U, 0x7fffffff);
     __syncwarp();
   }
 }

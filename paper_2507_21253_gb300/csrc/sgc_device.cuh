@@ -108,6 +108,27 @@ __device__ __forceinline__ T warp_min(T v) {
   }
   return v;
 }
+// Per-row flop bounds over one chunk of up to 32 union columns of a cluster:
+// lane l < K adds to *ub the B-row lengths of the chunk's columns whose mask
+// has bit l.  One warp reduction per row; every lane calls it (len = 0,
+// m = 0 past the cluster's end).  A chunk whose 32-bit partial sums could
+// overflow goes through the shared array s_big (per row, 64-bit) instead.
+__device__ __forceinline__ void add_row_bounds(uint32_t m, int64_t len, int K, int lane, int64_t* ub,
+                                               unsigned long long* s_big) {
+  if (__any_sync(FULL, len >= (1ll << 26))) {  // 32 terms below 2^26 stay below 2^31
+    while (m) {
+      const int l = __ffs(m) - 1;
+      m &= m - 1;
+      atomicAdd(&s_big[l], (unsigned long long)len);
+    }
+    return;
+  }
+  for (int l = 0; l < K; ++l) {
+    const unsigned sum = __reduce_add_sync(FULL, ((m >> l) & 1u) ? (unsigned)len : 0u);
+    if (lane == l) *ub += sum;
+  }
+}
+
 template <class T>
 __device__ __forceinline__ T warp_incl_scan(T v) {
   const int lane = lane_id();
