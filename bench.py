@@ -85,7 +85,7 @@ def parse():
                     help="merge of the hierarchical clustering: round-parallel on the GPU (default) or the serial heap")
     ap.add_argument("--no-alt-clustering", action="store_true", help="skip timing the other merge")
     ap.add_argument("--epochs", type=int, default=20, help="predictor training epochs")
-    ap.add_argument("--margin", type=float, default=1.1, help="capacity margin over the predicted output columns")
+    ap.add_argument("--margin", type=float, default=1.05, help="capacity margin over the predicted output columns")
     ap.add_argument("--fused-fma", type=int, default=0, help="FP64: accumulate with fused multiply-add")
     ap.add_argument("--cluster-load", type=int, default=0, help="numeric cluster-table fill limit, percent (0: default)")
     ap.add_argument("--cluster-kernel", type=int, default=0,
