@@ -246,10 +246,15 @@ int spgemm_numeric(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, void*
  * overlaps the whole numeric phase whatever the cluster order; C->col and
  * C->val are not written and may be NULL.
  * copy_stream: a stream of the caller's other than stream (not NULL).
- * Synchronises stream once, before the first range, to read the range
- * boundaries; on return every copy is ordered before the work enqueued on
- * stream afterwards, so the host buffers are complete once stream is.
- * Device-side failures are reported by sgc_workspace_status. */
+ * The range mode synchronises stream once, before the first range, to read
+ * the range boundaries; the direct mode does not synchronise.  In both, on
+ * return every copy is ordered before the work enqueued on stream afterwards,
+ * so the host buffers are complete once stream is.  Errors: nchunks outside
+ * 0..SGC_MAX_STREAM_CHUNKS, copy_stream NULL or equal to stream, NULL host
+ * buffers with nnz(C) > 0, or (direct mode) host buffers the device cannot
+ * address: SGC_INVALID_ARG; a workspace below spgemm_workspace_size:
+ * SGC_WORKSPACE_TOO_SMALL.  Device-side failures are reported by
+ * sgc_workspace_status. */
 #define SGC_MAX_STREAM_CHUNKS 64
 int spgemm_numeric_to_host(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, int64_t* host_row_ptr,
                            int32_t* host_col, void* host_val, int32_t nchunks, void* ws, size_t ws_bytes,
