@@ -283,7 +283,8 @@ def run_reference(args, rank: int):
     out = {"metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "impl": "reference", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": desc, "flops": flops},
+           "config": {"workload": desc, "n": int(A.nrows), "nnz_A": int(A.nnz), "flops": flops,
+                      "parallelism": "host cores"},
            "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                             "sample": f"{sample_rows} random rows of C per step (serial std::map Gustavson per row, "
                                       f"rows spread over {cores} OpenMP threads); rate scaled to the whole product"},
