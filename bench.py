@@ -2,11 +2,17 @@
 """Benchmark of cluster-wise SpGEMM (CSR_Cluster, hierarchical clustering) on GB300.
 
 One step = the whole per-product hot path on one input that is already
-resident in HBM: the symbolic phase (binning, cluster kernels, scan) and the
-numeric phase of C = A*A with A in CSR_Cluster form.  Preprocessing
-(hierarchical clustering + CSR_Cluster build) is timed separately and reported
-in units of one step.  The plain row-wise method runs on the same GPU in the
-same process and is reported beside it.
+resident in HBM.  The headline method is clustered + learned: the learned
+plan (features, MLP, capacities), one cluster-wise numeric pass into a slab,
+the exact path for under-predicted clusters, and the compaction into CSR C.
+The exact clustered path (symbolic + numeric) and the plain row-wise method
+run on the same GPU in the same process and are reported beside it.
+Preprocessing (hierarchical clustering + CSR_Cluster build) is timed
+separately and reported in units of one step.
+
+The headline line is the largest workload (the 27-point stencil on 160^3);
+the other four workloads are measured in the same run, with fewer steps, and
+reported under "configs".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
@@ -18,9 +24,9 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
-import re
+import multiprocessing as mp
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -35,37 +41,94 @@ from paper_2507_21253_gb300 import synth  # noqa: E402
 
 METRIC = "SpGEMM GFLOP/s & HBM GB/s, clustered+learned vs plain row-wise, same GB300"
 
+# The paper's own clustering figure, for context only (a CPU, other inputs):
+# Sec. 4.2 (geometric mean over its inputs), hardware from Sec. 4.1.
+PAPER_CONTEXT = {
+    "clustering_speedup_vs_rowwise_geomean": 1.39,
+    "hardware": "1x AMD EPYC 7763 (Milan), 64 threads on one CPU, 204.8 GB/s DDR4; C++/OpenMP (icpc -O3), "
+                "hash-table accumulator, average of 10 runs",
+    "inputs": "A^2 on 110 SuiteSparse matrices (not available here)",
+    "source": "Sec. 4.1 (evaluation setup) and Sec. 4.2 (impact of clustering)",
+}
+
 # generator of the predictor's training instances for each workload (seeded smaller
 # instances of the same generator) and how many of them
-TRAINING = {"stencil27_160": ("stencil_instance", 24), "stencil27_80": ("stencil_instance", 24),
-            "laplacian64": ("laplacian_instance", 24), "rmat16_f32": ("rmat_instance", 24),
-            "rmat16_i64": ("rmat_instance", 24), "planted1m": ("planted_instance", 200)}
+# and the training epochs over their clusters
+TRAINING = {"stencil27_160": ("stencil_instance", 24, 20), "stencil27_80": ("stencil_instance", 24, 20),
+            "laplacian64": ("laplacian_instance", 24, 20), "rmat16_f32": ("rmat_instance", 24, 20),
+            "rmat16_i64": ("rmat_instance", 24, 20), "planted1m": ("planted_instance", 200, 2)}
 
 WORKLOADS = {
-    "stencil27_160": ("C = A*A, A = 27-point stencil on a 160^3 grid (n = 4,096,000, nnz = 109,215,352), "
-                      "FP64 N(0,1) values, seeded random symmetric permutation; hierarchical clustering "
-                      "(jacc_th 0.3, max 8; merge as in 'clustering') + CSR_Cluster (masked layout)",
-                      lambda: synth.workload_stencil(5, nx=160)),
-    "stencil27_80": ("C = A*A, A = 27-point stencil on an 80^3 grid, FP64 N(0,1), seeded symmetric permutation; "
-                     "hierarchical clustering + CSR_Cluster",
-                     lambda: synth.workload_stencil(5, nx=80)),
-    "laplacian64": ("C = A*A, A = 2-D 5-point Laplacian 64x64 (FP64 4/-1), seeded symmetric permutation; "
-                    "hierarchical clustering + CSR_Cluster", lambda: synth.workload_laplacian(1)),
-    "rmat16_f32": ("C = A*A, A = R-MAT scale 16, edge factor 16, (0.57,0.19,0.19,0.05), duplicates merged, "
-                   "FP32 U(0,1); hierarchical clustering + CSR_Cluster", lambda: synth.workload_rmat("f32", 2)),
-    "rmat16_i64": ("C = A*A, A = R-MAT scale 16 as above, int64 U{1..3}; hierarchical clustering + CSR_Cluster",
-                   lambda: synth.workload_rmat("i64", 2)),
-    "batched256": ("256 independent products A_i*A_i: n_i log-uniform in [1e3, 2e5], row lengths floor of a "
-                   "power law (pdf ~ x^-2.1, mean 12, max 2000), uniform columns, FP64 N(0,1); packed "
-                   "block-diagonally, one launch sequence captured in one CUDA graph, autotuned", None),
-    "tallskinny_rmat18": ("C = A*B, A = R-MAT scale 18 graph (edge factor 16, (0.57,0.19,0.19,0.05), unit FP64 "
-                          "weights), B = BFS frontiers at distance 2 from 512 seeded sources valued by shortest-path "
-                          "counts (square x tall-skinny, the forward sweep of betweenness centrality); hierarchical "
-                          "clustering of A + CSR_Cluster", lambda: synth.workload_tallskinny(6)),
-    "planted1m": ("C = A*A, A = planted groups of 8 rows (n = 1,000,000, 11 of 16 shared columns + 5 random), "
-                  "FP64, seeded symmetric permutation; hierarchical clustering + CSR_Cluster",
-                  lambda: synth.workload_planted(4000)),
+    "stencil27_160": "C = A*A, A = 27-point stencil on a 160^3 grid (n = 4,096,000, nnz = 109,215,352), FP64 N(0,1) "
+                     "values, seeded random symmetric permutation; hierarchical clustering (jacc_th 0.3, max 8, "
+                     "round-parallel merge) + CSR_Cluster (masked layout)",
+    "stencil27_80": "C = A*A, A = 27-point stencil on an 80^3 grid, FP64 N(0,1), seeded symmetric permutation; "
+                    "hierarchical clustering + CSR_Cluster",
+    "laplacian64": "C = A*A, A = 2-D 5-point Laplacian 64x64 (FP64 4/-1), seeded symmetric permutation; "
+                   "hierarchical clustering + CSR_Cluster",
+    "rmat16_f32": "C = A*A, A = R-MAT scale 16, edge factor 16, (0.57,0.19,0.19,0.05), duplicates merged, "
+                  "FP32 U(0,1); hierarchical clustering + CSR_Cluster",
+    "rmat16_i64": "C = A*A, A = R-MAT scale 16 as above, int64 U{1..3}; hierarchical clustering + CSR_Cluster",
+    "batched256": "256 independent products A_i*A_i: n_i log-uniform in [1e3, 2e5], row lengths floor of a "
+                  "power law (pdf ~ x^-2.1, mean 12, max 2000), uniform columns, FP64 N(0,1); packed "
+                  "block-diagonally, one launch sequence captured in one CUDA graph, autotuned",
+    "tallskinny_rmat18": "C = A*B, A = R-MAT scale 18 graph (edge factor 16, (0.57,0.19,0.19,0.05), unit FP64 "
+                         "weights), B = BFS frontiers at distance 2 from 512 seeded sources valued by shortest-path "
+                         "counts (square x tall-skinny, the forward sweep of betweenness centrality); hierarchical "
+                         "clustering of A + CSR_Cluster",
+    "planted1m": "C = A*A, A = planted groups of 8 rows (n = 1,000,000, 11 of 16 shared columns + 5 random), "
+                 "FP64, seeded symmetric permutation; hierarchical clustering + CSR_Cluster",
 }
+# the other configurations measured beside the headline, in the order of their definitions
+CONFIGS = ("laplacian64", "rmat16_f32", "rmat16_i64", "batched256", "planted1m")
+
+
+# ---------------------------------------------------------------------------
+# input generation (host, numpy), in a spawn pool started before any CUDA call
+# ---------------------------------------------------------------------------
+def make_workload(name: str, batch: int = 256):
+    """(A, B) of a workload; for the batch, the list of its matrices."""
+    if name == "stencil27_160":
+        A = synth.workload_stencil(5, nx=160)
+    elif name == "stencil27_80":
+        A = synth.workload_stencil(5, nx=80)
+    elif name == "laplacian64":
+        A = synth.workload_laplacian(1)
+    elif name == "rmat16_f32":
+        A = synth.workload_rmat("f32", 2)
+    elif name == "rmat16_i64":
+        A = synth.workload_rmat("i64", 2)
+    elif name == "planted1m":
+        A = synth.workload_planted(4000)
+    elif name == "tallskinny_rmat18":
+        return synth.workload_tallskinny(6)
+    else:
+        raise ValueError(name)
+    return A, A
+
+
+def _task(t):
+    kind = t[0]
+    if kind == "workload":
+        return make_workload(t[1])
+    if kind == "powerlaw":
+        return synth.powerlaw_matrix(t[1])
+    from paper_2507_21253_gb300 import learned   # training instance generators (host only)
+    return getattr(learned, t[1])(t[2])
+
+
+def generate(tasks, procs: int):
+    """Results of the generation tasks, in order (a spawn pool: no CUDA state is forked)."""
+    if procs <= 1 or len(tasks) <= 1:
+        return [_task(t) for t in tasks]
+    big = [i for i, t in enumerate(tasks) if t[0] == "workload"]
+    order = big + [i for i in range(len(tasks)) if i not in big]    # long tasks first
+    with mp.get_context("spawn").Pool(min(procs, len(tasks))) as pool:
+        res = pool.map(_task, [tasks[i] for i in order], chunksize=1)
+    out = [None] * len(tasks)
+    for i, r in zip(order, res):
+        out[i] = r
+    return out
 
 
 def parse():
@@ -75,22 +138,22 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="stencil27_160", choices=sorted(WORKLOADS))
+    ap.add_argument("--configs", default=",".join(CONFIGS),
+                    help="other workloads measured beside the headline (comma list; empty: none)")
+    ap.add_argument("--config-steps", type=int, default=5, help="timed steps of each other workload")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-chunks", type=int, default=0,
-                    help="e2e numeric call: 0 = kernels store C straight into pinned host memory; k > 0 = k cluster "
-                         "ranges, each followed by a copy of the rows it finished; -1 = numeric, then one copy of C")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--clustering", default="parallel", choices=["parallel", "serial"],
-                    help="merge of the hierarchical clustering: round-parallel on the GPU (default) or the serial heap")
-    ap.add_argument("--no-alt-clustering", action="store_true", help="skip timing the other merge")
-    ap.add_argument("--epochs", type=int, default=20, help="predictor training epochs")
+    ap.add_argument("--no-alt-clustering", action="store_true", help="skip timing the serial merge's clusters")
+    ap.add_argument("--epochs", type=int, default=0, help="predictor training epochs (0: the workload's default)")
     ap.add_argument("--margin", type=float, default=1.05, help="capacity margin over the predicted output columns")
     ap.add_argument("--fused-fma", type=int, default=0, help="FP64: accumulate with fused multiply-add")
     ap.add_argument("--cluster-load", type=int, default=0, help="numeric cluster-table fill limit, percent (0: default)")
     ap.add_argument("--cluster-kernel", type=int, default=0,
                     help="numeric cluster kernel: 0 warp groups (default), 1 warp per cluster where it fits")
+    ap.add_argument("--max-warps", type=int, default=0, help="warps per cluster group / row CTA (0: default)")
     ap.add_argument("--batch", type=int, default=256, help="products in the batched workload")
+    ap.add_argument("--gen-procs", type=int, default=0, help="input generation processes (0: host cores)")
     return ap.parse_args()
 
 
@@ -117,6 +180,22 @@ def flops_of(A, B) -> int:
 
 def csr_bytes(M) -> int:
     return 8 * (M.nrows + 1) + M.nnz * (4 + M.val.itemsize)
+
+
+L2_BYTES = 129 * 2**20
+
+
+def l2_note(in_bytes: int) -> str:
+    if in_bytes < 2 * L2_BYTES:
+        return f"inputs {in_bytes / 1e6:.0f} MB < 2x L2 (129 MB): a 258 MB buffer is written before each timed step"
+    return f"inputs {in_bytes / 1e9:.2f} GB > 2x L2 (129 MB): no flush"
+
+
+def workload_config(name: str, A, B) -> dict:
+    """The `config` object of a JSON line: the same keys and values in both arms."""
+    in_bytes = csr_bytes(A) + (0 if B is A else csr_bytes(B))
+    return {"workload": WORKLOADS[name], "n": int(A.nrows), "nnz_A": int(A.nnz), "flops": flops_of(A, B),
+            "l2": l2_note(in_bytes), "parallelism": "one whole product per rank (replicas)"}
 
 
 # ---------------------------------------------------------------------------
@@ -177,12 +256,6 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample of rows)
 # ---------------------------------------------------------------------------
-def operands(make):
-    """(A, B) of a workload: generators return A (for C = A*A) or the pair."""
-    x = make()
-    return x if isinstance(x, tuple) else (x, x)
-
-
 def row_flops(A, B=None) -> np.ndarray:
     """Multiply-adds of each row of A*B (sum over a_ik of nnz(B_k))."""
     B = A if B is None else B
@@ -191,9 +264,10 @@ def row_flops(A, B=None) -> np.ndarray:
     return cs[A.row_ptr[1:]] - cs[A.row_ptr[:-1]]
 
 
-def oracle_sample_rate(A, target_s: float, seed: int = 9, rf=None, B=None):
-    """GFLOP/s of the CPU oracle (all host cores, rows over OpenMP threads) on a
-    seeded random row sample sized to take about target_s seconds."""
+def oracle_sample(A, target_s: float, seed: int = 9, rf=None, B=None):
+    """The CPU oracle (all host cores, rows over OpenMP threads) on a seeded random
+    row sample sized to take about target_s seconds: (GFLOP/s, threads, rows,
+    seconds of the timed sample)."""
     from oracle import gustavson as og
     og.build()
     threads = os.cpu_count() or 1
@@ -235,90 +309,149 @@ def numeric_sources_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profiles(workload: str, clustering: str):
-    """Per-launch DRAM bytes of the numeric phase from the ncu summary under profiles/,
-    or None when the summary has no figure for the workload and clustering or the
-    kernels changed since."""
+def traffic_from_profiles(workload: str):
+    """Per-launch DRAM bytes of the numeric phase from the ncu summary under profiles/
+    and how they were taken, or (None, None) when the summary has no figure for the
+    workload or the kernels changed since."""
     p = os.path.join(ROOT, "profiles", "traffic_cluster_numeric_stencil27.md")
     if not os.path.exists(p):
-        return None
-    digest, value = None, None
+        return None, None
+    digest, value, how = None, None, None
     with open(p) as fh:
         for line in fh:
             m = re.match(r"\s*sources digest:\s*(\w+)", line)
             if m:
                 digest = m.group(1)
-            m = re.match(r"\s*traffic per launch, %s, %s merge:\s*([0-9]+)" % (re.escape(workload), clustering),
-                         line)
+            m = re.match(r"\s*traffic per launch, %s:\s*([0-9]+)\s*\((.*)\)" % re.escape(workload), line)
             if m:
-                value = int(m.group(1))
+                value, how = int(m.group(1)), m.group(2)
     if value is None or digest != numeric_sources_digest():
-        return None
-    return value
+        return None, None
+    return value, how
 
 
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle on the host cores
 # ---------------------------------------------------------------------------
 def run_reference(args, rank: int):
     if rank != 0:
         return
-    desc, make = WORKLOADS[args.workload]
-    if make is None:   # the batch as one block-diagonal matrix (same products, same rows)
+    if args.workload == "batched256":   # the batch as one block-diagonal matrix (same products, same rows)
         A = synth.block_diag([synth.powerlaw_matrix(3000 + i) for i in range(args.batch)])
         B = A
+        cfg = {"workload": WORKLOADS["batched256"], "products": args.batch, "rows": int(A.nrows),
+               "nnz_A": int(A.nnz), "flops": flops_of(A, B), "l2": "inputs larger than L2; no flush",
+               "parallelism": "one whole product per rank (replicas)"}
     else:
-        A, B = operands(make)
+        A, B = make_workload(args.workload)
+        cfg = workload_config(args.workload, A, B)
     flops = flops_of(A, B)
-    steps = []
-    per_step_s = 8.0
     rf = row_flops(A, B)
-    cores = os.cpu_count() or 1
-    sample_rows = 0
+    rates, secs, sample_rows, cores = [], [], 0, os.cpu_count() or 1
+    per_step_s = 3.0
     for s in range(args.warmup + args.steps):
-        gf, cores, sample_rows, dt = oracle_sample_rate(A, per_step_s if s >= args.warmup else 1.0, seed=100 + s,
-                                                        rf=rf, B=B)
+        gf, cores, sample_rows, dt = oracle_sample(A, per_step_s if s >= args.warmup else 0.5, seed=100 + s, rf=rf,
+                                                   B=B)
         if s >= args.warmup:
-            steps.append(gf)
-    value = float(np.mean(steps))
-    ms_per_step = 2.0 * flops / (value * 1e9) * 1e3
+            rates.append(gf)
+            secs.append(dt)
+    value = float(np.mean(rates))
     out = {"metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "impl": "reference", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": desc, "n": int(A.nrows), "nnz_A": int(A.nnz), "flops": flops,
-                      "parallelism": "host cores"},
+           "steps": args.steps, "warmup": args.warmup,
+           # one step = the oracle on a bounded random row sample of the product (the time actually spent)
+           "ms_per_step": round(1e3 * float(np.mean(secs)), 3),
+           "full_product_ms_extrapolated": round(2.0 * flops / (value * 1e9) * 1e3, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": A.val.dtype.name.replace("float", "f").replace("int", "i"), "data": "synthetic",
+           "config": cfg,
            "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-                            "sample": f"{sample_rows} random rows of C per step (serial std::map Gustavson per row, "
-                                      f"rows spread over {cores} OpenMP threads); rate scaled to the whole product"},
+                            "sample": f"each step {sample_rows} seeded random rows of C (about {per_step_s:.0f} s; "
+                                      f"serial std::map Gustavson per row, rows over {cores} OpenMP threads); "
+                                      f"GFLOP/s = 2 x the sampled rows' multiply-adds / time"},
            "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def run_ours(args, rank: int, world: int, local_rank: int):
-    import torch
-    import torch.distributed as dist
-    from paper_2507_21253_gb300 import build as sgc_build
-    sgc_build.build()
-    from paper_2507_21253_gb300 import sgc
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+class Ctx:
+    """Per-process GPU context of the measurements."""
 
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    desc, make = WORKLOADS[args.workload]
-    A, B = operands(make)
-    square = B is A
-    flops = flops_of(A, B)
-    Ad = sgc.DeviceCsr.from_host(A, dev)
-    Bd = Ad if square else sgc.DeviceCsr.from_host(B, dev)
-    torch.cuda.synchronize()
+    def __init__(self, args, world, rank, dev):
+        import torch
+        from paper_2507_21253_gb300 import sgc
+        self.args, self.world, self.rank, self.dev = args, world, rank, dev
+        self.torch, self.sgc = torch, sgc
+        self.stream = torch.cuda.current_stream()
+        self.flush_buf = None
 
-    def barrier():
-        if world > 1:
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
             dist.barrier()
 
-    # ---- preprocessing: hierarchical clustering + CSR_Cluster build ----------
-    parallel = args.clustering == "parallel"
-    hc_main = sgc.hcluster_reorder_parallel if parallel else sgc.hcluster_reorder
-    hc_alt = sgc.hcluster_reorder if parallel else sgc.hcluster_reorder_parallel
+    def flush(self):
+        if self.flush_buf is not None:
+            self.flush_buf.zero_()
+
+    def set_flush(self, in_bytes: int):
+        torch = self.torch
+        self.flush_buf = (torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=self.dev)
+                          if in_bytes < 2 * L2_BYTES else None)
+
+    def timed(self, fns, steps: int):
+        """Per-step times (ms) of each function in fns, run back to back, CUDA events on the stream."""
+        torch = self.torch
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)] for _ in range(steps)]
+        for e in ev:
+            self.flush()
+            e[0].record(self.stream)
+            for i, f in enumerate(fns):
+                f()
+                e[i + 1].record(self.stream)
+        torch.cuda.synchronize()
+        return [[e[i].elapsed_time(e[i + 1]) for e in ev] for i in range(len(fns))]
+
+
+def cluster_format_bytes(nrows: int, ncl: int, nucols: int, nvals: int, val_bytes: int) -> int:
+    """Bytes of CSR_Cluster: cluster_ptr, ucol_ptr, val_ptr (int64), perm, ucol, mask, value slots."""
+    return 3 * 8 * (ncl + 1) + 4 * nrows + 8 * nucols + val_bytes * nvals
+
+
+def memory_overhead(cx: Ctx, Ad, A, perm_hc, cptr_hc) -> dict:
+    """bytes(CSR_Cluster) / bytes(CSR) for hierarchical, fixed-length and variable-length
+    clusters, padded (the paper's placeholders) and masked layouts (Sec. 4.5)."""
+    sgc = cx.sgc
+    srcs = {"hierarchical": (perm_hc, cptr_hc), "fixed8": sgc.cluster_fixed_length(A.nrows, 8, cx.dev),
+            "variable": sgc.cluster_variable_length(Ad, sgc.JACC_TH, sgc.MAX_CLUSTER)}
+    out = {}
+    for how, (perm, cptr) in srcs.items():
+        ncl = int(cptr.numel()) - 1
+        row = {}
+        for lname, lay in (("padded", sgc.LAYOUT_PADDED), ("masked", sgc.LAYOUT_MASKED)):
+            _, _, nu, nv = sgc.csr_cluster_build_count(Ad, perm, cptr, lay)
+            row[lname] = round(cluster_format_bytes(A.nrows, ncl, nu, nv, A.val.itemsize) / csr_bytes(A), 4)
+        row["nclusters"] = ncl
+        out[how] = row
+    return out
+
+
+def measure_product(cx: Ctx, name: str, A, B, train_mats, steps: int, warmup: int, headline: bool) -> dict:
+    """Clustered+learned, clustered exact and row-wise C = A*B of one workload."""
+    torch, sgc, args, world = cx.torch, cx.sgc, cx.args, cx.world
+    square = B is A
+    flops = flops_of(A, B)
+    Ad = sgc.DeviceCsr.from_host(A, cx.dev)
+    Bd = Ad if square else sgc.DeviceCsr.from_host(B, cx.dev)
+    cx.set_flush(csr_bytes(A) + (0 if square else csr_bytes(B)))
+    torch.cuda.synchronize()
+    res = {"workload": WORKLOADS[name], "n": int(A.nrows), "nnz_A": int(A.nnz), "flops": flops,
+           "dtype": A.val.dtype.name.replace("float", "f").replace("int", "i"), "steps": steps, "warmup": warmup}
+
+    # ---- preprocessing: hierarchical clustering (round-parallel merge) + CSR_Cluster build
     t0 = time.perf_counter()
-    perm, cptr = hc_main(Ad, sgc.JACC_TH, sgc.MAX_CLUSTER)
+    perm, cptr = sgc.hcluster_reorder_parallel(Ad, sgc.JACC_TH, sgc.MAX_CLUSTER)
     torch.cuda.synchronize()
     t_hc = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -327,80 +460,61 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     t_build = time.perf_counter() - t0
 
     opt = sgc.options(fused_fma=args.fused_fma, cluster_load_pct=args.cluster_load,
-                      cluster_kernel=args.cluster_kernel)
-    ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Bd, opt), dev)
+                      cluster_kernel=args.cluster_kernel, max_warps=args.max_warps)
+    ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Bd, opt), cx.dev)
     rp, nnz = sgc.spgemm_symbolic(Acl, Bd, ws, opt)
     C = sgc.spgemm_numeric(Acl, Bd, rp, nnz, ws, opt)
     sgc.workspace_status(ws)
-    stream = torch.cuda.current_stream()
-
-    # inputs below twice the L2 (129 MB): overwrite a 258 MB buffer before each timed step
-    l2_bytes = 129 * 2**20
-    in_bytes = csr_bytes(A) + (0 if square else csr_bytes(B))
-    flush_buf = torch.empty(2 * l2_bytes // 4, dtype=torch.float32, device=dev) if in_bytes < 2 * l2_bytes else None
-
-    def flush():
-        if flush_buf is not None:
-            flush_buf.zero_()
-
-    l2_note = (f"inputs {in_bytes / 1e6:.0f} MB < 2x L2: a 258 MB buffer is written before each timed step"
-               if flush_buf is not None else f"inputs {in_bytes / 1e9:.2f} GB > 2x L2 (129 MB): no flush")
-
-    def timed_loop(sym_fn, num_fn, steps):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        for e0, e1, e2 in ev:
-            flush()
-            e0.record(stream)
-            sym_fn()
-            e1.record(stream)
-            num_fn()
-            e2.record(stream)
-        torch.cuda.synchronize()
-        sym = [a.elapsed_time(b) for a, b, _ in ev]
-        num = [b.elapsed_time(c) for _, b, c in ev]
-        return sym, num
-
     sym_c = lambda: sgc.spgemm_symbolic(Acl, Bd, ws, opt, c_row_ptr=rp, sync=False)  # noqa: E731
     num_c = lambda: sgc.spgemm_numeric(Acl, Bd, rp, nnz, ws, opt, C=C)  # noqa: E731
-    timed_loop(sym_c, num_c, args.warmup)
-    barrier()
+    cx.timed([sym_c, num_c], warmup)
+    cx.barrier()
     torch.cuda.synchronize()
     l0 = sgc.kernel_launches()
-    with ClockSampler(local_rank) as clk:
-        t_wall = time.perf_counter()
-        sym_ms, num_ms = timed_loop(sym_c, num_c, args.steps)
-        t_wall = time.perf_counter() - t_wall
-    barrier()
-    launches = sgc.kernel_launches() - l0
+    with ClockSampler(cx.dev.index or 0) as clk_exact:
+        sym_ms, num_ms = cx.timed([sym_c, num_c], steps)
+    cx.barrier()
+    exact_launches = sgc.kernel_launches() - l0
     sgc.workspace_status(ws)
-    step_ms = max_over_ranks(float(np.mean([a + b for a, b in zip(sym_ms, num_ms)])), world, dev)
-    exact_value = job_gflops(flops, world, step_ms)
-
-    # ---- plain row-wise method, same GPU ---------------------------------------
-    wsr = sgc.Workspace(sgc.spgemm_rowwise_workspace_size(Ad, Bd, opt), dev)
-    rpr, nnzr = sgc.spgemm_rowwise_symbolic(Ad, Bd, wsr, opt)
+    step_ms = max_over_ranks(float(np.mean([a + b for a, b in zip(sym_ms, num_ms)])), world, cx.dev)
+    res["nnz_C"] = int(nnz)
+    res["nclusters"] = int(Acl.nclusters)
+    res["one_row_clusters"] = int((torch.diff(cptr) == 1).sum().item())
+    res["clustered_exact"] = {"ms_per_step": round(step_ms, 4), "gflops": round(job_gflops(flops, world, step_ms), 3),
+                              "phases_ms": {"symbolic": round(float(np.mean(sym_ms)), 4),
+                                            "numeric": round(float(np.mean(num_ms)), 4)}}
     del C
     torch.cuda.empty_cache()
+
+    # ---- plain row-wise method, same GPU
+    wsr = sgc.Workspace(sgc.spgemm_rowwise_workspace_size(Ad, Bd, opt), cx.dev)
+    rpr, nnzr = sgc.spgemm_rowwise_symbolic(Ad, Bd, wsr, opt)
     Cr = sgc.spgemm_rowwise_numeric(Ad, Bd, rpr, nnzr, wsr, opt)
     sgc.workspace_status(wsr)
     sym_r = lambda: sgc.spgemm_rowwise_symbolic(Ad, Bd, wsr, opt, c_row_ptr=rpr, sync=False)  # noqa: E731
     num_r = lambda: sgc.spgemm_rowwise_numeric(Ad, Bd, rpr, nnzr, wsr, opt, C=Cr)  # noqa: E731
-    timed_loop(sym_r, num_r, args.warmup)
-    rsym, rnum = timed_loop(sym_r, num_r, args.steps)
+    cx.timed([sym_r, num_r], warmup)
+    rsym, rnum = cx.timed([sym_r, num_r], steps)
     sgc.workspace_status(wsr)
-    row_ms = max_over_ranks(float(np.mean([a + b for a, b in zip(rsym, rnum)])), world, dev)
-    del Cr
+    row_ms = max_over_ranks(float(np.mean([a + b for a, b in zip(rsym, rnum)])), world, cx.dev)
+    res["rowwise"] = {"ms_per_step": round(row_ms, 4), "gflops": round(job_gflops(flops, world, row_ms), 3),
+                      "phases_ms": {"symbolic": round(float(np.mean(rsym)), 4),
+                                    "numeric": round(float(np.mean(rnum)), 4)}}
+    del Cr, wsr
     torch.cuda.empty_cache()
 
-    # ---- clustered + learned: predictor trained on the GPU, symbolic-free path ---
-    learned_out = None
-    if not args.no_learned and args.workload in TRAINING:
+    # ---- clustered + learned: predictor trained on the GPU, symbolic-free path
+    learned = None
+    launches = None
+    clk = None
+    params = None
+    if not args.no_learned and train_mats:
         from paper_2507_21253_gb300 import learned as lrn
-        gen_name, ntrain = TRAINING[args.workload]
+        gen_name, _, epochs = TRAINING[name]
+        epochs = args.epochs or epochs
+        info = {}
         t0 = time.perf_counter()
-        params, tloss = lrn.train(getattr(lrn, gen_name), range(1000, 1000 + ntrain), epochs=args.epochs,
-                                  device=dev, parallel=parallel)
+        params, tloss = lrn.train_on(train_mats, epochs=epochs, device=cx.dev, parallel=True, info=info)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         Lrn = sgc.LearnedSpgemm(Acl, Bd, params=params, margin=args.margin, opt=opt)
@@ -413,61 +527,40 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             Lrn.phase1()
             Lrn.phase2(C=Cl)
 
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             learned_step()
         torch.cuda.synchronize()
-        lev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        barrier()
+        lev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        cx.barrier()
         torch.cuda.synchronize()
         l0 = sgc.kernel_launches()
-        with ClockSampler(local_rank) as clk:      # the headline's timed region
+        with ClockSampler(cx.dev.index or 0) as clk:      # the headline's timed region
             for e0, e1 in lev:
-                flush()
-                e0.record(stream)
+                cx.flush()
+                e0.record(cx.stream)
                 learned_step()
-                e1.record(stream)
+                e1.record(cx.stream)
             torch.cuda.synchronize()
-        barrier()
+        cx.barrier()
         launches = sgc.kernel_launches() - l0
         sgc.workspace_status(Lrn.ws)
-        l_ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in lev])), world, dev)
-        learned_out = {"value": round(job_gflops(flops, world, l_ms), 3), "unit": "GFLOP/s",
-                       "ms_per_step": round(l_ms, 4), "overflow_clusters": int(Lrn.n_overflow),
-                       "slab_over_nnzC": round(Lrn.slab_elems / max(nnz, 1), 4),
-                       "margin": args.margin,
-                       "train": {"instances": ntrain, "generator": gen_name, "epochs": args.epochs,
-                                 "seconds": round(t_train, 2),
-                                 "final_loss": round(float(tloss[-50:].mean().item()), 5)},
-                       "step": "plan (features, MLP, capacities) + slab pass + exact fallback + compaction"}
+        l_ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in lev])), world, cx.dev)
+        learned = {"ms_per_step": round(l_ms, 4), "gflops": round(job_gflops(flops, world, l_ms), 3),
+                   "overflow_clusters": int(Lrn.n_overflow), "slab_over_nnzC": round(Lrn.slab_elems / max(nnz, 1), 4),
+                   "margin": args.margin,
+                   "train": {"instances": len(train_mats), "generator": gen_name, "epochs": epochs,
+                             "samples": info.get("samples"), "steps": info.get("steps"),
+                             "seconds": round(t_train, 2),
+                             "final_loss": round(float(tloss[-50:].mean().item()), 5)},
+                   "step": "plan (features, MLP, capacities) + slab pass + exact fallback + compaction"}
         del Cl, Lrn
         torch.cuda.empty_cache()
+    res["clustered_learned"] = learned
+    head_ms = learned["ms_per_step"] if learned else step_ms
+    res["speedup_vs_rowwise"] = {"learned": round(row_ms / learned["ms_per_step"], 4) if learned else None,
+                                 "exact": round(row_ms / step_ms, 4)}
 
-    # ---- the other merge of the hierarchical clustering: its preprocessing time and exact step
-    par = None
-    if not args.no_alt_clustering:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        perm_p, cptr_p = hc_alt(Ad, sgc.JACC_TH, sgc.MAX_CLUSTER)
-        torch.cuda.synchronize()
-        t_hcp = time.perf_counter() - t0
-        Acl_p = sgc.csr_cluster_build(Ad, perm_p, cptr_p, sgc.LAYOUT_MASKED)
-        ws_p = sgc.Workspace(sgc.spgemm_workspace_size(Acl_p, Bd, opt), dev)
-        rp_p, nnz_p = sgc.spgemm_symbolic(Acl_p, Bd, ws_p, opt)
-        C_p = sgc.spgemm_numeric(Acl_p, Bd, rp_p, nnz_p, ws_p, opt)
-        sym_p = lambda: sgc.spgemm_symbolic(Acl_p, Bd, ws_p, opt, c_row_ptr=rp_p, sync=False)  # noqa: E731
-        num_p = lambda: sgc.spgemm_numeric(Acl_p, Bd, rp_p, nnz_p, ws_p, opt, C=C_p)  # noqa: E731
-        timed_loop(sym_p, num_p, args.warmup)
-        psym, pnum = timed_loop(sym_p, num_p, args.steps)
-        sgc.workspace_status(ws_p)
-        p_ms = max_over_ranks(float(np.mean([a + b for a, b in zip(psym, pnum)])), world, dev)
-        par = {"clustering": ("serial heap merge (Algorithm 3)" if parallel else "round-parallel merge"),
-               "hcluster_s": round(t_hcp, 3), "nclusters": int(Acl_p.nclusters),
-               "in_spgemm_units": round(t_hcp / (p_ms * 1e-3), 1),
-               "clustered_exact": {"value": round(job_gflops(flops, world, p_ms), 3), "ms_per_step": round(p_ms, 4)}}
-        del C_p, Acl_p, ws_p
-        torch.cuda.empty_cache()
-
-    # ---- algorithmic bytes ----------------------------------------------------
+    # ---- algorithmic bytes of the numeric launch and its roofline
     ucol = Acl.ucol.cpu().numpy()
     staged = int(np.sum(np.diff(B.row_ptr)[ucol]))      # sum over clusters of the B elements staged
     ncl = Acl.nclusters
@@ -478,172 +571,55 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     num_avg = float(np.mean(num_ms))
     peak, peak_kind = measured_peaks()
     achieved = num_bytes / (num_avg * 1e-3) / 1e9
-    traffic = traffic_from_profiles(args.workload, args.clustering)
     compulsory = csr_bytes(A) + csr_bytes(B) + c_bytes
-
-    # ---- end to end through the public API, host buffers -----------------------
-    e2e = None
-    if not args.no_e2e:
-        pin = lambda x: torch.from_numpy(x).pin_memory()  # noqa: E731
-        h_rp, h_col, h_val = pin(A.row_ptr), pin(A.col), pin(A.val)
-        if not square:
-            h_brp, h_bcol, h_bval = pin(B.row_ptr), pin(B.col), pin(B.val)
-        e_steps = max(1, min(args.steps, 3))
-        h_out = None
-        times, stages = [], []
-        chunks = args.e2e_chunks
-        for s in range(e_steps + 1):
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            ev[0].record(stream)
-            Ad.row_ptr.copy_(h_rp, non_blocking=True)
-            Ad.col.copy_(h_col, non_blocking=True)
-            Ad.val.copy_(h_val, non_blocking=True)
-            if not square:
-                Bd.row_ptr.copy_(h_brp, non_blocking=True)
-                Bd.col.copy_(h_bcol, non_blocking=True)
-                Bd.val.copy_(h_bval, non_blocking=True)
-            ev[1].record(stream)
-            Acl2 = sgc.csr_cluster_build(Ad, perm, cptr, sgc.LAYOUT_MASKED)
-            ev[2].record(stream)
-            ws2 = sgc.Workspace(sgc.spgemm_workspace_size(Acl2, Bd, opt))
-            rp2, nnz2 = sgc.spgemm_symbolic(Acl2, Bd, ws2, opt)
-            ev[3].record(stream)
-            if h_out is None:
-                h_out = (torch.empty(A.nrows + 1, dtype=torch.int64, pin_memory=True),
-                         torch.empty(nnz2, dtype=torch.int32, pin_memory=True),
-                         torch.empty(nnz2, dtype=Ad.val.dtype, pin_memory=True))
-            if chunks >= 0:  # numeric with C streamed to the host buffers while it computes
-                C2 = sgc.spgemm_numeric_to_host(Acl2, Bd, rp2, nnz2, ws2, h_out[1], h_out[2], h_out[0],
-                                                nchunks=chunks, opt=opt)
-                ev[4].record(stream)
-            else:            # numeric, then one copy of C
-                C2 = sgc.spgemm_numeric(Acl2, Bd, rp2, nnz2, ws2, opt)
-                ev[4].record(stream)
-                h_out[0].copy_(C2.row_ptr, non_blocking=True)
-                h_out[1].copy_(C2.col, non_blocking=True)
-                h_out[2].copy_(C2.val, non_blocking=True)
-            ev[5].record(stream)
-            sgc.workspace_status(ws2)
-            torch.cuda.synchronize()
-            if s > 0:
-                times.append(time.perf_counter() - t)
-                stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(5)])
-            del C2, Acl2, ws2, rp2
-        e_s = max_over_ranks(float(np.mean(times)), world, dev)
-        h2d = int(h_rp.numel() * 8 + h_col.numel() * 4 + h_val.numel() * h_val.element_size())
-        if not square:
-            h2d += int(h_brp.numel() * 8 + h_bcol.numel() * 4 + h_bval.numel() * h_bval.element_size())
-        d2h = int(h_out[0].numel() * 8 + h_out[1].numel() * 4 + h_out[2].numel() * h_out[2].element_size())
-        st_ms = np.mean(np.array(stages), axis=0)
-        if chunks >= 0:
-            stage_ms = {"h2d": round(float(st_ms[0]), 2), "csr_cluster_build": round(float(st_ms[1]), 2),
-                        "symbolic": round(float(st_ms[2]), 2),
-                        "numeric_with_d2h_overlapped": round(float(st_ms[3] + st_ms[4]), 2)}
-            how = ("the numeric kernels store C straight into pinned host memory" if chunks == 0 else
-                   f"{chunks} cluster ranges, C copied to pinned host memory as its rows become final")
-            what = (f"H2D of A (CSR) from pinned host memory, csr_cluster_build, spgemm_symbolic, "
-                    f"spgemm_numeric_to_host ({how})")
-        else:
-            stage_ms = {"h2d": round(float(st_ms[0]), 2), "csr_cluster_build": round(float(st_ms[1]), 2),
-                        "symbolic": round(float(st_ms[2]), 2), "numeric": round(float(st_ms[3]), 2),
-                        "d2h": round(float(st_ms[4]), 2)}
-            what = ("H2D of A (CSR) from pinned host memory, csr_cluster_build, spgemm_symbolic + "
-                    "spgemm_numeric, D2H of C (CSR) to pinned host memory")
-        e2e = {"value": round(job_gflops(flops, world, e_s * 1e3), 3), "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": round(e_s * 1e3, 2), "stages_ms": stage_ms, "step": what}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        gf, cores, nrows_s, dt = oracle_sample_rate(A, 12.0, B=B)
-        cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": f"{nrows_s} random rows of C ({dt:.1f} s; serial std::map Gustavson per row, rows "
-                         f"over {cores} OpenMP threads), rate scaled to GFLOP/s"}
-
-    if rank == 0:
-        clocks = clk.summary()
-        # headline: clustered + learned (the metric's method); exact clustered reported beside it
-        head_ms = learned_out["ms_per_step"] if learned_out else step_ms
-        value = job_gflops(flops, world, head_ms)
-        out = {
-            "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(head_ms, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": A.val.dtype.name.replace("float", "f").replace("int", "i"),
-            "data": "synthetic",
-            "config": {"workload": desc, "n": A.nrows, "nnz_A": A.nnz, "flops": flops, "nnz_C": nnz,
-                       "nclusters": ncl, "l2": l2_note,
-                       "parallelism": "replicas" if world > 1 else "1 GPU"},
-            "method": "clustered+learned" if learned_out else "clustered (exact symbolic + numeric)",
-            "clustered_exact": {"value": round(exact_value, 3), "unit": "GFLOP/s", "ms_per_step": round(step_ms, 4),
-                                "phases_ms": {"symbolic": round(float(np.mean(sym_ms)), 4),
-                                              "numeric": round(num_avg, 4)}},
-            "learned": learned_out,
-            "rowwise": {"value": round(job_gflops(flops, world, row_ms), 3), "unit": "GFLOP/s",
-                        "ms_per_step": round(row_ms, 4),
-                        "phases_ms": {"symbolic": round(float(np.mean(rsym)), 4),
-                                      "numeric": round(float(np.mean(rnum)), 4)}},
-            "speedup_vs_rowwise": round(row_ms / head_ms, 4),
-            "speedup_exact_vs_rowwise": round(row_ms / step_ms, 4),
-            "hbm": {"step_GBs": round((num_bytes + sym_bytes) / (step_ms * 1e-3) / 1e9, 2),
-                    "compulsory_bytes": compulsory,
-                    "compulsory_frac": round(compulsory / (step_ms * 1e-3) / (peak * 1e9), 4),
-                    "staged_B_elements": staged, "reuse_R": round(flops / max(staged, 1), 4)},
-            "roofline": {"bound": "hbm", "kernel": "cluster-wise numeric phase (spgemm_numeric)",
-                         "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                         "traffic": traffic, "algorithmic_bytes_per_launch": num_bytes},
-            "clustering": ("hierarchical, round-parallel merge on the GPU (jacc_th 0.3, max 8)" if parallel else
-                           "hierarchical, serial heap merge (Algorithm 3; jacc_th 0.3, max 8)"),
-            "alternative_clustering": par,
-            "preprocess": {"hcluster_s": round(t_hc, 3), "csr_cluster_build_s": round(t_build, 4),
-                           "in_spgemm_units": round((t_hc + t_build) / (step_ms * 1e-3), 1)},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
-            "timed_wall_s": round(t_wall, 3),
-        }
-        print(json.dumps(out), flush=True)
+    res["numeric_roofline"] = {"bound": "hbm", "achieved_GBs": round(achieved, 2), "peak_GBs": peak,
+                               "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                               "algorithmic_bytes_per_launch": int(num_bytes)}
+    res["hbm"] = {"step_GBs": round((num_bytes + sym_bytes) / (step_ms * 1e-3) / 1e9, 2),
+                  "compulsory_bytes": int(compulsory),
+                  "compulsory_frac": round(compulsory / (head_ms * 1e-3) / (peak * 1e9), 4),
+                  "staged_B_elements": staged, "reuse_R": round(flops / max(staged, 1), 4)}
+    res["preprocess"] = {"hcluster_s": round(t_hc, 3), "csr_cluster_build_s": round(t_build, 4),
+                         "in_steps": round((t_hc + t_build) / (head_ms * 1e-3), 1)}
+    res["csr_cluster_bytes_over_csr"] = memory_overhead(cx, Ad, A, perm, cptr)
+    res["_internal"] = {"Ad": Ad, "Bd": Bd, "perm": perm, "cptr": cptr, "opt": opt, "num_bytes": num_bytes,
+                        "params": params, "exact_launches": exact_launches, "clk_exact": clk_exact,
+                        "num_avg": num_avg, "launches": launches, "clk": clk, "head_ms": head_ms,
+                        "step_ms": step_ms, "row_ms": row_ms, "nnz": nnz, "square": square}
+    return res
 
 
-def run_batched(args, rank: int, world: int, local_rank: int):
-    """Batched products: autotuned CUDA-graph replay vs default graph vs one launch sequence per product."""
-    import torch
-    from paper_2507_21253_gb300 import build as sgc_build
-    sgc_build.build()
-    from paper_2507_21253_gb300 import autotune, sgc
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    t0 = time.perf_counter()
-    mats = [synth.powerlaw_matrix(3000 + i) for i in range(args.batch)]
-    t_gen = time.perf_counter() - t0
+def measure_batched(cx: Ctx, mats, steps: int, warmup: int) -> dict:
+    """Batched products: autotuned CUDA-graph replay vs default graph vs one launch
+    sequence per product, and the row-wise method on the packed batch."""
+    torch, sgc = cx.torch, cx.sgc
+    from paper_2507_21253_gb300 import autotune
     flops = sum(flops_of(A, A) for A in mats)
-    dm = [sgc.DeviceCsr.from_host(A, dev) for A in mats]
+    dm = [sgc.DeviceCsr.from_host(A, cx.dev) for A in mats]
     P, row_off, col_off = sgc.csr_batch_pack(dm)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = autotune.tune(P, reps=3)
+    res = autotune.tune(P, reps=2)
     t_tune = time.perf_counter() - t0
     best = res["best"]
     perm, cptr = autotune.cluster(P, best["clustering"])
     Acl = sgc.csr_cluster_build(P, perm, cptr, sgc.LAYOUT_MASKED)
     g = sgc.SpgemmGraph(Acl, P, autotune.options_of(best))
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         g.launch()
     g.stream.synchronize()
-    l0 = sgc.kernel_launches()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(local_rank) as clk:
-        for a, b in ev:
-            a.record(g.stream)
-            g.launch()
-            b.record(g.stream)
-        g.stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        a.record(g.stream)
+        g.launch()
+        b.record(g.stream)
+    g.stream.synchronize()
     ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     nnz = g.C.nnz
-    default = next(t for t in res["trials"] if t["clustering"] == "hc8" and t["staging"] == sgc.STAGING_BULK
-                   and t["load_pct"] == 75)
-    # one symbolic + numeric launch sequence per product (host sync for each product's nnz)
+    default = res["default"]
+    # one symbolic + numeric launch sequence per product
     per = []
-    hcs = [sgc.hcluster_reorder(d) for d in dm]
+    hcs = [sgc.hcluster_reorder_parallel(d) for d in dm]
     cls = [sgc.csr_cluster_build(d, pr, cp) for d, (pr, cp) in zip(dm, hcs)]
     wss = [sgc.Workspace(sgc.spgemm_workspace_size(c, d)) for c, d in zip(cls, dm)]
     outs = []
@@ -661,23 +637,261 @@ def run_batched(args, rank: int, world: int, local_rank: int):
         torch.cuda.synchronize()
         per.append(s0.elapsed_time(s1))
     per_ms = float(min(per))
-    if rank == 0:
-        gf = lambda t: round(world * 2.0 * flops / (t * 1e-3) / 1e9, 3)  # noqa: E731
-        out = {"metric": METRIC, "value": gf(ms), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-               "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": WORKLOADS["batched256"][0], "products": args.batch,
-                          "rows": int(P.nrows), "nnz_A": int(P.nnz), "flops": int(flops), "nnz_C": int(nnz),
-                          "l2": "inputs larger than L2; no flush", "parallelism": "1 GPU"},
-               "method": "batched cluster-wise, one CUDA graph (autotuned)",
-               "autotune": {"best": best, "seconds": round(t_tune, 2), "trials": len(res["trials"])},
-               "default_graph": {"value": gf(default["ms"]), "ms_per_step": default["ms"], "config": default},
-               "per_product_launches": {"value": gf(per_ms), "ms_per_step": round(per_ms, 4),
-                                        "launch_sequences": args.batch},
-               "speedup_vs_per_product": round(per_ms / ms, 3),
-               "gpu_launches": int(g.kernels_per_launch * args.steps), "clocks": clk.summary(),
-               "generation_s": round(t_gen, 1)}
+    del outs, wss, cls, hcs
+    # the row-wise method on the packed batch
+    wsr = sgc.Workspace(sgc.spgemm_rowwise_workspace_size(P, P), cx.dev)
+    rpr, nnzr = sgc.spgemm_rowwise_symbolic(P, P, wsr)
+    Cr = sgc.spgemm_rowwise_numeric(P, P, rpr, nnzr, wsr)
+    rsym, rnum = cx.timed([lambda: sgc.spgemm_rowwise_symbolic(P, P, wsr, c_row_ptr=rpr, sync=False),
+                           lambda: sgc.spgemm_rowwise_numeric(P, P, rpr, nnzr, wsr, C=Cr)], warmup + steps)
+    row_ms = float(np.mean([a + b for a, b in zip(rsym[warmup:], rnum[warmup:])]))
+    sgc.workspace_status(wsr)
+    del Cr, wsr, g
+    torch.cuda.empty_cache()
+    gf = lambda t: round(2.0 * flops / (t * 1e-3) / 1e9, 3)  # noqa: E731
+    return {"workload": WORKLOADS["batched256"], "products": len(mats), "rows": int(P.nrows), "nnz_A": int(P.nnz),
+            "flops": int(flops), "nnz_C": int(nnz), "dtype": "f64", "steps": steps, "warmup": warmup,
+            "clustered_graph": {"ms_per_step": round(ms, 4), "gflops": gf(ms),
+                                "method": "batched cluster-wise, one CUDA graph (autotuned)"},
+            "autotune": {"best": best, "seconds": round(t_tune, 2), "trials": len(res["trials"]),
+                         "space": res.get("space")},
+            "default_graph": ({"ms_per_step": default["ms"], "gflops": gf(default["ms"]), "config": default}
+                              if default else None),
+            "per_product_launches": {"ms_per_step": round(per_ms, 4), "gflops": gf(per_ms),
+                                     "launch_sequences": len(mats)},
+            "rowwise_packed": {"ms_per_step": round(row_ms, 4), "gflops": gf(row_ms)},
+            "speedup_vs_rowwise": round(row_ms / ms, 4), "speedup_vs_per_product": round(per_ms / ms, 3)}
+
+
+def fp64_floor(cx: Ctx, flops: int) -> dict:
+    """Measured FP64 operation rates and the arithmetic floor they put under the numeric phase."""
+    sgc = cx.sgc
+    r = {k: round(sgc.fp64_rate(op, 2000, cx.dev), 1) for op, k in ((0, "dmul_gops"), (1, "dadd_gops"),
+                                                                      (2, "dfma_gops"))}
+    r["numeric_floor_ms_separate"] = round(flops / (r["dmul_gops"] * 1e9) * 1e3 + flops / (r["dadd_gops"] * 1e9) * 1e3,
+                                           3)
+    r["numeric_floor_ms_fused"] = round(flops / (r["dfma_gops"] * 1e9) * 1e3, 3)
+    return r
+
+
+def e2e_learned(cx: Ctx, A, B, internal: dict, train_params, steps: int) -> dict:
+    """The headline method end to end through the public API: H2D of A from pinned host
+    memory, csr_cluster_build (clusters reused from preprocessing), learned plan, slab
+    pass, exact fallback and compaction with C stored into pinned host memory."""
+    torch, sgc, args = cx.torch, cx.sgc, cx.args
+    Ad, Bd, square = internal["Ad"], internal["Bd"], internal["square"]
+    opt = internal["opt"]
+    pin = lambda x: torch.from_numpy(x).pin_memory()  # noqa: E731
+    h_rp, h_col, h_val = pin(A.row_ptr), pin(A.col), pin(A.val)
+    h_out = None
+    times, stages = [], []
+    for s in range(steps + 1):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ev[0].record(cx.stream)
+        Ad.row_ptr.copy_(h_rp, non_blocking=True)
+        Ad.col.copy_(h_col, non_blocking=True)
+        Ad.val.copy_(h_val, non_blocking=True)
+        ev[1].record(cx.stream)
+        Acl2 = sgc.csr_cluster_build(Ad, internal["perm"], internal["cptr"], sgc.LAYOUT_MASKED)
+        ev[2].record(cx.stream)
+        L = sgc.LearnedSpgemm(Acl2, Bd, params=train_params, margin=args.margin, opt=opt)
+        L.phase1()
+        ev[3].record(cx.stream)
+        if h_out is None:
+            h_out = (torch.empty(A.nrows + 1, dtype=torch.int64, pin_memory=True),
+                     torch.empty(L.nnz, dtype=torch.int32, pin_memory=True),
+                     torch.empty(L.nnz, dtype=Ad.val.dtype, pin_memory=True))
+        h_out[0].copy_(L.c_row_ptr, non_blocking=True)
+        L.phase2_to_host(h_out[1], h_out[2])
+        ev[4].record(cx.stream)
+        ev[5].record(cx.stream)
+        sgc.workspace_status(L.ws)
+        torch.cuda.synchronize()
+        if s > 0:
+            times.append(time.perf_counter() - t)
+            stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+        del L, Acl2
+    e_s = max_over_ranks(float(np.mean(times)), cx.world, cx.dev)
+    h2d = int(h_rp.numel() * 8 + h_col.numel() * 4 + h_val.numel() * h_val.element_size())
+    d2h = int(h_out[0].numel() * 8 + h_out[1].numel() * 4 + h_out[2].numel() * h_out[2].element_size())
+    st = np.mean(np.array(stages), axis=0)
+    flops = flops_of(A, B)
+    return {"value": round(job_gflops(flops, cx.world, e_s * 1e3), 3), "unit": "GFLOP/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e_s * 1e3, 2),
+            "stages_ms": {"h2d": round(float(st[0]), 2), "csr_cluster_build": round(float(st[1]), 2),
+                          "learned_plan_and_slab_pass": round(float(st[2]), 2),
+                          "compaction_into_host_memory": round(float(st[3]), 2)},
+            "step": "H2D of A (CSR) from pinned host memory, csr_cluster_build, spgemm_learned_plan + _phase1, "
+                    "spgemm_learned_phase2 storing C into pinned host memory (row pointer copied beside it)"}
+
+
+def run_batched_headline(cx: Ctx, args, inputs: dict):
+    """`--workload batched256`: the batch alone, one JSON line."""
+    steps = args.steps
+    l0 = cx.sgc.kernel_launches()
+    with ClockSampler(cx.dev.index or 0) as clk:
+        r = measure_batched(cx, inputs["batched256"], steps, args.warmup)
+    if cx.rank == 0:
+        ms = r["clustered_graph"]["ms_per_step"]
+        out = {"metric": METRIC, "value": round(job_gflops(r["flops"], cx.world, ms), 3), "unit": "GFLOP/s",
+               "n_gpus": cx.world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": WORKLOADS["batched256"], "products": r["products"], "rows": r["rows"],
+                          "nnz_A": r["nnz_A"], "flops": r["flops"], "l2": "inputs larger than L2; no flush",
+                          "parallelism": "one whole product per rank (replicas)"},
+               "batched": r, "gpu_launches": int(cx.sgc.kernel_launches() - l0), "clocks": clk.summary(),
+               "launch_count_scope": "all library launches of the measurement (tuning included)"}
         print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank: int, world: int, local_rank: int, inputs: dict):
+    import torch
+    from paper_2507_21253_gb300 import build as sgc_build
+    sgc_build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    cx = Ctx(args, world, rank, dev)
+    sgc = cx.sgc
+    name = args.workload
+    if name == "batched256":
+        run_batched_headline(cx, args, inputs)
+        return
+    A, B = inputs[name]
+    train = inputs.get(("train", name))
+    flops = flops_of(A, B)
+    res = measure_product(cx, name, A, B, train, args.steps, args.warmup, headline=True)
+    it = res.pop("_internal")
+
+    # ---- the serial merge's clusters (Algorithm 3): preprocessing time and exact step
+    alt = None
+    if not args.no_alt_clustering:
+        Ad, Bd, opt = it["Ad"], it["Bd"], it["opt"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        perm_s, cptr_s = sgc.hcluster_reorder(Ad, sgc.JACC_TH, sgc.MAX_CLUSTER)
+        torch.cuda.synchronize()
+        t_hcs = time.perf_counter() - t0
+        Acl_s = sgc.csr_cluster_build(Ad, perm_s, cptr_s, sgc.LAYOUT_MASKED)
+        ws_s = sgc.Workspace(sgc.spgemm_workspace_size(Acl_s, Bd, opt), dev)
+        rp_s, nnz_s = sgc.spgemm_symbolic(Acl_s, Bd, ws_s, opt)
+        C_s = sgc.spgemm_numeric(Acl_s, Bd, rp_s, nnz_s, ws_s, opt)
+        f = [lambda: sgc.spgemm_symbolic(Acl_s, Bd, ws_s, opt, c_row_ptr=rp_s, sync=False),
+             lambda: sgc.spgemm_numeric(Acl_s, Bd, rp_s, nnz_s, ws_s, opt, C=C_s)]
+        cx.timed(f, args.warmup)
+        ssym, snum = cx.timed(f, args.steps)
+        sgc.workspace_status(ws_s)
+        s_ms = max_over_ranks(float(np.mean([a + b for a, b in zip(ssym, snum)])), world, dev)
+        alt = {"clustering": "serial heap merge (Algorithm 3)", "hcluster_s": round(t_hcs, 3),
+               "nclusters": int(Acl_s.nclusters), "in_spgemm_units": round(t_hcs / (s_ms * 1e-3), 1),
+               "clustered_exact": {"gflops": round(job_gflops(flops, world, s_ms), 3), "ms_per_step": round(s_ms, 4)}}
+        del C_s, Acl_s, ws_s
+        torch.cuda.empty_cache()
+
+    fp64 = fp64_floor(cx, flops)
+
+    # ---- end to end through the public API, host buffers (the headline method)
+    e2e = None
+    if not args.no_e2e and it["params"] is not None:
+        e2e = e2e_learned(cx, A, B, it, it["params"], max(1, min(args.steps, 3)))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        gf, cores, nrows_s, dt = oracle_sample(A, 12.0, B=B)
+        cpu = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"{nrows_s} random rows of C ({dt:.1f} s; serial std::map Gustavson per row, rows "
+                         f"over {cores} OpenMP threads), rate scaled to GFLOP/s"}
+
+    # ---- the other workloads, measured beside the headline
+    configs = {}
+    for cname in [c for c in args.configs.split(",") if c and c != name]:
+        steps_c = max(1, min(args.steps, args.config_steps))
+        if cname == "batched256":
+            configs[cname] = measure_batched(cx, inputs["batched256"], steps_c, args.warmup)
+        else:
+            Ac, Bc = inputs[cname]
+            r = measure_product(cx, cname, Ac, Bc, inputs.get(("train", cname)), steps_c, args.warmup,
+                                headline=False)
+            r.pop("_internal")
+            configs[cname] = r
+        torch.cuda.empty_cache()
+
+    if rank == 0:
+        learned_head = res["clustered_learned"] is not None
+        clocks = (it["clk"] if learned_head else it["clk_exact"]).summary()
+        launches = it["launches"] if learned_head else it["exact_launches"]
+        head_ms = it["head_ms"]
+        traffic, traffic_how = traffic_from_profiles(name)
+        nr = res["numeric_roofline"]
+        out = {
+            "metric": METRIC, "value": round(job_gflops(flops, world, head_ms), 3), "unit": "GFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head_ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": res["dtype"],
+            "data": "synthetic",
+            "config": workload_config(name, A, B),
+            "method": "clustered+learned" if res["clustered_learned"] else "clustered (exact symbolic + numeric)",
+            "nnz_C": res["nnz_C"], "nclusters": res["nclusters"], "one_row_clusters": res["one_row_clusters"],
+            "clustered_exact": res["clustered_exact"], "learned": res["clustered_learned"], "rowwise": res["rowwise"],
+            "speedup_vs_rowwise": round(it["row_ms"] / head_ms, 4),
+            "speedup_exact_vs_rowwise": round(it["row_ms"] / it["step_ms"], 4),
+            "hbm": res["hbm"],
+            "roofline": {"bound": "hbm", "kernel": "cluster-wise numeric phase (spgemm_numeric, exact path)",
+                         "achieved": nr["achieved_GBs"], "peak": nr["peak_GBs"], "unit": "GB/s",
+                         "frac": nr["frac"], "peak_kind": nr["peak_kind"], "traffic": traffic,
+                         "algorithmic_bytes_per_launch": nr["algorithmic_bytes_per_launch"],
+                         "achieved_source": "algorithmic bytes of one numeric launch / its mean CUDA-event time in "
+                                            "this run (measured at this size)",
+                         "traffic_source": traffic_how,
+                         "target_frac": 0.5, "target_met": nr["frac"] >= 0.5},
+            "fp64": fp64,
+            "clustering": "hierarchical, round-parallel merge on the GPU (jacc_th 0.3, max 8)",
+            "alternative_clustering": alt,
+            "preprocess": res["preprocess"],
+            "csr_cluster_bytes_over_csr": res["csr_cluster_bytes_over_csr"],
+            "configs": configs,
+            "paper_context": PAPER_CONTEXT,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches or 0), "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+
+
+def _names(args) -> list:
+    return [args.workload] + [c for c in args.configs.split(",") if c and c != args.workload]
+
+
+def gen_tasks(args) -> list:
+    """Host generation tasks of every workload measured and of its training instances (no duplicates)."""
+    tasks = []
+    for n in _names(args):
+        if n == "batched256":
+            tasks += [("powerlaw", 3000 + i) for i in range(args.batch)]
+            continue
+        tasks.append(("workload", n))
+        if n in TRAINING and not args.no_learned:
+            gen, cnt, _ = TRAINING[n]
+            tasks += [("train", gen, 1000 + i) for i in range(cnt)]
+    seen, out = set(), []
+    for t in tasks:
+        if t not in seen:
+            seen.add(t)
+            out.append(t)
+    return out
+
+
+def collect(args, tasks, results) -> dict:
+    """inputs[name] = (A, B) (the batch: its list of matrices); inputs[("train", name)] = training matrices."""
+    by_task = dict(zip(tasks, results))
+    inputs = {}
+    for n in _names(args):
+        if n == "batched256":
+            inputs[n] = [by_task[("powerlaw", 3000 + i)] for i in range(args.batch)]
+            continue
+        inputs[n] = by_task[("workload", n)]
+        if n in TRAINING and not args.no_learned:
+            gen, cnt, _ = TRAINING[n]
+            inputs[("train", n)] = [by_task[("train", gen, 1000 + i)] for i in range(cnt)]
+    return inputs
 
 
 def main():
@@ -689,14 +903,16 @@ def main():
         run_reference(args, rank)
         return
     if args.workload == "batched256":
-        run_batched(args, rank, world, local_rank)
-        return
+        args.configs = ""                          # the batch alone as the headline line
+    tasks = gen_tasks(args)
+    procs = args.gen_procs or max(1, min(16, os.cpu_count() or 1))
+    inputs = collect(args, tasks, generate(tasks, procs))      # before any CUDA call
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    run_ours(args, rank, world, local_rank)
+    run_ours(args, rank, world, local_rank, inputs)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

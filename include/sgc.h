@@ -133,7 +133,12 @@ typedef struct sgc_options {
                                per cluster (B rows prefetched into L2 and streamed through a small
                                shared-memory ring) where the cluster's working set fits in 16 KB,
                                warp groups otherwise */
-  int32_t reserved[8];
+  int32_t wait_polls;       /* polls of a bounded device-side wait on an mbarrier (the cluster kernels'
+                               bulk copies) before it gives up and the call reports SGC_DEVICE_TIMEOUT;
+                               0 = default (2^22 polls, about 0.3 s); < 0 = give up without polling, which
+                               exercises the timeout path.  After giving up, a kernel waits (with the
+                               default limit) for the copies it has in flight before it returns. */
+  int32_t reserved[7];
 } sgc_options;
 
 /* Version of this ABI (SGC_ABI_VERSION). */
@@ -149,6 +154,16 @@ const char* sgc_last_error(void);
 
 /* Fills *opt with the defaults. */
 int sgc_default_options(sgc_options* opt);
+
+/* Measured throughput of the FP64 pipe, the arithmetic floor of the numeric
+ * phase (one multiply and one add per multiply-add of C = A*B, or one fused
+ * multiply-add with sgc_options.fused_fma = 1).  op 0: multiply, 1: add,
+ * 2: fused multiply-add.  Runs independent dependency chains on every SM of
+ * the current device, `iters` rounds of 16 operations per thread, after one
+ * untimed run; *gops_host receives operations (one per lane per
+ * instruction) per second / 1e9, timed with CUDA events on `stream`.  sink: a
+ * device double the kernel may write.  Synchronises. */
+int sgc_fp64_rate(int32_t op, int32_t iters, double* sink, double* gops_host, void* stream);
 
 /* Reads and clears the device status word kept in a spgemm workspace
  * (a failed device check or timeout in an asynchronous call such as
@@ -410,10 +425,32 @@ int spgemm_graph_destroy(sgc_graph* graph);
  *     Synchronises.
  *   phase2: copies slab rows into C and runs the exact numeric pass on the
  *     flagged clusters.  C (allocated by the caller with nnz(C)) equals the
- *     result of spgemm_symbolic + spgemm_numeric exactly.  Asynchronous.
+ *     result of spgemm_symbolic + spgemm_numeric exactly.  C->col and C->val
+ *     may be device memory or page-locked host memory mapped for the device
+ *     (cudaHostAlloc / cudaHostRegister): the kernels then store C's entries
+ *     straight into host memory; pageable host memory is rejected with
+ *     SGC_INVALID_ARG.  Asynchronous.
  *   All three take the same workspace (spgemm_learned_workspace_size).
  * ------------------------------------------------------------------------- */
 #define SGC_NNZ_PREDICTOR_PARAMS 1377
+#define SGC_NNZ_PREDICTOR_MAX_SETS 2
+
+/* nnz_predictor_save / nnz_predictor_load: checkpoints of trained predictors.
+ * A file holds nsets (1..SGC_NNZ_PREDICTOR_MAX_SETS) parameter sets of
+ * SGC_NNZ_PREDICTOR_PARAMS FP32 values each, back to back in `params` (device),
+ * and a metadata string: magic "SGCNNZP2", uint32 nsets, uint32 metadata
+ * length, the metadata bytes, the parameters; little-endian.  Files written
+ * with magic "SGCNNZP1" (one set) load as one set.
+ * save: meta may be NULL.  Synchronises the stream (reads params), then writes
+ *   the file; SGC_INVALID_ARG if the file cannot be opened, SGC_CUDA_ERROR if
+ *   a write fails.
+ * load: writes *nsets_out sets into params (device, room for max_sets sets)
+ *   and, when meta is not NULL, up to meta_cap - 1 metadata bytes and a
+ *   terminating 0.  SGC_INVALID_ARG for a missing file, a wrong magic, size or
+ *   set count, or more sets than max_sets.  Synchronises. */
+int nnz_predictor_save(const char* path, const float* params, int32_t nsets, const char* meta, void* stream);
+int nnz_predictor_load(const char* path, float* params, int32_t max_sets, int32_t* nsets_out, char* meta,
+                       size_t meta_cap, void* stream);
 typedef struct sgc_predictor {
   const float* params;   /* device, SGC_NNZ_PREDICTOR_PARAMS FP32 values (ignored if ncap is set) */
   float margin;          /* capacity margin over the prediction (e.g. 1.25) */

@@ -43,6 +43,9 @@ ResolvedOptions resolve(const sgc_options* opt) {
   if (r.cl_load < 20) r.cl_load = 20;
   if (r.cl_load > 75) r.cl_load = 75;
   r.lean = (opt && opt->cluster_kernel == 1) ? 1 : 0;
+  r.wait_limit = WAIT_POLLS_DEFAULT;
+  if (opt && opt->wait_polls > 0) r.wait_limit = (uint32_t)opt->wait_polls;
+  if (opt && opt->wait_polls < 0) r.wait_limit = 0;
   return r;
 }
 
@@ -928,15 +931,46 @@ int spgemm_learned_phase1(const sgc_csr_cluster* A, const sgc_csr* B, int32_t* s
   return rc;
 }
 
+// Device address through which kernels write an output array: the array itself
+// (device memory), or the device-mapped address of page-locked host memory.
+static int output_view(void* p, void** out, const char* what) {
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+    cudaGetLastError();
+    SGC_FAIL(SGC_INVALID_ARG, std::string(what) + ": not device or page-locked host memory");
+  }
+  if (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) {
+    *out = p;
+    return SGC_OK;
+  }
+  if (pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+    *out = pa.devicePointer;
+    return SGC_OK;
+  }
+  SGC_FAIL(SGC_INVALID_ARG, std::string(what) + ": pageable host memory (page-locked, mapped memory required)");
+}
+
 int spgemm_learned_phase2(const sgc_csr_cluster* A, const sgc_csr* B, const int32_t* slab_col,
-                          const void* slab_val, sgc_csr* C, void* ws, size_t ws_bytes, const sgc_options* opt,
+                          const void* slab_val, sgc_csr* C_in, void* ws, size_t ws_bytes, const sgc_options* opt,
                           void* stream) {
   int rc = check_product(A, B, true);
   if (rc) return rc;
-  rc = check_csr(C, "C", true);
+  rc = check_csr(C_in, "C", true);
   if (rc) return rc;
-  if (C->nrows != A->nrows || C->ncols != B->ncols || C->dtype != A->dtype)
+  if (C_in->nrows != A->nrows || C_in->ncols != B->ncols || C_in->dtype != A->dtype)
     SGC_FAIL(SGC_INVALID_ARG, "C shape or dtype inconsistent with A*B");
+  sgc_csr Cv = *C_in;  // C's entries may live in page-locked host memory: write through its device addresses
+  if (Cv.nnz > 0) {
+    void* pc = nullptr;
+    void* pv = nullptr;
+    rc = output_view(Cv.col, &pc, "C.col");
+    if (rc) return rc;
+    rc = output_view(Cv.val, &pv, "C.val");
+    if (rc) return rc;
+    Cv.col = (int32_t*)pc;
+    Cv.val = pv;
+  }
+  sgc_csr* C = &Cv;
   LwWs w = carve_lw(ws, ws_bytes, A->nrows, A->nclusters);
   if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
   cudaStream_t s = (cudaStream_t)stream;
@@ -958,6 +992,87 @@ int spgemm_learned_phase2(const sgc_csr_cluster* A, const sgc_csr* B, const int3
     case SGC_F64: SGC_CUDA((run_cluster_phase<false, SGC_F64>(av, bv, cv, C->row_ptr, eb, w.sp.status, L))); break;
     default: SGC_CUDA((run_cluster_phase<false, SGC_I64>(av, bv, cv, C->row_ptr, eb, w.sp.status, L))); break;
   }
+  return SGC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Predictor checkpoints: magic "SGCNNZP2", uint32 nsets, uint32 meta length,
+// the metadata bytes, then nsets x SGC_NNZ_PREDICTOR_PARAMS FP32 values, all
+// little-endian.  Files with magic "SGCNNZP1" (one set, same layout) load too.
+// ---------------------------------------------------------------------------
+int nnz_predictor_save(const char* path, const float* params, int32_t nsets, const char* meta, void* stream) {
+  if (!path || !params || nsets < 1 || nsets > SGC_NNZ_PREDICTOR_MAX_SETS)
+    SGC_FAIL(SGC_INVALID_ARG, "nnz_predictor_save: NULL path / params or nsets outside 1..SGC_NNZ_PREDICTOR_MAX_SETS");
+  const size_t n = (size_t)nsets * SGC_NNZ_PREDICTOR_PARAMS;
+  std::vector<float> h(n);
+  cudaStream_t s = (cudaStream_t)stream;
+  SGC_CUDA(cudaMemcpyAsync(h.data(), params, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+  SGC_CUDA(cudaStreamSynchronize(s));
+  const uint32_t mlen = meta ? (uint32_t)std::strlen(meta) : 0u;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) SGC_FAIL(SGC_INVALID_ARG, std::string("nnz_predictor_save: cannot open ") + path);
+  unsigned char head[16];
+  std::memcpy(head, "SGCNNZP2", 8);
+  const uint32_t ns = (uint32_t)nsets;
+  for (int b = 0; b < 4; ++b) {
+    head[8 + b] = (unsigned char)(ns >> (8 * b));
+    head[12 + b] = (unsigned char)(mlen >> (8 * b));
+  }
+  bool ok = std::fwrite(head, 1, 16, f) == 16;
+  if (ok && mlen) ok = std::fwrite(meta, 1, mlen, f) == mlen;
+  for (size_t i = 0; ok && i < n; ++i) {
+    uint32_t u;
+    std::memcpy(&u, &h[i], 4);
+    unsigned char b4[4] = {(unsigned char)u, (unsigned char)(u >> 8), (unsigned char)(u >> 16),
+                           (unsigned char)(u >> 24)};
+    ok = std::fwrite(b4, 1, 4, f) == 4;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) SGC_FAIL(SGC_CUDA_ERROR, std::string("nnz_predictor_save: write failed: ") + path);
+  return SGC_OK;
+}
+
+int nnz_predictor_load(const char* path, float* params, int32_t max_sets, int32_t* nsets_out, char* meta,
+                       size_t meta_cap, void* stream) {
+  if (!path || !params || !nsets_out || max_sets < 1) SGC_FAIL(SGC_INVALID_ARG, "nnz_predictor_load: bad arguments");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) SGC_FAIL(SGC_INVALID_ARG, std::string("nnz_predictor_load: cannot open ") + path);
+  std::vector<unsigned char> data;
+  unsigned char buf[65536];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof buf, f)) > 0) data.insert(data.end(), buf, buf + got);
+  std::fclose(f);
+  auto u32 = [&](size_t o) {
+    return (uint32_t)data[o] | ((uint32_t)data[o + 1] << 8) | ((uint32_t)data[o + 2] << 16) |
+           ((uint32_t)data[o + 3] << 24);
+  };
+  if (data.size() < 16) SGC_FAIL(SGC_INVALID_ARG, "nnz_predictor_load: file too short");
+  const bool v2 = std::memcmp(data.data(), "SGCNNZP2", 8) == 0;
+  const bool v1 = std::memcmp(data.data(), "SGCNNZP1", 8) == 0;
+  if (!v1 && !v2) SGC_FAIL(SGC_INVALID_ARG, "nnz_predictor_load: not a predictor checkpoint");
+  // version 1 stores the parameter count, version 2 the number of sets
+  const uint32_t a = u32(8), mlen = u32(12);
+  if (v1 && a != SGC_NNZ_PREDICTOR_PARAMS) SGC_FAIL(SGC_INVALID_ARG, "nnz_predictor_load: wrong parameter count");
+  const uint32_t nsets = v1 ? 1u : a;
+  if (nsets < 1 || nsets > (uint32_t)SGC_NNZ_PREDICTOR_MAX_SETS)
+    SGC_FAIL(SGC_INVALID_ARG, "nnz_predictor_load: bad number of parameter sets");
+  if ((int32_t)nsets > max_sets) SGC_FAIL(SGC_INVALID_ARG, "nnz_predictor_load: more sets than max_sets");
+  const size_t n = (size_t)nsets * SGC_NNZ_PREDICTOR_PARAMS;
+  if (data.size() != 16 + (size_t)mlen + 4 * n) SGC_FAIL(SGC_INVALID_ARG, "nnz_predictor_load: wrong file size");
+  std::vector<float> h(n);
+  for (size_t i = 0; i < n; ++i) {
+    const uint32_t u = u32(16 + mlen + 4 * i);
+    std::memcpy(&h[i], &u, 4);
+  }
+  if (meta && meta_cap > 0) {
+    const size_t m = mlen < meta_cap - 1 ? mlen : meta_cap - 1;
+    std::memcpy(meta, data.data() + 16, m);
+    meta[m] = 0;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  SGC_CUDA(cudaMemcpyAsync(params, h.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  SGC_CUDA(cudaStreamSynchronize(s));
+  *nsets_out = (int32_t)nsets;
   return SGC_OK;
 }
 

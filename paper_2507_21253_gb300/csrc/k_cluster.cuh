@@ -105,12 +105,14 @@ __host__ __device__ inline int warp_class(int64_t need) {
 // Warps per cluster for a shared-memory class: small footprints are small
 // clusters (one warp each); larger ones get a warp group so that more warps
 // share each byte of shared memory.
-__host__ __device__ inline int group_warps(int cls) {
+// max_warps (an option, 1..8) caps the group: fewer warps a cluster, more clusters in flight.
+__host__ __device__ inline int group_warps(int cls, int max_warps) {
   const int b = warp_class_bytes(cls);
-  return b <= 8 * 1024 ? 1 : (b <= 16 * 1024 ? 2 : (b <= 32 * 1024 ? 4 : 8));
+  const int w = b <= 8 * 1024 ? 1 : (b <= 16 * 1024 ? 2 : (b <= 32 * 1024 ? 4 : 8));
+  return w < max_warps ? w : (max_warps < 1 ? 1 : max_warps);
 }
-__host__ __device__ inline int groups_per_cta(int cls) {
-  int g = 8 / group_warps(cls);
+__host__ __device__ inline int groups_per_cta(int cls, int gw) {
+  int g = 8 / gw;
   const int by_smem = SMEM_MAX / warp_class_bytes(cls);
   return g < by_smem ? g : (by_smem < 1 ? 1 : by_smem);
 }
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
                                                               const int32_t* items, const int32_t* count_ptr,
                                                               int32_t* nout_rec, const int32_t* uc_rec, int mode,
                                                               int region_bytes, int gw, int fused, int cl_load,
-                                                              LearnedOut lo, void* status) {
+                                                              LearnedOut lo, uint32_t wait_limit, void* status) {
   using In = typename VT<DT>::In;
   using Acc = typename VT<DT>::Acc;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -327,12 +329,22 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       }
     }
     if (bulk) {
-      const bool ok = mbar_wait_bounded(bar, phase, WAIT_LIMIT);
-      phase ^= 1u;
-      if (!__all_sync(FULL, ok)) {
-        if (lane == 0) raise(st, DEV_TIMEOUT, 30, c);
-        return;  // timeouts are not expected; the group's other warps time out alike
+      // Every warp of the group takes the same decision: each posts whether its
+      // wait completed, then all read the posts after one group barrier, so no
+      // warp is left waiting at a later group barrier for warps that returned.
+      const bool ok = __all_sync(FULL, mbar_wait_bounded(bar, phase, wait_limit));
+      if (lane == 0) hdr[1 + wg] = ok ? 0 : 1;
+      group_sync(gw, gid);
+      int gave_up = 0;
+      for (int q = 0; q < gw; ++q) gave_up |= hdr[1 + q];
+      if (gave_up) {
+        if (gt == 0) raise(st, DEV_TIMEOUT, 30, c);
+        // the group's copies may still be landing in its shared memory: wait for
+        // them (bounded) before the CTA may exit, then give up on the launch
+        mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+        return;
       }
+      phase ^= 1u;
     }
     group_sync(gw, gid);
 

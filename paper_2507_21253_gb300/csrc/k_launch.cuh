@@ -109,7 +109,7 @@ cudaError_t launch_lean_classes(const AClusterView& A, const BView& B, const CVi
     const unsigned grid = grid_for(A.ncl, w, L.sms, best_occ[b]);
     kl<<<grid, w * 32, (size_t)w * rb, L.s>>>(A, B, C, bins.lean_items + (int64_t)b * bins.ncl,
                                                bins.count + BIN_LEAN0 + b, nout_rec, rb, L.o.cl_load, L.mode == 1,
-                                               lo, status);
+                                               lo, L.o.wait_limit, status);
     note_launches(1);
   }
   return cudaGetLastError();
@@ -145,7 +145,7 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
     attr = true;
   }
   for (int b = 0; b < NDB; ++b) {
-    const int gw = group_warps(b), groups = groups_per_cta(b);
+    const int gw = group_warps(b, L.o.max_warps), groups = groups_per_cta(b, gw);
     const int rbytes = warp_class_bytes(b);
     const size_t smem = (size_t)groups * rbytes;
     const int threads = groups * gw * 32;
@@ -153,7 +153,7 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
     const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
     kd<<<grid, threads, smem, L.s>>>(A, B, C, c_rp, bins.dense_items + (int64_t)b * bins.ncl, bins.count + b,
                                       bins.nout_rec, bins.uc_rec, L.mode, rbytes, gw, L.o.fused, L.o.cl_load,
-                                      LearnedOut{}, status);
+                                      LearnedOut{}, L.o.wait_limit, status);
     note_launches(1);
   }
   e = cudaGetLastError();
@@ -177,7 +177,7 @@ cudaError_t run_cluster_learned(const AClusterView& A, const BView& B, const Bin
     attr = true;
   }
   for (int b = 0; b < NDB; ++b) {
-    const int gw = group_warps(b), groups = groups_per_cta(b);
+    const int gw = group_warps(b, L.o.max_warps), groups = groups_per_cta(b, gw);
     const int rbytes = warp_class_bytes(b);
     const size_t smem = (size_t)groups * rbytes;
     const int threads = groups * gw * 32;
@@ -185,7 +185,7 @@ cudaError_t run_cluster_learned(const AClusterView& A, const BView& B, const Bin
     const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
     kd<<<grid, threads, smem, L.s>>>(A, B, CView{}, nullptr, lbins.dense_items + (int64_t)b * lbins.ncl,
                                       lbins.count + b, nullptr, lbins.uc_rec, L.mode, rbytes, gw, L.o.fused,
-                                      L.o.cl_load, lo, status);
+                                      L.o.cl_load, lo, L.o.wait_limit, status);
     note_launches(1);
   }
   cudaError_t e = cudaGetLastError();

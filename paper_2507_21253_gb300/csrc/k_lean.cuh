@@ -79,7 +79,7 @@ template <int DT, bool FUSED>
 __global__ void __launch_bounds__(256) k_cluster_lean(AClusterView A, BView B, CView C, const int32_t* items,
                                                       const int32_t* count_ptr, const int32_t* nout_rec,
                                                       int region_bytes, int cl_load, int bulk, LearnedOut lo,
-                                                      void* status) {
+                                                      uint32_t wait_limit, void* status) {
   using In = typename VT<DT>::In;
   using Acc = typename VT<DT>::Acc;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -138,9 +138,11 @@ __global__ void __launch_bounds__(256) k_cluster_lean(AClusterView A, BView B, C
     }
     auto await_a = [&]() -> bool {  // completes this cluster's A-value copy; false on timeout
       if (!win) return true;
-      const bool ok = mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+      const bool ok = __all_sync(FULL, mbar_wait_bounded(bar, phase, wait_limit));
+      // after a timeout the copy may still be landing: wait for it (bounded) before the warp returns
+      if (!ok) mbar_wait_bounded(bar, phase, WAIT_LIMIT);
       phase ^= 1u;
-      return __all_sync(FULL, ok);
+      return ok;
     };
     int run_a = 0;
     for (int tb = 0; tb < T; tb += 32) {

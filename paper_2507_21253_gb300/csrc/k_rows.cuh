@@ -12,7 +12,7 @@
 namespace sgc {
 
 constexpr int SMEM_MAX = 232448;          // 227 KB opt-in shared memory per CTA
-constexpr uint32_t WAIT_LIMIT = 1u << 22;  // mbarrier polls before giving up (~0.3 s)
+constexpr uint32_t WAIT_LIMIT = WAIT_POLLS_DEFAULT;  // polls of the drain after a timed-out wait
 
 enum { SRC_CSR = 0, SRC_CLUSTER = 1 };
 

@@ -55,6 +55,7 @@ constexpr int64_t HEAVY_SYM = 4 * SGC_HEAVY_ROW_OUTPUTS;  // symbolic: min(ub, n
 constexpr int64_t TOPK_HEAVY = 6144;
 constexpr int TOPK_LG_MAX = 13;
 constexpr int NUM_TABLE_LOAD = 50;  // default fill limit of the numeric cluster table
+constexpr uint32_t WAIT_POLLS_DEFAULT = 1u << 22;  // mbarrier polls before a wait gives up (~0.3 s)
 
 struct ResolvedOptions {
   int staging;
@@ -66,6 +67,7 @@ struct ResolvedOptions {
   int fused;
   int cl_load;  // numeric cluster-table fill limit, percent
   int lean;     // numeric: 1 = warp-per-cluster kernel where it fits
+  uint32_t wait_limit;  // mbarrier polls before a bounded wait gives up
 };
 ResolvedOptions resolve(const sgc_options* opt);
 

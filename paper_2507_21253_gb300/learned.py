@@ -8,15 +8,9 @@ the workload's generator.
 """
 from __future__ import annotations
 
-import os
-import struct
-
-import numpy as np
 import torch
 
 from . import sgc, synth
-
-MAGIC = b"SGCNNZP1"
 
 
 def instance_data(A, jacc_th: float = sgc.JACC_TH, max_cluster: int = sgc.MAX_CLUSTER, device="cuda",
@@ -37,9 +31,17 @@ def instance_data(A, jacc_th: float = sgc.JACC_TH, max_cluster: int = sgc.MAX_CL
 def train(make_instance, seeds, epochs: int = 4, batch: int = 256, lr: float = 2e-3, init_seed: int = 1,
           device="cuda", parallel: bool = False):
     """Trains on instances make_instance(seed) for seed in seeds; returns (params, per-step loss)."""
+    return train_on([make_instance(s) for s in seeds], epochs=epochs, batch=batch, lr=lr, init_seed=init_seed,
+                    device=device, parallel=parallel)
+
+
+def train_on(instances, epochs: int = 4, batch: int = 256, lr: float = 2e-3, init_seed: int = 1, device="cuda",
+             parallel: bool = False, info: dict | None = None):
+    """Trains on the given host matrices (each squared); returns (params, per-step loss).
+    `info`, when given, receives the number of samples (clusters) and of steps."""
     feats, ys = [], []
-    for s in seeds:
-        X, y = instance_data(make_instance(s), device=device, parallel=parallel)
+    for A in instances:
+        X, y = instance_data(A, device=device, parallel=parallel)
         feats.append(X)
         ys.append(y)
     X = torch.cat(feats)
@@ -50,27 +52,19 @@ def train(make_instance, seeds, epochs: int = 4, batch: int = 256, lr: float = 2
     order_d = torch.from_numpy(order[: steps * batch]).to(device)
     init = torch.from_numpy(synth.mlp_init(init_seed)).to(device)
     params, loss = sgc.nnz_predictor_train(X, y, order_d, steps, batch, lr, init)
+    if info is not None:
+        info.update(samples=n, steps=steps)
     return params, loss
 
 
 def save(path: str, params: torch.Tensor, meta: str = "") -> None:
-    """Versioned checkpoint: magic, parameter count, metadata, FP32 parameters."""
-    p = params.detach().float().cpu().numpy()
-    m = meta.encode()
-    with open(path, "wb") as fh:
-        fh.write(MAGIC + struct.pack("<II", p.size, len(m)) + m + p.tobytes())
+    """Versioned checkpoint written by the library (nnz_predictor_save)."""
+    sgc.nnz_predictor_save(path, params, meta)
 
 
 def load(path: str, device="cuda") -> torch.Tensor:
-    with open(path, "rb") as fh:
-        data = fh.read()
-    if data[:8] != MAGIC:
-        raise ValueError(f"{path}: not a predictor checkpoint")
-    n, mlen = struct.unpack("<II", data[8:16])
-    if n != sgc.NPARAM:
-        raise ValueError(f"{path}: {n} parameters, expected {sgc.NPARAM}")
-    p = np.frombuffer(data[16 + mlen:16 + mlen + 4 * n], dtype=np.float32).copy()
-    return torch.from_numpy(p).to(device)
+    """Parameters of a checkpoint (nnz_predictor_load), on the device."""
+    return sgc.nnz_predictor_load(path, device)[0]
 
 
 # generators of training instances, by workload family

@@ -61,7 +61,7 @@ class Predictor(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("staging", i32), ("validate", i32), ("stage_elems", i32), ("max_warps", i32),
                 ("load_pct", i32), ("fused_fma", i32), ("cluster_load_pct", i32), ("cluster_kernel", i32),
-                ("reserved", i32 * 8)]
+                ("wait_polls", i32), ("reserved", i32 * 7)]
 
 
 def _sig(name, *args):
@@ -118,6 +118,10 @@ _c = {
                                   P(i64), vp, ctypes.c_size_t, P(Options), vp),
     "spgemm_learned_phase2": _sig("spgemm_learned_phase2", P(ClusterStruct), P(CsrStruct), vp, vp, P(CsrStruct), vp,
                                   ctypes.c_size_t, P(Options), vp),
+    "nnz_predictor_save": _sig("nnz_predictor_save", ctypes.c_char_p, vp, i32, ctypes.c_char_p, vp),
+    "nnz_predictor_load": _sig("nnz_predictor_load", ctypes.c_char_p, vp, i32, P(i32), ctypes.c_char_p,
+                               ctypes.c_size_t, vp),
+    "sgc_fp64_rate": _sig("sgc_fp64_rate", i32, i32, vp, P(ctypes.c_double), vp),
     "csr_batch_pack": _sig("csr_batch_pack", i32, vp, P(CsrStruct), vp, vp, vp),
     "spgemm_graph_create": _sig("spgemm_graph_create", P(ClusterStruct), P(CsrStruct), P(CsrStruct), vp,
                                 ctypes.c_size_t, P(Options), vp, P(vp)),
@@ -152,11 +156,12 @@ def _ptr(t):
 
 
 def options(staging=STAGING_AUTO, validate=0, stage_elems=0, max_warps=0, load_pct=0, fused_fma=0,
-            cluster_load_pct=0, cluster_kernel=0) -> Options:
+            cluster_load_pct=0, cluster_kernel=0, wait_polls=0) -> Options:
     o = Options()
     _call("sgc_default_options", ctypes.byref(o))
     o.staging, o.validate, o.stage_elems, o.max_warps, o.load_pct = staging, validate, stage_elems, max_warps, load_pct
     o.fused_fma, o.cluster_load_pct, o.cluster_kernel = fused_fma, cluster_load_pct, cluster_kernel
+    o.wait_polls = wait_polls
     return o
 
 
@@ -519,6 +524,35 @@ def nnz_predictor_train(X, y, order, steps: int, batch: int, lr: float, init, wi
     return params, loss
 
 
+NNZ_PREDICTOR_MAX_SETS = 2
+
+
+def nnz_predictor_save(path: str, params: torch.Tensor, meta: str = "") -> None:
+    """Writes a checkpoint of one or more parameter sets (device FP32, a multiple of NPARAM values)."""
+    p = params.detach().to(torch.float32).contiguous()
+    if p.numel() % NPARAM:
+        raise ValueError(f"params: a multiple of {NPARAM} values")
+    _call("nnz_predictor_save", os.fsencode(path), _ptr(p), p.numel() // NPARAM, meta.encode(), _stream())
+
+
+def nnz_predictor_load(path: str, device="cuda"):
+    """Reads a checkpoint: (params as a device FP32 tensor of nsets * NPARAM values, metadata)."""
+    p = torch.empty(NNZ_PREDICTOR_MAX_SETS * NPARAM, dtype=torch.float32, device=device)
+    ns = i32()
+    meta = ctypes.create_string_buffer(4096)
+    _call("nnz_predictor_load", os.fsencode(path), _ptr(p), NNZ_PREDICTOR_MAX_SETS, ctypes.byref(ns), meta,
+          len(meta), _stream())
+    return p[: ns.value * NPARAM].clone(), meta.value.decode(errors="replace")
+
+
+def fp64_rate(op: int, iters: int = 2000, device="cuda") -> float:
+    """Measured FP64 operations per second / 1e9 (op 0 multiply, 1 add, 2 fused multiply-add)."""
+    sink = torch.zeros(1, dtype=torch.float64, device=device)
+    g = ctypes.c_double()
+    _call("sgc_fp64_rate", int(op), int(iters), _ptr(sink), ctypes.byref(g), _stream())
+    return g.value
+
+
 class LearnedSpgemm:
     """The symbolic-free learned path: plan (capacities), phase 1 (slab + row counts), phase 2 (C)."""
 
@@ -567,6 +601,19 @@ class LearnedSpgemm:
         _call("spgemm_learned_phase2", ctypes.byref(a), ctypes.byref(b), _ptr(self.slab_col), _ptr(self.slab_val),
               ctypes.byref(c), self.ws.ptr, self.ws.nbytes, _o(self.opt), _stream())
         return C
+
+    def phase2_to_host(self, host_col: torch.Tensor, host_val: torch.Tensor):
+        """Phase 2 with C's columns and values stored straight into pinned host tensors
+        (complete once the current stream is); C's row pointer stays in self.c_row_ptr."""
+        if host_col.dtype != torch.int32 or host_col.numel() < self.nnz or not host_col.is_pinned():
+            raise ValueError("host_col: pinned int32 host tensor of nnz(C) elements")
+        if host_val.dtype != self.B.val.dtype or host_val.numel() < self.nnz or not host_val.is_pinned():
+            raise ValueError("host_val: pinned host tensor of nnz(C) elements of B's value type")
+        c = CsrStruct(self.A.nrows, self.B.ncols, int(self.nnz), _ptr(self.c_row_ptr), _ptr(host_col),
+                      _ptr(host_val), _DT[self.B.val.dtype], 0)
+        a, b = self.A.struct(), self.B.struct()
+        _call("spgemm_learned_phase2", ctypes.byref(a), ctypes.byref(b), _ptr(self.slab_col), _ptr(self.slab_val),
+              ctypes.byref(c), self.ws.ptr, self.ws.nbytes, _o(self.opt), _stream())
 
     def run(self) -> DeviceCsr:
         self.phase1()

@@ -32,7 +32,8 @@ def test_header_declares_the_path():
     names = declared_functions()
     for n in ("csr_cluster_build", "spgemm_symbolic", "spgemm_numeric", "spgemm_rowwise_symbolic",
               "spgemm_rowwise_numeric", "hcluster_reorder", "cluster_variable_length", "spgemm_learned_phase1",
-              "spgemm_graph_create", "nnz_predictor_train", "csr_cluster_build_count_noalloc"):
+              "spgemm_graph_create", "nnz_predictor_train", "nnz_predictor_save", "nnz_predictor_load",
+              "sgc_fp64_rate", "csr_cluster_build_count_noalloc"):
         assert n in names
     assert len(names) >= 30
 

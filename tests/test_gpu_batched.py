@@ -67,9 +67,14 @@ def test_autotuner_picks_a_valid_config(sgc, tmp_path):
     mats = small_batch(6)
     P, row_off, col_off = sgc.csr_batch_pack([sgc.DeviceCsr.from_host(A) for A in mats])
     cache = str(tmp_path / "tune.json")
-    res = autotune.tune(P, reps=2, cache_path=cache, clusterings=("hc8", "fixed4"), loads=(75,))
+    space = {"clustering": ("hc8", "fixed4"), "staging": (sgc.STAGING_BULK, sgc.STAGING_LDG), "load_pct": (75,),
+             "max_warps": (8, 2)}
+    res = autotune.tune(P, reps=2, cache_path=cache, space=space)
+    # coordinate search: the start, then one new trial per other value of each dimension
     assert len(res["trials"]) == 4 and res["best"]["ms"] == min(t["ms"] for t in res["trials"])
-    again = autotune.tune(P, reps=2, cache_path=cache)       # served from the cache
+    assert res["default"] == res["trials"][0]
+    assert {t["max_warps"] for t in res["trials"]} == {8, 2}
+    again = autotune.tune(P, reps=2, cache_path=cache, space=space)       # served from the cache
     assert again["best"] == res["best"]
     best = res["best"]
     perm, cptr = autotune.cluster(P, best["clustering"])

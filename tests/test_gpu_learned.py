@@ -196,9 +196,41 @@ def test_training_gain_over_untrained(sgc):
 
 
 def test_checkpoint_round_trip(sgc, tmp_path):
+    """A trained predictor round-trips through nnz_predictor_save / _load (C ABI):
+    same parameters bit for bit, same metadata, same inferences; a one-set file of
+    the earlier format loads; a truncated file and a wrong magic are refused."""
+    import struct
+
     import torch
     from paper_2507_21253_gb300 import learned
-    p = torch.from_numpy(synth.mlp_init(5)).cuda()
+    params, _ = learned.train(learned.stencil_instance, [2, 3], epochs=2)
     f = str(tmp_path / "pred.bin")
-    learned.save(f, p, meta="planted")
-    assert torch.equal(learned.load(f), p)
+    learned.save(f, params, meta="stencil27 epochs=2")
+    back, meta = sgc.nnz_predictor_load(f)
+    assert torch.equal(back, params) and meta == "stencil27 epochs=2"
+    X = sgc.cluster_features(*_clustered(sgc, synth.stencil27_3d(14, 14, 14, seed=9)))
+    assert torch.equal(sgc.nnz_predictor_infer(back, X), sgc.nnz_predictor_infer(params, X))
+    two = torch.cat([params, params * 0.5])                       # two parameter sets in one file
+    sgc.nnz_predictor_save(f, two)
+    assert torch.equal(sgc.nnz_predictor_load(f)[0], two)
+    p = params.cpu().numpy()
+    v1 = str(tmp_path / "v1.bin")
+    with open(v1, "wb") as fh:                                    # one set, magic of the earlier format
+        fh.write(b"SGCNNZP1" + struct.pack("<II", p.size, 3) + b"abc" + p.tobytes())
+    back1, meta1 = sgc.nnz_predictor_load(v1)
+    assert torch.equal(back1, params) and meta1 == "abc"
+    with open(v1, "r+b") as fh:
+        fh.truncate(100)
+    with pytest.raises(sgc.SgcError) as e:
+        sgc.nnz_predictor_load(v1)
+    assert e.value.code == sgc.SGC_INVALID_ARG
+    with open(v1, "wb") as fh:
+        fh.write(b"NOTAPRED" + bytes(64))
+    with pytest.raises(sgc.SgcError):
+        sgc.nnz_predictor_load(v1)
+
+
+def _clustered(sgc, A):
+    Ad = sgc.DeviceCsr.from_host(A)
+    perm, cptr = sgc.hcluster_reorder_parallel(Ad)
+    return sgc.csr_cluster_build(Ad, perm, cptr, sgc.LAYOUT_MASKED), Ad

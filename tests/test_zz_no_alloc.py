@@ -76,3 +76,28 @@ def test_noalloc_rejects_oversized_input():
                   sgc._ptr(up), ctypes.byref(nu), ctypes.byref(nv), sgc._stream())
     assert rc == sgc.SGC_INVALID_ARG
     assert "limit" in sgc._lib.sgc_last_error().decode()
+
+
+def test_noalloc_failed_call_leaves_nothing_stale():
+    """A call that fails its device check (a row listed twice in perm) returns
+    SGC_DEVICE_CHECK_FAILED; the next valid call on the shared array returns 0
+    and matches the workspace entry point, so the failure left no stale flags
+    or status behind."""
+    import torch
+    sgc = lib()
+    A_h = random_sparse(3000, 2000, 0.005, 71, "f64")
+    A = sgc.DeviceCsr.from_host(A_h)
+    perm, cptr = synth.random_clusters(A_h.nrows, 71, 8)
+    bad = perm.copy()
+    bad[1] = bad[0]                    # row perm[0] twice, row perm[1] never: not a permutation
+    bad_d = torch.as_tensor(bad, dtype=torch.int32, device="cuda")
+    cptr_d = torch.as_tensor(cptr, dtype=torch.int64, device="cuda")
+    rc, *_ = _call(sgc, A, bad_d, cptr_d, sgc.LAYOUT_MASKED)
+    assert rc == sgc.SGC_DEVICE_CHECK_FAILED, sgc._lib.sgc_last_error().decode()
+    perm_d = torch.as_tensor(perm, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        ref_up, ref_vp, ref_nu, ref_nv = sgc.csr_cluster_build_count(A, perm_d, cptr_d, sgc.LAYOUT_MASKED)
+        rc, up, vp, nu, nv = _call(sgc, A, perm_d, cptr_d, sgc.LAYOUT_MASKED)
+        assert rc == 0, sgc._lib.sgc_last_error().decode()
+        assert (nu, nv) == (ref_nu, ref_nv)
+        assert torch.equal(up, ref_up) and torch.equal(vp, ref_vp)
