@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define SGC_ABI_VERSION 1
+#define SGC_ABI_VERSION 2
 
 enum {
   SGC_OK = 0,
@@ -403,10 +403,19 @@ int spgemm_graph_destroy(sgc_graph* graph);
  *   training); ws must be the workspace of a completed spgemm_symbolic.
  * Parameters: 1377 FP32 values W1[32][8], b1[32], W2[32][32], b2[32], w3[32], b3.
  * nnz_predictor_train: `steps` Adam steps (beta 0.9/0.999, eps 1e-8, rate lr)
- *   from `init`, batch `batch` (<= 256) samples order[s*batch .. +batch) at
- *   step s, loss = mean over valid samples (y >= 0) of (yhat - y)^2 / 2; one
- *   CTA, fixed summation order (deterministic).  loss_out: per step (nullable).
- * nnz_predictor_grad: the loss and gradient of one batch (samples idx[0..batch)).
+ *   from `init`, batch `batch` (a multiple of 32, at most
+ *   SGC_NNZ_PREDICTOR_MAX_BATCH) samples order[s*batch .. +batch) at step s,
+ *   loss = mean over valid samples (y >= 0) of (yhat - y)^2 / 2.  Data
+ *   parallel: one CTA per 32 samples of the batch in one cooperative launch;
+ *   each CTA sums its samples' gradients in sample order, and after a grid
+ *   barrier every CTA adds the CTAs' sums in CTA order and applies the same
+ *   update, so the result is deterministic.  loss_out: per step (nullable).
+ *   ws: device workspace of nnz_predictor_train_workspace_size(batch) bytes;
+ *   a grid barrier that does not complete within its bounded wait records
+ *   SGC_DEVICE_TIMEOUT there (read it with sgc_workspace_status).
+ *   Asynchronous.
+ * nnz_predictor_grad: the loss and gradient of one batch (samples idx[0..batch)),
+ *   same workspace rule.
  * nnz_predictor_infer: yhat for n samples.
  *
  * spgemm_learned_*: C = A*B without the exact symbolic pass.
@@ -462,11 +471,13 @@ int cluster_features(const sgc_csr_cluster* A, const sgc_csr* B, float* features
 int nnz_predictor_targets(const sgc_csr_cluster* A, const sgc_csr* B, const void* ws, size_t ws_bytes, float* y,
                           void* stream);
 int nnz_predictor_infer(const float* params, const float* features, int64_t n, float* yhat, void* stream);
+#define SGC_NNZ_PREDICTOR_MAX_BATCH 4096
+int nnz_predictor_train_workspace_size(int32_t batch, size_t* bytes);
 int nnz_predictor_grad(const float* params, const float* features, const float* y, const int32_t* idx,
-                       int32_t batch, float* grad, float* loss, void* stream);
+                       int32_t batch, float* grad, float* loss, void* ws, size_t ws_bytes, void* stream);
 int nnz_predictor_train(const float* features, const float* y, int64_t n, const int32_t* order, int64_t steps,
-                        int32_t batch, float lr, const float* init, float* params_out, float* loss_out,
-                        void* stream);
+                        int32_t batch, float lr, const float* init, float* params_out, float* loss_out, void* ws,
+                        size_t ws_bytes, void* stream);
 int spgemm_learned_workspace_size(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_options* opt,
                                   size_t* bytes);
 int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_predictor* pred,

@@ -837,21 +837,35 @@ int nnz_predictor_infer(const float* params, const float* features, int64_t n, f
   return SGC_OK;
 }
 
+int nnz_predictor_train_workspace_size(int32_t batch, size_t* bytes) {
+  if (!bytes || batch < 32 || batch > SGC_NNZ_PREDICTOR_MAX_BATCH || batch % 32)
+    SGC_FAIL(SGC_INVALID_ARG, "batch must be a multiple of 32 in 32..SGC_NNZ_PREDICTOR_MAX_BATCH; bytes non-NULL");
+  *bytes = mlp_train_ws_bytes(batch);
+  return SGC_OK;
+}
+
 int nnz_predictor_grad(const float* params, const float* features, const float* y, const int32_t* idx,
-                       int32_t batch, float* grad, float* loss, void* stream) {
-  if (batch < 32 || batch > 256 || batch % 32 || !params || !features || !y || !idx || !grad)
-    SGC_FAIL(SGC_INVALID_ARG, "batch must be a multiple of 32 in 32..256; NULL pointer");
-  SGC_CUDA(mlp_train_run(features, y, idx, 1, batch, 0.0f, params, nullptr, loss, 1, grad, (cudaStream_t)stream));
+                       int32_t batch, float* grad, float* loss, void* ws, size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  int rc = nnz_predictor_train_workspace_size(batch, &need);
+  if (rc) return rc;
+  if (!params || !features || !y || !idx || !grad) SGC_FAIL(SGC_INVALID_ARG, "NULL pointer");
+  if (!ws || ws_bytes < need) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  SGC_CUDA(mlp_train_run(features, y, idx, 1, batch, 0.0f, params, nullptr, loss, 1, grad, ws,
+                         (cudaStream_t)stream));
   return SGC_OK;
 }
 
 int nnz_predictor_train(const float* features, const float* y, int64_t n, const int32_t* order, int64_t steps,
-                        int32_t batch, float lr, const float* init, float* params_out, float* loss_out,
-                        void* stream) {
-  if (batch < 32 || batch > 256 || batch % 32) SGC_FAIL(SGC_INVALID_ARG, "batch must be a multiple of 32 in 32..256");
+                        int32_t batch, float lr, const float* init, float* params_out, float* loss_out, void* ws,
+                        size_t ws_bytes, void* stream) {
+  size_t need = 0;
+  int rc = nnz_predictor_train_workspace_size(batch, &need);
+  if (rc) return rc;
   if (n <= 0 || steps < 0 || !features || !y || !order || !init || !params_out)
     SGC_FAIL(SGC_INVALID_ARG, "bad arguments");
-  SGC_CUDA(mlp_train_run(features, y, order, steps, batch, lr, init, params_out, loss_out, 0, nullptr,
+  if (!ws || ws_bytes < need) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
+  SGC_CUDA(mlp_train_run(features, y, order, steps, batch, lr, init, params_out, loss_out, 0, nullptr, ws,
                          (cudaStream_t)stream));
   return SGC_OK;
 }

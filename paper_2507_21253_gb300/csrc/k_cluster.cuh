@@ -3,11 +3,13 @@
 // CSR_Cluster format, several independent groups per CTA, each with its own
 // shared-memory region and mbarrier; warps of a group sync on a named barrier.
 //
-//  1. Stage: every B row k in the cluster's column union, and the cluster's
-//     own value slots, are copied into the warp's shared memory once (1D bulk
-//     async copies completing on the warp's mbarrier, or cooperative loads),
-//     so each needed B row is read from memory once per cluster rather than
-//     once per row of the cluster.
+//  1. Stage: the column ids of every B row k in the cluster's column union,
+//     and the cluster's own value slots, are copied into the group's shared
+//     memory once (1D bulk async copies completing on the group's mbarrier,
+//     or cooperative loads); the B rows' values are brought into L2 with 1D
+//     bulk prefetches at the same time and read from there in step 3, so each
+//     needed B row is fetched from memory once per cluster rather than once
+//     per row of the cluster, and shared memory holds ids only.
 //  2. Map: the staged column ids are inserted once into a warp-local hash
 //     table, giving the cluster's output-column union; each staged id is then
 //     rewritten in place as a local id (numeric: its rank in column order,
@@ -46,7 +48,7 @@ __host__ __device__ inline int cluster_table_log2(bool sym, int64_t nb, int num_
 }
 
 struct WarpLayout {
-  int desc, stage_c, stage_v, stage_a, table, sorted, scratch, acc, flags, total;
+  int desc, stage_c, stage_a, table, sorted, scratch, acc, flags, total;
 };
 
 // Layout of one cluster in a warp's region.  T union columns, U staged B
@@ -55,20 +57,16 @@ struct WarpLayout {
 __host__ __device__ inline WarpLayout warp_layout(bool sym, int64_t T, int64_t U, int64_t nva, int LH, int64_t nout,
                                                   int K, int in_bytes, int acc_bytes, bool bulk) {
   WarpLayout L{};
-  const int64_t pad_c = bulk ? 6 : 0, pad_v = bulk ? (in_bytes == 8 ? 2 : 6) : 0;
+  const int64_t pad_c = bulk ? 6 : 0;
   int64_t o = 256;  // mbarrier, counters, scan partials (group header)
-  L.desc = (int)o;
-  o += 20 * T;
+  L.desc = (int)o;  // numeric: int64 B row start per column, then four int32 arrays
+  o += (sym ? 16 : 24) * T;
   o = (o + 15) & ~15ll;
   L.stage_c = (int)o;
   o += 4 * (U + pad_c * T);
   o = (o + 15) & ~15ll;
-  L.stage_v = (int)o;
   L.stage_a = (int)o;
   if (!sym) {
-    o += (int64_t)in_bytes * (U + pad_v * T);
-    o = (o + 15) & ~15ll;
-    L.stage_a = (int)o;
     o += (int64_t)in_bytes * (nva + 2 * (16 / in_bytes));
     o = (o + 15) & ~15ll;
   }
@@ -118,8 +116,8 @@ __host__ __device__ inline int groups_per_cta(int cls, int gw) {
 }
 
 struct WDesc {  // struct-of-arrays per union column, in the group's region
+  int64_t* bs;     // numeric: start of the B row in B.col / B.val
   int32_t* off_c;  // staged col offset (elements); bit 31: copy with loads (bulk mode)
-  int32_t* off_v;  // staged val offset (elements)
   int32_t* len;
   uint32_t* mask;
   int32_t* aoff;   // MASKED: staged value slot of (t, lowest row of the mask)
@@ -225,23 +223,23 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       continue;
     }
     WDesc d;
-    d.off_c = (int32_t*)(my + Ly.desc);
-    d.off_v = d.off_c + T;
-    d.len = d.off_v + T;
+    d.bs = (int64_t*)(my + Ly.desc);
+    d.off_c = SYM ? (int32_t*)d.bs : (int32_t*)(d.bs + T);
+    d.len = d.off_c + T;
     d.mask = (uint32_t*)(d.len + T);
     d.aoff = (int32_t*)(d.mask + T);
     int32_t* stage_c = (int32_t*)(my + Ly.stage_c);
-    In* stage_v = (In*)(my + Ly.stage_v);
     In* stage_a = (In*)(my + Ly.stage_a);
+    const In* bval = (const In*)B.val;
     int32_t* table = (int32_t*)(my + Ly.table);
     const int TH = 1 << LH;
 
     // ---- 1. descriptors and staging ---------------------------------------
-    int64_t run_c = 0, run_v = 0, run_a = 0;
+    int64_t run_c = 0, run_a = 0;
     if (bulk) fence_proxy_async_smem();  // earlier generic accesses to the region precede async writes
     for (int64_t tb = 0; tb < T; tb += GT) {
       const int64_t i = tb + gt;
-      int wc = 0, wv = 0, shc = 0, shv = 0, len = 0;
+      int wc = 0, shc = 0, len = 0;
       uint32_t m = 0;
       int64_t s = 0;
       bool ldg = !bulk;
@@ -253,40 +251,34 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
         len = (int)(e - s);
         if (bulk) {
           if (len > 0) {
-            constexpr int VA = 16 / (int)sizeof(In);
             const int64_t cs = s & ~3ll, ce = (e + 3) & ~3ll;
-            const int64_t vs = s & ~(int64_t)(VA - 1), ve = (e + VA - 1) & ~(int64_t)(VA - 1);
             wc = (int)(ce - cs);
-            wv = SYM ? 0 : (int)(ve - vs);
             shc = (int)(s - cs);
-            shv = (int)(s - vs);
-            if (ce > B.nnz || (!SYM && ve > B.nnz)) ldg = true;  // window would pass the array end
+            if (ce > B.nnz) ldg = true;  // window would pass the array end
+            // numeric: the row's values go to L2 now and are read from there while accumulating
+            if (!SYM) bulk_prefetch_row(B.val, s, len, (int)sizeof(In), B.nnz);
           }
         } else {
           wc = len;
-          wv = SYM ? 0 : len;
         }
       }
-      // one scan of three packed counters: col window (21 bits), val window (21 bits), mask bits
+      // one scan of two packed counters: col window (32 bits), mask bits
       uint64_t tot;
-      const uint64_t ex = group_excl_scan64((uint64_t)wc | ((uint64_t)wv << 21) | ((uint64_t)__popc(m) << 42), gw,
-                                            gid, wg, red64, &tot);
-      const int oc = (int)(ex & 0x1fffff), ov = (int)((ex >> 21) & 0x1fffff), oa = (int)(ex >> 42);
-      const int tc = (int)(tot & 0x1fffff), tv = (int)((tot >> 21) & 0x1fffff), ta = (int)(tot >> 42);
+      const uint64_t ex = group_excl_scan64((uint64_t)wc | ((uint64_t)__popc(m) << 32), gw, gid, wg, red64, &tot);
+      const int oc = (int)(ex & 0xffffffffu), oa = (int)(ex >> 32);
+      const int tc = (int)(tot & 0xffffffffu), ta = (int)(tot >> 32);
       if (i < T) {
+        if (!SYM) d.bs[i] = s;
         d.off_c[i] = (int32_t)(run_c + oc + shc) | (ldg ? (int32_t)0x80000000 : 0);
-        d.off_v[i] = (int32_t)(run_v + ov + shv);
         d.len[i] = len;
         d.mask[i] = m;
         d.aoff[i] = (int32_t)(run_a + oa);
         if (bulk && !ldg && len > 0) {
-          mbar_expect_tx(bar, (uint32_t)wc * 4u + (uint32_t)wv * (uint32_t)sizeof(In));
+          mbar_expect_tx(bar, (uint32_t)wc * 4u);
           bulk_g2s(stage_c + run_c + oc, B.col + (s - shc), (uint32_t)wc * 4u, bar);
-          if (!SYM) bulk_g2s(stage_v + run_v + ov, (const In*)B.val + (s - shv), (uint32_t)wv * sizeof(In), bar);
         }
       }
       run_c += tc;
-      run_v += tv;
       run_a += ta;
     }
     // the cluster's own value slots (numeric): one window covering [v0, v0 + nva)
@@ -322,11 +314,8 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       if (n == 0) continue;
       const int32_t k = A.ucol[u0 + i];
       const int64_t s = B.rp[k];
-      const int dc = oc & 0x7fffffff, dv = d.off_v[i];
-      for (int q = lane; q < n; q += 32) {
-        stage_c[dc + q] = B.col[s + q];
-        if (!SYM) stage_v[dv + q] = ((const In*)B.val)[s + q];
-      }
+      const int dc = oc & 0x7fffffff;
+      for (int q = lane; q < n; q += 32) stage_c[dc + q] = B.col[s + q];
     }
     if (bulk) {
       // Every warp of the group takes the same decision: each posts whether its
@@ -545,7 +534,9 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       const bool padded = A.layout == SGC_LAYOUT_PADDED;
       // ---- 3. accumulate: warp per row, the row's union columns in ascending order.
       // Each lane loads the descriptor and a_lt of one union column of a chunk of
-      // 32; the columns the row has are then broadcast one by one.
+      // 32; the columns the row has are then taken one by one, lanes over the
+      // entries of B row t (ids from shared memory, values from L2), with the
+      // next column's first 32 values loaded while the current one is applied.
       const int T32 = (int)T;
       for (int l = wg; l < K; l += gw) {
         Acc* al = acc + l * n_out;
@@ -555,36 +546,56 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
           const int t = tb + lane;
           const uint32_t mm = t < T32 ? d.mask[t] : 0u;
           const bool has = (mm >> l) & 1u;
-          int tn = 0, tc = 0, tv = 0;
+          int tn = 0, tc = 0;
+          int64_t ts = 0;
           In ta{};
           if (has) {
             tn = d.len[t];
             tc = d.off_c[t] & 0x7fffffff;
-            tv = d.off_v[t];
+            ts = d.bs[t];
             ta = padded ? av[t * K + l] : av[d.aoff[t] + __popc(mm & below)];
           }
           unsigned bits = __ballot_sync(FULL, has);
+          if (!bits) continue;
+          int src = __ffs(bits) - 1;
+          int n = __shfl_sync(FULL, tn, src), dc = __shfl_sync(FULL, tc, src);
+          int64_t bs = __shfl_sync(FULL, ts, src);
+          In a = __shfl_sync(FULL, ta, src);
+          In bv = lane < n ? bval[bs + lane] : In{};
           while (bits) {
-            const int src = __ffs(bits) - 1;
             bits &= bits - 1;
-            const int n = __shfl_sync(FULL, tn, src);
-            const int dc = __shfl_sync(FULL, tc, src);
-            const int dv = __shfl_sync(FULL, tv, src);
-            const In a = __shfl_sync(FULL, ta, src);
-            if (fused) {
+            int n2 = 0, dc2 = 0;
+            int64_t bs2 = 0;
+            In a2{}, bv2{};
+            if (bits) {  // warp-uniform: the next column's descriptor and first values
+              src = __ffs(bits) - 1;
+              n2 = __shfl_sync(FULL, tn, src);
+              dc2 = __shfl_sync(FULL, tc, src);
+              bs2 = __shfl_sync(FULL, ts, src);
+              a2 = __shfl_sync(FULL, ta, src);
+              if (lane < n2) bv2 = bval[bs2 + lane];
+            }
+            if (fused) {  // kernel-uniform: one arithmetic form per launch
               for (int q = lane; q < n; q += 32) {
+                const In b = q < 32 ? bv : bval[bs + q];
                 const int lid = stage_c[dc + q];
-                al[lid] = VT<DT>::madd(al[lid], a, stage_v[dv + q], true);
+                al[lid] = VT<DT>::madd(al[lid], a, b, true);
                 fl[lid] = 1;
               }
             } else {
               for (int q = lane; q < n; q += 32) {
+                const In b = q < 32 ? bv : bval[bs + q];
                 const int lid = stage_c[dc + q];
-                al[lid] = VT<DT>::madd(al[lid], a, stage_v[dv + q], false);
+                al[lid] = VT<DT>::madd(al[lid], a, b, false);
                 fl[lid] = 1;
               }
             }
             __syncwarp();  // the next column's lanes read what these lanes wrote
+            n = n2;
+            dc = dc2;
+            bs = bs2;
+            a = a2;
+            bv = bv2;
           }
         }
         // ---- 4. emit row l in column order ----------------------------------

@@ -3,8 +3,9 @@
 // Sec. 5); this is the library's extension:
 //  * cluster features (8 FP32 values per cluster from A's cluster structure
 //    and B's row lengths),
-//  * an 8-32-32-1 ReLU MLP in FP32: forward, exact backward, Adam, trained by
-//    one persistent CTA with a fixed summation order (deterministic),
+//  * an 8-32-32-1 ReLU MLP in FP32: forward, exact backward, Adam, trained
+//    data-parallel by a cooperative grid with a fixed summation order
+//    (deterministic),
 //  * capacities n_cap = ceil(margin * expm1(yhat)) per cluster, binning,
 //    slab offsets, and the compaction of slab rows into CSR.
 #include "k_launch.cuh"
@@ -109,26 +110,77 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const float* params, const fl
     yhat[s] = mlp_forward(P, X + s * NFEAT, h1, h2);
 }
 
-// One CTA; batch = blockDim.x samples per step (thread i = sample i).  Each
-// step: forward, loss gradient (mean over the valid samples: y >= 0), exact
-// backward, per-parameter gradient sums over the batch in sample order, Adam.
-// grad_only: one step on samples order[0..B), gradient and loss written, no update.
-__global__ void __launch_bounds__(256) k_mlp_train(const float* X, const float* y, const int32_t* order,
-                                                   int64_t steps, float lr, const float* init, float* params_out,
-                                                   float* loss_out, int grad_only, float* grad_out) {
+// Data-parallel training over a cooperative grid of G CTAs: each step, CTA g
+// takes samples order[step * B + 32 g .. + 32) of the batch (thread i < 32:
+// sample i): forward, residual, exact backward, then the CTA's partial
+// gradient (parameter q summed over its 32 samples in sample order) goes to
+// global memory.  After a grid barrier every CTA sums the G partials in CTA
+// order, divides by the batch's count of valid samples (y >= 0) and applies
+// the same Adam update to its own copy of the parameters, so all copies stay
+// identical and the result does not depend on timing (deterministic).
+// Per-sample arrays are stored feature-major ([unit][sample]) so the 32
+// sample-threads of a warp touch 32 different banks.  grad_only: one step,
+// the gradient and the loss are written, no update.
+constexpr int TR_S = 32;          // samples per CTA per step
+constexpr int TR_THREADS = 128;   // threads per CTA (the first 32 run the per-sample passes)
+constexpr int TR_SP = TR_S + 1;   // padded stride of the per-sample arrays
+
+struct TrainWs {
+  DevStatus status;
+  unsigned int bar_count, bar_gen;
+  unsigned int pad[12];
+};
+
+// Grid barrier for a cooperative launch: bounded spin; returns false (and
+// records DEV_TIMEOUT) when the other CTAs do not arrive in time.
+__device__ bool grid_barrier(TrainWs* w, unsigned int nctas, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    volatile unsigned int* gen = &w->bar_gen;
+    const unsigned int g0 = *gen;
+    if (atomicAdd(&w->bar_count, 1u) == nctas - 1) {
+      atomicExch(&w->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&w->bar_gen, 1u);
+    } else {
+      uint32_t polls = 0;
+      while (*gen == g0) {
+        if (++polls > (1u << 24)) {
+          ok = 0;
+          raise(&w->status, DEV_TIMEOUT, 60, (int64_t)blockIdx.x);
+          break;
+        }
+        if (polls > 64) __nanosleep(128);
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(TR_THREADS) k_mlp_train(const float* X, const float* y, const int32_t* order,
+                                                          int64_t steps, int B, float lr, const float* init,
+                                                          float* params_out, float* loss_out, int grad_only,
+                                                          float* grad_out, TrainWs* w, float* partial) {
   extern __shared__ __align__(16) float smf[];
-  const int B = blockDim.x, i = threadIdx.x;
+  __shared__ int s_ok;
+  const int i = threadIdx.x, T = blockDim.x, g = blockIdx.x, G = gridDim.x;
   float* P = smf;
   float* M = P + PPAD;
   float* V = M + PPAD;
-  float* Xs = V + PPAD;          // B * 8
-  float* H1 = Xs + B * NFEAT;    // B * 32 (after ReLU)
-  float* H2 = H1 + B * NH;
-  float* D1 = H2 + B * NH;       // dL/dz1
-  float* D2 = D1 + B * NH;       // dL/dz2
-  float* DY = D2 + B * NH;       // dL/dyhat
-  float* LS = DY + B;            // per-sample loss terms
-  for (int q = i; q < NPARAM; q += B) {
+  float* Xs = V + PPAD;           // [NFEAT][TR_SP]
+  float* H1 = Xs + NFEAT * TR_SP;  // [NH][TR_SP] after ReLU
+  float* H2 = H1 + NH * TR_SP;
+  float* D1 = H2 + NH * TR_SP;     // dL/dz1 (unnormalised: residual instead of residual / count)
+  float* D2 = D1 + NH * TR_SP;
+  float* DY = D2 + NH * TR_SP;     // [TR_SP]
+  float* LS = DY + TR_SP;          // [TR_SP] per-sample r^2 / 2
+  float* VL = LS + TR_SP;          // [TR_SP] 1 if valid
+  for (int q = i; q < NPARAM; q += T) {
     P[q] = init[q];
     M[q] = 0.0f;
     V[q] = 0.0f;
@@ -136,71 +188,95 @@ __global__ void __launch_bounds__(256) k_mlp_train(const float* X, const float* 
   __syncthreads();
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   float b1t = 1.0f, b2t = 1.0f;
+  const int PW = PPAD + 2;  // per-CTA partial record: NPARAM gradient sums, loss sum, valid count
   for (int64_t st = 0; st < steps; ++st) {
-    const int32_t s = order[st * B + i];
-    const float yv = y[s];
-    for (int f = 0; f < NFEAT; ++f) Xs[i * NFEAT + f] = X[(int64_t)s * NFEAT + f];
-    const bool valid = yv >= 0.0f;
-    const float yh = mlp_forward(P, Xs + i * NFEAT, H1 + i * NH, H2 + i * NH);
-    const int nvalid = __syncthreads_count(valid);
-    const float r = valid ? yh - yv : 0.0f;
-    const float dy = nvalid > 0 ? r / (float)nvalid : 0.0f;
-    DY[i] = dy;
-    LS[i] = nvalid > 0 ? 0.5f * r * r / (float)nvalid : 0.0f;
-    for (int o = 0; o < NH; ++o) D2[i * NH + o] = H2[i * NH + o] > 0.0f ? dy * P[OW3 + o] : 0.0f;
-    for (int k = 0; k < NH; ++k) {
-      float g = 0.0f;
-      for (int o = 0; o < NH; ++o) g = __fmaf_rn(D2[i * NH + o], P[OW2 + o * NH + k], g);
-      D1[i * NH + k] = H1[i * NH + k] > 0.0f ? g : 0.0f;
+    float* part = partial + (size_t)(st & 1) * G * PW;
+    if (i < TR_S) {
+      const int32_t sidx = order[st * B + (int64_t)g * TR_S + i];
+      const float yv = y[sidx];
+      float x[NFEAT], h1[NH], h2[NH];
+      for (int f = 0; f < NFEAT; ++f) {
+        x[f] = X[(int64_t)sidx * NFEAT + f];
+        Xs[f * TR_SP + i] = x[f];
+      }
+      const float yh = mlp_forward(P, x, h1, h2);
+      const bool valid = yv >= 0.0f;
+      const float r = valid ? yh - yv : 0.0f;
+      DY[i] = r;
+      LS[i] = 0.5f * r * r;
+      VL[i] = valid ? 1.0f : 0.0f;
+      for (int o = 0; o < NH; ++o) {
+        H1[o * TR_SP + i] = h1[o];
+        H2[o * TR_SP + i] = h2[o];
+        D2[o * TR_SP + i] = h2[o] > 0.0f ? r * P[OW3 + o] : 0.0f;
+      }
+      for (int k = 0; k < NH; ++k) {
+        float acc = 0.0f;
+        for (int o = 0; o < NH; ++o) acc = __fmaf_rn(D2[o * TR_SP + i], P[OW2 + o * NH + k], acc);
+        D1[k * TR_SP + i] = h1[k] > 0.0f ? acc : 0.0f;
+      }
     }
     __syncthreads();
-    // gradients: parameter q summed over samples 0..B-1 in order
-    for (int q = i; q < NPARAM; q += B) {
-      float g = 0.0f;
+    // this CTA's partial gradient: parameter q summed over its samples in order
+    for (int q = i; q < NPARAM + 2; q += T) {
+      float gq = 0.0f;
       if (q < OB1) {
         const int o = q / NFEAT, f = q % NFEAT;
-        for (int b = 0; b < B; ++b) g = __fmaf_rn(D1[b * NH + o], Xs[b * NFEAT + f], g);
+        for (int b = 0; b < TR_S; ++b) gq = __fmaf_rn(D1[o * TR_SP + b], Xs[f * TR_SP + b], gq);
       } else if (q < OW2) {
         const int o = q - OB1;
-        for (int b = 0; b < B; ++b) g += D1[b * NH + o];
+        for (int b = 0; b < TR_S; ++b) gq += D1[o * TR_SP + b];
       } else if (q < OB2) {
         const int o = (q - OW2) / NH, k = (q - OW2) % NH;
-        for (int b = 0; b < B; ++b) g = __fmaf_rn(D2[b * NH + o], H1[b * NH + k], g);
+        for (int b = 0; b < TR_S; ++b) gq = __fmaf_rn(D2[o * TR_SP + b], H1[k * TR_SP + b], gq);
       } else if (q < OW3) {
         const int o = q - OB2;
-        for (int b = 0; b < B; ++b) g += D2[b * NH + o];
+        for (int b = 0; b < TR_S; ++b) gq += D2[o * TR_SP + b];
       } else if (q < OB3) {
         const int k = q - OW3;
-        for (int b = 0; b < B; ++b) g = __fmaf_rn(DY[b], H2[b * NH + k], g);
+        for (int b = 0; b < TR_S; ++b) gq = __fmaf_rn(DY[b], H2[k * TR_SP + b], gq);
+      } else if (q == OB3) {
+        for (int b = 0; b < TR_S; ++b) gq += DY[b];
+      } else if (q == NPARAM) {
+        for (int b = 0; b < TR_S; ++b) gq += LS[b];
       } else {
-        for (int b = 0; b < B; ++b) g += DY[b];
+        for (int b = 0; b < TR_S; ++b) gq += VL[b];
       }
+      part[(size_t)g * PW + (q < NPARAM ? q : PPAD + (q - NPARAM))] = gq;
+    }
+    if (!grid_barrier(w, (unsigned)G, &s_ok)) return;
+    // every CTA: the batch gradient as the CTA-ordered sum of the partials, then Adam
+    float nvalid = 0.0f, lsum = 0.0f;
+    for (int c = 0; c < G; ++c) {
+      lsum += part[(size_t)c * PW + PPAD];
+      nvalid += part[(size_t)c * PW + PPAD + 1];
+    }
+    const float inv = nvalid > 0.0f ? 1.0f / nvalid : 0.0f;
+    if (g == 0 && i == 0 && (loss_out || grad_only)) {
+      if (loss_out) loss_out[st] = lsum * inv;
+    }
+    if (!grad_only) {
+      b1t *= b1;
+      b2t *= b2;
+    }
+    for (int q = i; q < NPARAM; q += T) {
+      float gq = 0.0f;
+      for (int c = 0; c < G; ++c) gq += part[(size_t)c * PW + q];
+      gq *= inv;
       if (grad_only) {
-        grad_out[q] = g;
-      } else {
-        M[q] = b1 * M[q] + (1.0f - b1) * g;
-        V[q] = b2 * V[q] + (1.0f - b2) * g * g;
+        if (g == 0) grad_out[q] = gq;
+        continue;
       }
-    }
-    if (loss_out || grad_only) {
-      __syncthreads();
-      if (i == 0) {
-        float l = 0.0f;
-        for (int b = 0; b < B; ++b) l += LS[b];
-        if (loss_out) loss_out[st] = l;
-      }
-    }
-    if (grad_only) return;
-    b1t *= b1;
-    b2t *= b2;
-    __syncthreads();
-    for (int q = i; q < NPARAM; q += B) {
+      M[q] = b1 * M[q] + (1.0f - b1) * gq;
+      V[q] = b2 * V[q] + (1.0f - b2) * gq * gq;
       const float mh = M[q] / (1.0f - b1t), vh = V[q] / (1.0f - b2t);
       P[q] -= lr * mh / (sqrtf(vh) + eps);
     }
+    if (grad_only) return;
     __syncthreads();
   }
-  for (int q = i; q < NPARAM; q += B) params_out[q] = P[q];
+  if (g == 0)
+    for (int q = i; q < NPARAM; q += T) params_out[q] = P[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -312,21 +388,39 @@ cudaError_t mlp_infer_run(const float* params, const float* X, int64_t n, float*
   return cudaGetLastError();
 }
 
-size_t mlp_train_smem(int B) { return sizeof(float) * (3 * PPAD + (size_t)B * (NFEAT + 4 * NH + 2)); }
+size_t mlp_train_smem() { return sizeof(float) * (3 * PPAD + (size_t)TR_SP * (NFEAT + 4 * NH + 3)); }
+
+size_t mlp_train_ws_bytes(int B) {
+  const size_t G = (size_t)(B / TR_S);
+  return 256 + sizeof(float) * 2 * G * (PPAD + 2) + 256;
+}
 
 cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, int64_t steps, int B, float lr,
                           const float* init, float* params_out, float* loss_out, int grad_only, float* grad_out,
-                          cudaStream_t s) {
+                          void* ws, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_mlp_train<<<1, B, mlp_train_smem(B), s>>>(X, y, order, steps, lr, init, params_out, loss_out, grad_only,
-                                              grad_out);
+  const int G = B / TR_S;
+  TrainWs* w = (TrainWs*)ws;
+  float* partial = (float*)((char*)ws + 256);
+  cudaError_t e = cudaMemsetAsync(w, 0, sizeof(TrainWs), s);
+  if (e != cudaSuccess) return e;
+  if (steps <= 0) {  // no step: the initial parameters
+    if (!grad_only && params_out != init)
+      return cudaMemcpyAsync(params_out, init, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, s);
+    return cudaSuccess;
+  }
+  const size_t smem = mlp_train_smem();
+  void* args[] = {(void*)&X, (void*)&y, (void*)&order, (void*)&steps, (void*)&B, (void*)&lr, (void*)&init,
+                  (void*)&params_out, (void*)&loss_out, (void*)&grad_only, (void*)&grad_out, (void*)&w,
+                  (void*)&partial};
+  e = cudaLaunchCooperativeKernel((const void*)k_mlp_train, dim3(G), dim3(TR_THREADS), args, smem, s);
   note_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const int32_t* ncap_in,

