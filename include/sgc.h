@@ -398,9 +398,12 @@ int spgemm_graph_destroy(sgc_graph* graph);
  *   log1p(ncols(B))/16, (last - first union column + 1)/ncols(B);
  *   T = union columns, U = sum of nnz(B_t) over them, row flop bound
  *   ub_l = sum of nnz(B_t) over the row's columns.  Asynchronous.
- * nnz_predictor_targets: y[c] = log1p(n_out) for the clusters the symbolic
- *   phase handled in the cluster kernel, -1 for the others (ignored by
- *   training); ws must be the workspace of a completed spgemm_symbolic.
+ * nnz_predictor_targets: training targets from a completed spgemm_symbolic
+ *   (ws: its workspace; c_row_ptr: C's row pointer it wrote): y[c] =
+ *   log1p(n_out) for the clusters the symbolic phase handled in the cluster
+ *   kernel and for one-row clusters (whose n_out is their row's count), -1 for
+ *   the others (ignored by training); y_total[c] (nullable) = log1p(nnz_c),
+ *   nnz_c = the summed counts of the cluster's rows (always known).
  * Parameters: 1377 FP32 values W1[32][8], b1[32], W2[32][32], b2[32], w3[32], b3.
  * nnz_predictor_train: `steps` Adam steps (beta 0.9/0.999, eps 1e-8, rate lr)
  *   from `init`, batch `batch` (a multiple of 32, at most
@@ -421,17 +424,22 @@ int spgemm_graph_destroy(sgc_graph* graph);
  * spgemm_learned_*: C = A*B without the exact symbolic pass.
  *   plan: features -> MLP (or the caller's per-cluster capacities) -> per
  *     cluster n_cap = min(min(U, ncols(B)), max(1, ceil(margin * scale *
- *     max(expm1(yhat), 0)))) (FP32) -> per row slab capacity min(h_l, n_cap),
- *     h_l = min(ub_l, ncols(B)); returns the slab size (elements) in
- *     *slab_elems_host.  Synchronises.
- *   phase1: one cluster-wise pass computes every cluster whose n_out <= n_cap
- *     into the caller's slab (slab_col int32, slab_val of A's dtype, slab_elems
- *     each) and writes its row counts; a cluster with more output columns
- *     (an under-prediction) is flagged and its rows go through the exact
- *     symbolic pass, as do the rows of one-row clusters (the row kernels'
- *     work in every path); c_row_ptr (nrows+1) is C's row pointer;
- *     *c_nnz_host = nnz(C), *n_overflow_host = clusters sent to the exact path.
- *     Synchronises.
+ *     max(expm1(yhat), 0)))) (FP32), the capacity of the cluster's column
+ *     table and accumulators; with params_total, nnz_hat_c = ceil(
+ *     margin_total * scale * max(expm1(yhat_total), 0)), capped by the bound
+ *     sum_l min(h_l, n_cap) (h_l = min(ub_l, ncols(B))), which is used instead
+ *     when params_total is NULL.  The slab is one pool of sum_c nnz_hat_c
+ *     elements, returned in *slab_elems_host.  Clusters of every size,
+ *     one-row clusters included, are planned this way; a cluster whose
+ *     working set exceeds shared memory goes to the exact path.  Synchronises.
+ *   phase1: one cluster-wise pass computes every planned cluster whose n_out
+ *     <= n_cap, counts its rows, reserves their total from the pool with one
+ *     atomic and writes the rows there (positions in the pool depend on
+ *     timing, C does not); a cluster with more output columns than n_cap
+ *     (an under-prediction), or one that finds the pool exhausted, is
+ *     flagged and its rows go through the exact symbolic pass; c_row_ptr
+ *     (nrows+1) is C's row pointer; *c_nnz_host = nnz(C), *n_overflow_host =
+ *     clusters sent to the exact path.  Synchronises.
  *   phase2: copies slab rows into C and runs the exact numeric pass on the
  *     flagged clusters.  C (allocated by the caller with nnz(C)) equals the
  *     result of spgemm_symbolic + spgemm_numeric exactly.  C->col and C->val
@@ -461,15 +469,21 @@ int nnz_predictor_save(const char* path, const float* params, int32_t nsets, con
 int nnz_predictor_load(const char* path, float* params, int32_t max_sets, int32_t* nsets_out, char* meta,
                        size_t meta_cap, void* stream);
 typedef struct sgc_predictor {
-  const float* params;   /* device, SGC_NNZ_PREDICTOR_PARAMS FP32 values (ignored if ncap is set) */
-  float margin;          /* capacity margin over the prediction (e.g. 1.25) */
-  float scale;           /* multiplies the prediction (1 = as predicted) */
-  const int32_t* ncap;   /* optional device array of nclusters capacities used instead of the MLP */
+  const float* params;        /* device, SGC_NNZ_PREDICTOR_PARAMS FP32 values: predicts log1p(n_out)
+                                 (ignored if ncap is set) */
+  float margin;               /* capacity margin over the prediction (e.g. 1.25) */
+  float scale;                /* multiplies both predictions (1 = as predicted) */
+  const int32_t* ncap;        /* optional device array of nclusters capacities used instead of the MLP */
+  const float* params_total;  /* optional device parameter set predicting log1p(nnz_c), the cluster's
+                                 output nonzeros (its rows' counts summed), which sizes the slab; NULL:
+                                 the slab is sized by the bound sum_l min(h_l, n_cap) */
+  float margin_total;         /* margin of the slab over the summed nnz_c predictions; 0 = margin */
+  int32_t reserved;
 } sgc_predictor;
 
 int cluster_features(const sgc_csr_cluster* A, const sgc_csr* B, float* features, void* stream);
-int nnz_predictor_targets(const sgc_csr_cluster* A, const sgc_csr* B, const void* ws, size_t ws_bytes, float* y,
-                          void* stream);
+int nnz_predictor_targets(const sgc_csr_cluster* A, const sgc_csr* B, const void* ws, size_t ws_bytes,
+                          const int64_t* c_row_ptr, float* y, float* y_total, void* stream);
 int nnz_predictor_infer(const float* params, const float* features, int64_t n, float* yhat, void* stream);
 #define SGC_NNZ_PREDICTOR_MAX_BATCH 4096
 int nnz_predictor_train_workspace_size(int32_t batch, size_t* bytes);

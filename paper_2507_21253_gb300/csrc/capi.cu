@@ -782,8 +782,11 @@ struct LwWs {
   BinOut lb;
   float* X;
   float* yhat;
+  float* yhat_tot;
   int32_t *ncap, *flag, *flist, *flist_count, *flist_plan, *h_pos;
-  int64_t* slab_off;
+  int64_t* slab_off;  // per position: the row's place in the slab (written by the learned kernels)
+  int64_t* tot_cap;   // ncl + 1: prefix of the clusters' slab shares; tot_cap[ncl] = pool capacity
+  unsigned long long* pool;
   size_t bytes;
 };
 LwWs carve_lw(void* base, size_t cap, int64_t nrows, int64_t ncl) {
@@ -799,6 +802,7 @@ LwWs carve_lw(void* base, size_t cap, int64_t nrows, int64_t ncl) {
   w.lb.uc_rec = w.sp.bins.uc_rec;
   w.X = cv.take<float>(ncl * 8);
   w.yhat = cv.take<float>(ncl);
+  w.yhat_tot = cv.take<float>(ncl);
   w.ncap = cv.take<int32_t>(ncl);
   w.flag = cv.take<int32_t>(ncl);
   w.flist = cv.take<int32_t>(ncl);
@@ -806,6 +810,8 @@ LwWs carve_lw(void* base, size_t cap, int64_t nrows, int64_t ncl) {
   w.flist_plan = cv.take<int32_t>(1);
   w.h_pos = cv.take<int32_t>(nrows);
   w.slab_off = cv.take<int64_t>(nrows + 1);
+  w.tot_cap = cv.take<int64_t>(ncl + 1);
+  w.pool = cv.take<unsigned long long>(1);
   w.bytes = cv.off + 256;
   return w;
 }
@@ -820,14 +826,14 @@ int cluster_features(const sgc_csr_cluster* A, const sgc_csr* B, float* features
   return SGC_OK;
 }
 
-int nnz_predictor_targets(const sgc_csr_cluster* A, const sgc_csr* B, const void* ws, size_t ws_bytes, float* y,
-                          void* stream) {
+int nnz_predictor_targets(const sgc_csr_cluster* A, const sgc_csr* B, const void* ws, size_t ws_bytes,
+                          const int64_t* c_row_ptr, float* y, float* y_total, void* stream) {
   int rc = check_product(A, B, false);
   if (rc) return rc;
   SpWs w = carve_sp((void*)ws, ws_bytes, A->nrows, A->nclusters);
   if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "not a symbolic workspace of this A");
-  if (A->nclusters > 0 && !y) SGC_FAIL(SGC_INVALID_ARG, "y is NULL");
-  SGC_CUDA(targets_run(w.bins.nout_rec, A->nclusters, y, num_sms(), (cudaStream_t)stream));
+  if (A->nclusters > 0 && (!y || !c_row_ptr)) SGC_FAIL(SGC_INVALID_ARG, "y or c_row_ptr is NULL");
+  SGC_CUDA(targets_run(cview(A, false), w.bins.nout_rec, c_row_ptr, y, y_total, num_sms(), (cudaStream_t)stream));
   return SGC_OK;
 }
 
@@ -883,7 +889,8 @@ int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_pr
   int rc = check_product(A, B, false);
   if (rc) return rc;
   if (!pred || !slab_elems_host || (!pred->params && !pred->ncap)) SGC_FAIL(SGC_INVALID_ARG, "bad predictor");
-  if (!(pred->margin > 0.0f) || !(pred->scale >= 0.0f)) SGC_FAIL(SGC_INVALID_ARG, "margin must be > 0, scale >= 0");
+  if (!(pred->margin > 0.0f) || !(pred->scale >= 0.0f) || !(pred->margin_total >= 0.0f))
+    SGC_FAIL(SGC_INVALID_ARG, "margin must be > 0, margin_total >= 0, scale >= 0");
   LwWs w = carve_lw(ws, ws_bytes, A->nrows, A->nclusters);
   if (!ws || ws_bytes < w.bytes) SGC_FAIL(SGC_WORKSPACE_TOO_SMALL, "workspace too small");
   cudaStream_t s = (cudaStream_t)stream;
@@ -897,13 +904,16 @@ int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_pr
   const BView bv = bview(B, false);
   SGC_CUDA(features_run(av, bv, w.X, w.sp.bins.uc_rec, w.h_pos, sms, s));
   if (!pred->ncap) SGC_CUDA(mlp_infer_run(pred->params, w.X, A->nclusters, w.yhat, sms, s));
+  const bool tot = pred->params_total != nullptr;
+  if (tot) SGC_CUDA(mlp_infer_run(pred->params_total, w.X, A->nclusters, w.yhat_tot, sms, s));
+  const float mtot = pred->margin_total > 0.0f ? pred->margin_total : pred->margin;
   const int inb = dtype_bytes(A->dtype);
-  SGC_CUDA(learned_bin_run(av, bv, w.yhat, pred->ncap, pred->margin, pred->scale, w.sp.bins.uc_rec, w.h_pos, w.ncap,
-                           w.slab_off, w.flag, w.flist, w.flist_count, w.lb, inb, 8, mode, o.cl_load, o.lean, sms,
-                           s));
-  SGC_CUDA(inclusive_scan_i64(w.slab_off + 1, A->nrows, w.sp.scan_tmp, s));
+  SGC_CUDA(learned_bin_run(av, bv, w.yhat, tot ? w.yhat_tot : nullptr, pred->ncap, pred->margin, mtot, pred->scale,
+                           w.sp.bins.uc_rec, w.h_pos, w.ncap, w.tot_cap, w.flag, w.flist, w.flist_count, w.lb, inb, 8,
+                           mode, o.cl_load, o.lean, sms, s));
+  SGC_CUDA(inclusive_scan_i64(w.tot_cap + 1, A->nclusters, w.sp.scan_tmp, s));
   SGC_CUDA(cudaMemcpyAsync(w.flist_plan, w.flist_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-  SGC_CUDA(cudaMemcpyAsync(slab_elems_host, w.slab_off + A->nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SGC_CUDA(cudaMemcpyAsync(slab_elems_host, w.tot_cap + A->nclusters, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   return sync_status(w.sp.status, s);
 }
 
@@ -923,10 +933,12 @@ int spgemm_learned_phase1(const sgc_csr_cluster* A, const sgc_csr* B, int32_t* s
   SGC_CUDA(cudaMemsetAsync(w.sp.status, 0, sizeof(DevStatus), s));
   SGC_CUDA(cudaMemsetAsync(c_row_ptr, 0, sizeof(int64_t), s));
   SGC_CUDA(cudaMemcpyAsync(w.flist_count, w.flist_plan, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  SGC_CUDA(cudaMemsetAsync(w.pool, 0, sizeof(unsigned long long), s));
   if (A->nrows > 0) {
     const AClusterView av = cview(A, true);
     const BView bv = bview(B, true);
-    const LearnedOut lo{1, w.ncap, w.slab_off, slab_col, slab_val, c_row_ptr, w.flag, w.flist, w.flist_count};
+    const LearnedOut lo{1,      w.ncap,        w.slab_off, slab_col, slab_val,
+                        c_row_ptr, w.flag,     w.flist,    w.flist_count, w.pool, w.tot_cap + A->nclusters};
     switch (A->dtype) {
       case SGC_F32: SGC_CUDA(run_cluster_learned<SGC_F32>(av, bv, w.lb, lo, w.sp.status, L)); break;
       case SGC_F64: SGC_CUDA(run_cluster_learned<SGC_F64>(av, bv, w.lb, lo, w.sp.status, L)); break;

@@ -58,7 +58,7 @@ __host__ __device__ inline WarpLayout warp_layout(bool sym, int64_t T, int64_t U
                                                   int K, int in_bytes, int acc_bytes, bool bulk) {
   WarpLayout L{};
   const int64_t pad_c = bulk ? 6 : 0;
-  int64_t o = 256;  // mbarrier, counters, scan partials (group header)
+  int64_t o = 512;  // group header: mbarrier, counters, scan partials, per-row counts, slab base
   L.desc = (int)o;  // numeric: int64 B row start per column, then four int32 arrays
   o += (sym ? 16 : 24) * T;
   o = (o + 15) & ~15ll;
@@ -175,6 +175,37 @@ __device__ __forceinline__ uint64_t group_excl_scan64(uint64_t v, int gw, int gi
   return base + incl - v;
 }
 
+// Row l of a cluster: its entries are the set flags fl[0..n_out) in rank (=
+// column) order; emit writes at most `cap` of them at out0 and returns the
+// row's count (warp-collective), count_row only counts.
+template <int DT>
+__device__ __forceinline__ int64_t emit_row(const typename VT<DT>::Acc* al, const uint8_t* fl, const int32_t* srt,
+                                           int n_out, int32_t* ocol, typename VT<DT>::In* oval, int64_t out0,
+                                           int64_t cap) {
+  const unsigned lt = lanemask_lt();
+  int64_t nn = 0;
+  for (int x0 = 0; x0 < n_out; x0 += 32) {
+    const int x = x0 + lane_id();
+    const bool f = x < n_out && fl[x];
+    const unsigned bal = __ballot_sync(FULL, f);
+    const int64_t pos = nn + __popc(bal & lt);
+    if (f && pos < cap) {
+      ocol[out0 + pos] = srt[x];
+      oval[out0 + pos] = VT<DT>::out(al[x]);
+    }
+    nn += __popc(bal);
+  }
+  return nn;
+}
+__device__ __forceinline__ int count_row(const uint8_t* fl, int n_out) {
+  int nn = 0;
+  for (int x0 = 0; x0 < n_out; x0 += 32) {
+    const int x = x0 + lane_id();
+    nn += __popc(__ballot_sync(FULL, x < n_out && fl[x]));
+  }
+  return nn;
+}
+
 template <bool SYM, int DT>
 __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A, BView B, CView C, int64_t* c_rp_sym,
                                                               const int32_t* items, const int32_t* count_ptr,
@@ -190,11 +221,14 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
   unsigned char* my = sm + (size_t)gid * region_bytes;
   uint64_t* bar = (uint64_t*)my;
   // group header: [0,8) mbarrier; [8,72) ints: [0] distinct count, [1..8] per-warp flags, [9] cursor;
-  // [72,104) / [104,136) per-warp key min / max; [136,200) per-warp 64-bit scan partials
+  // [72,104) / [104,136) per-warp key min / max; [136,200) per-warp 64-bit scan partials;
+  // [256,384) per-row counts (learned); [384,392) the cluster's slab offset (learned)
   int* hdr = (int*)(my + 8);
   int* wmin = (int*)(my + 72);
   int* wmax = (int*)(my + 104);
   uint64_t* red64 = (uint64_t*)(my + 136);
+  int32_t* rcnt = (int32_t*)(my + 256);  // learned: per-row counts of the cluster
+  int64_t* sbase = (int64_t*)(my + 384);  // learned: the cluster's slab pool offset
   DevStatus* st = (DevStatus*)status;
   const bool bulk = mode == 1;
   if (bulk) {
@@ -598,39 +632,45 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
             bv = bv2;
           }
         }
-        // ---- 4. emit row l in column order ----------------------------------
-        const int64_t orow = A.perm[p0 + l];
-        int64_t out0, expect;
-        int32_t* ocol = C.col;
-        In* oval = (In*)C.val;
-        if (lo.active) {  // slab slot of this position; capacity = distance to the next
-          out0 = lo.slab_off[p0 + l];
-          expect = lo.slab_off[p0 + l + 1] - out0;
-          ocol = lo.slab_col;
-          oval = (In*)lo.slab_val;
+        // ---- 4. emit row l in column order (exact); learned: count it ---------
+        if (!lo.active) {
+          const int64_t orow = A.perm[p0 + l];
+          const int64_t out0 = C.rp[orow], expect = C.rp[orow + 1] - out0;
+          const int64_t nn = emit_row<DT>(al, fl, srt, n_out, C.col, (In*)C.val, out0, expect);
+          if (nn != expect && lane == 0) raise(st, DEV_INTERNAL, 33, orow);
         } else {
-          out0 = C.rp[orow];
-          expect = C.rp[orow + 1] - out0;
+          const int nn = count_row(fl, n_out);
+          if (lane == 0) rcnt[l] = nn;
         }
-        int64_t nn = 0;
-        for (int x0 = 0; x0 < n_out; x0 += 32) {
-          const int x = x0 + lane;
-          const bool f = x < n_out && fl[x];
-          const unsigned bal = __ballot_sync(FULL, f);
-          const int64_t pos = nn + __popc(bal & lt);
-          if (f && pos < expect) {
-            ocol[out0 + pos] = srt[x];
-            oval[out0 + pos] = VT<DT>::out(al[x]);
+      }
+      if (lo.active) {
+        // learned: one reservation from the slab pool for the whole cluster, then
+        // each row at the pool offset plus the counts of the rows before it
+        group_sync(gw, gid);
+        if (gt == 0) {
+          int64_t tot = 0;
+          for (int q = 0; q < K; ++q) tot += rcnt[q];
+          const int64_t base = pool_reserve(lo, tot);
+          *sbase = base;
+          if (base < 0) {  // pool exhausted: the exact path computes this cluster
+            lo.flag[c] = 1;
+            lo.flist[atomicAdd(lo.flist_count, 1)] = c;
           }
-          nn += __popc(bal);
         }
-        if (lo.active) {
-          if (lane == 0) {
-            lo.cnt[orow + 1] = nn;
-            if (nn > expect) raise(st, DEV_INTERNAL, 34, orow);
+        group_sync(gw, gid);
+        const int64_t base = *sbase;
+        if (base >= 0) {
+          for (int l = wg; l < K; l += gw) {
+            int64_t off = base;
+            for (int q = 0; q < l; ++q) off += rcnt[q];
+            const int64_t nn = emit_row<DT>(acc + l * n_out, flg + l * n_out, srt, n_out, lo.slab_col,
+                                            (In*)lo.slab_val, off, rcnt[l]);
+            if (lane == 0) {
+              const int64_t orow = A.perm[p0 + l];
+              lo.slab_off[p0 + l] = off;
+              lo.cnt[orow + 1] = nn;
+            }
           }
-        } else if (nn != expect && lane == 0) {
-          raise(st, DEV_INTERNAL, 33, orow);
         }
       }
     }

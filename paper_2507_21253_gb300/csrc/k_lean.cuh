@@ -362,41 +362,41 @@ __global__ void __launch_bounds__(256) k_cluster_lean(AClusterView A, BView B, C
     }
 
     // ---- 4. emit each row in column order ------------------------------------
-    for (int l = 0; l < K; ++l) {
-      const int64_t orow = A.perm[p0 + l];
-      int64_t out0, expect;
-      int32_t* ocol = C.col;
-      In* oval = (In*)C.val;
-      if (lo.active) {
-        out0 = lo.slab_off[p0 + l];
-        expect = lo.slab_off[p0 + l + 1] - out0;
-        ocol = lo.slab_col;
-        oval = (In*)lo.slab_val;
-      } else {
-        out0 = C.rp[orow];
-        expect = C.rp[orow + 1] - out0;
+    if (!lo.active) {
+      for (int l = 0; l < K; ++l) {
+        const int64_t orow = A.perm[p0 + l];
+        const int64_t out0 = C.rp[orow], expect = C.rp[orow + 1] - out0;
+        const int64_t nn = emit_row<DT>(acc + l * n_out, flg + l * n_out, srt, n_out, C.col, (In*)C.val, out0, expect);
+        if (nn != expect && lane == 0) raise(st, DEV_INTERNAL, 42, orow);
       }
-      const Acc* al = acc + l * n_out;
-      const uint8_t* fl = flg + l * n_out;
-      int64_t nn = 0;
-      for (int x0 = 0; x0 < n_out; x0 += 32) {
-        const int x = x0 + lane;
-        const bool f = x < n_out && fl[x];
-        const unsigned bal = __ballot_sync(FULL, f);
-        const int64_t pos = nn + __popc(bal & lt);
-        if (f && pos < expect) {
-          ocol[out0 + pos] = srt[x];
-          oval[out0 + pos] = VT<DT>::out(al[x]);
-        }
-        nn += __popc(bal);
+    } else {
+      // learned: lane l holds row l's count; one reservation from the slab pool for the
+      // cluster, then each row at the pool offset plus the counts of the rows before it
+      int my = 0;
+      for (int l = 0; l < K; ++l) {
+        const int nn = count_row(flg + l * n_out, n_out);
+        if (lane == l) my = nn;
       }
-      if (lo.active) {
+      const int ex = warp_incl_scan(my) - my;
+      const int tot = __shfl_sync(FULL, ex + my, 31);
+      int64_t base = 0;
+      if (lane == 0) base = pool_reserve(lo, tot);
+      base = __shfl_sync(FULL, base, 0);
+      if (base < 0) {  // pool exhausted: the exact path computes this cluster
         if (lane == 0) {
-          lo.cnt[orow + 1] = nn;
-          if (nn > expect) raise(st, DEV_INTERNAL, 41, orow);
+          lo.flag[c] = 1;
+          lo.flist[atomicAdd(lo.flist_count, 1)] = c;
         }
-      } else if (nn != expect && lane == 0) {
-        raise(st, DEV_INTERNAL, 42, orow);
+      } else {
+        for (int l = 0; l < K; ++l) {
+          const int64_t off = base + __shfl_sync(FULL, ex, l);
+          const int n = __shfl_sync(FULL, my, l);
+          emit_row<DT>(acc + l * n_out, flg + l * n_out, srt, n_out, lo.slab_col, (In*)lo.slab_val, off, n);
+          if (lane == 0) {
+            lo.slab_off[p0 + l] = off;
+            lo.cnt[A.perm[p0 + l] + 1] = n;
+          }
+        }
       }
     }
     __syncwarp();

@@ -7,7 +7,7 @@
 //    data-parallel by a cooperative grid with a fixed summation order
 //    (deterministic),
 //  * capacities n_cap = ceil(margin * expm1(yhat)) per cluster, binning,
-//    slab offsets, and the compaction of slab rows into CSR.
+//    the slab pool's size, and the compaction of slab rows into CSR.
 #include "k_launch.cuh"
 
 namespace sgc {
@@ -76,10 +76,21 @@ __global__ void __launch_bounds__(256) k_features(AClusterView A, BView B, float
   }
 }
 
-// training targets log1p(n_out) from the symbolic phase's per-cluster record; -1 if absent
-__global__ void k_targets(const int32_t* nout, int64_t ncl, float* y) {
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncl; c += (int64_t)gridDim.x * blockDim.x)
-    y[c] = nout[c] >= 0 ? log1pf((float)nout[c]) : -1.0f;
+// Training targets from a completed symbolic phase (thread per cluster):
+// log1p(n_out) from the cluster kernel's record (a one-row cluster: its row's
+// count), -1 where absent; log1p(nnz_c), the cluster's rows' counts summed.
+__global__ void k_targets(AClusterView A, const int32_t* nout, const int64_t* c_rp, float* y, float* y_tot) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < A.ncl; c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p0 = A.cptr[c], p1 = A.cptr[c + 1];
+    int64_t tot = 0;
+    for (int64_t p = p0; p < p1; ++p) {
+      const int64_t r = A.perm[p];
+      tot += c_rp[r + 1] - c_rp[r];
+    }
+    const int32_t no = nout[c];
+    y[c] = no >= 0 ? log1pf((float)no) : (p1 - p0 == 1 ? log1pf((float)tot) : -1.0f);
+    if (y_tot) y_tot[c] = log1pf((float)tot);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -290,11 +301,12 @@ __device__ __forceinline__ int32_t capacity_of(float yhat, int64_t bound, float 
   return (int32_t)min64(bound, cap);
 }
 
-__global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, const float* yhat, const int32_t* ncap_in,
-                                                     float margin, float scale, const int32_t* uc, const int32_t* h_pos,
-                                                     int32_t* ncap_out, int64_t* capw, int32_t* flag, int32_t* flist,
-                                                     int32_t* flist_count, BinOut lb, int in_bytes, int acc_bytes,
-                                                     int bulk, int cl_load, int lean) {
+__global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, const float* yhat, const float* yhat_tot,
+                                                     const int32_t* ncap_in, float margin, float margin_tot,
+                                                     float scale, const int32_t* uc, const int32_t* h_pos,
+                                                     int32_t* ncap_out, int64_t* tot_cap, int32_t* flag,
+                                                     int32_t* flist, int32_t* flist_count, BinOut lb, int in_bytes,
+                                                     int acc_bytes, int bulk, int cl_load, int lean) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   for (int64_t c = gw; c < A.ncl; c += nwarps) {
@@ -306,13 +318,19 @@ __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, co
     const int64_t bound = min64(U, B.ncols);
     const int32_t ncap = ncap_in ? (int32_t)min64(ncap_in[c], bound) : capacity_of(yhat[c], bound, margin, scale);
     int cls = -1, lcls = -1;
-    if (K > 1 && U < (1ll << 28) && T < (1ll << 24)) {  // one-row clusters: row kernels, exact path
+    if (U < (1ll << 28) && T < (1ll << 24)) {  // clusters of every size, one-row clusters included
       const int LH = cluster_table_log2(false, ncap, cl_load);
       if (lean) lcls = lean_class(lean_layout(T, nva, LH, ncap, K, in_bytes, acc_bytes).total);
       if (lcls < 0) cls = warp_class(warp_layout(false, T, U, nva, LH, ncap, K, in_bytes, acc_bytes, bulk != 0).total);
     }
     const bool take = cls >= 0 || lcls >= 0;
+    // the cluster's share of the slab: its predicted nnz, capped by the bound sum_l min(h_l, n_cap)
+    int64_t hb = lane < K ? min64((int64_t)h_pos[p0 + lane], (int64_t)ncap) : 0;
+    hb = warp_sum(hb);
     if (lane == 0) {
+      int64_t share = hb;
+      if (yhat_tot) share = min64(hb, (int64_t)capacity_of(yhat_tot[c], hb, margin_tot, scale));
+      tot_cap[c + 1] = take ? share : 0;
       ncap_out[c] = ncap;
       flag[c] = take ? 0 : 1;
       if (lcls >= 0) {
@@ -325,7 +343,6 @@ __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, co
         flist[atomicAdd(flist_count, 1)] = (int32_t)c;
       }
     }
-    if (lane < K) capw[p0 + lane + 1] = take ? min64((int64_t)h_pos[p0 + lane], (int64_t)ncap) : 0;
   }
 }
 
@@ -374,9 +391,10 @@ cudaError_t features_run(const AClusterView& A, const BView& B, float* X, int32_
   return cudaGetLastError();
 }
 
-cudaError_t targets_run(const int32_t* nout, int64_t ncl, float* y, int sms, cudaStream_t s) {
-  if (ncl <= 0) return cudaSuccess;
-  k_targets<<<grid_for(ncl, 256, sms, 8), 256, 0, s>>>(nout, ncl, y);
+cudaError_t targets_run(const AClusterView& A, const int32_t* nout, const int64_t* c_rp, float* y, float* y_tot,
+                        int sms, cudaStream_t s) {
+  if (A.ncl <= 0) return cudaSuccess;
+  k_targets<<<grid_for(A.ncl, 256, sms, 8), 256, 0, s>>>(A, nout, c_rp, y, y_tot);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -423,20 +441,21 @@ cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, 
   return e;
 }
 
-cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const int32_t* ncap_in,
-                            float margin, float scale, const int32_t* uc, const int32_t* h_pos, int32_t* ncap_out,
-                            int64_t* capw, int32_t* flag, int32_t* flist, int32_t* flist_count, const BinOut& lb,
-                            int in_bytes, int acc_bytes, int bulk, int cl_load, int lean, int sms, cudaStream_t s) {
+cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const float* yhat_tot,
+                            const int32_t* ncap_in, float margin, float margin_tot, float scale, const int32_t* uc,
+                            const int32_t* h_pos, int32_t* ncap_out, int64_t* tot_cap, int32_t* flag, int32_t* flist,
+                            int32_t* flist_count, const BinOut& lb, int in_bytes, int acc_bytes, int bulk, int cl_load,
+                            int lean, int sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(lb.count, 0, sizeof(int32_t) * NBIN_ALL, s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(flist_count, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(capw, 0, sizeof(int64_t), s);
+  e = cudaMemsetAsync(tot_cap, 0, sizeof(int64_t), s);
   if (e != cudaSuccess) return e;
   if (A.ncl <= 0) return cudaSuccess;
-  k_learned_bin<<<grid_for(A.ncl, 8, sms, 8), 256, 0, s>>>(A, B, yhat, ncap_in, margin, scale, uc, h_pos, ncap_out,
-                                                            capw, flag, flist, flist_count, lb, in_bytes, acc_bytes,
-                                                            bulk, cl_load, lean);
+  k_learned_bin<<<grid_for(A.ncl, 8, sms, 8), 256, 0, s>>>(A, B, yhat, yhat_tot, ncap_in, margin, margin_tot, scale,
+                                                            uc, h_pos, ncap_out, tot_cap, flag, flist, flist_count, lb,
+                                                            in_bytes, acc_bytes, bulk, cl_load, lean);
   note_launches(1);
   return cudaGetLastError();
 }

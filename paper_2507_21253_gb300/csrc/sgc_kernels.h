@@ -68,14 +68,22 @@ struct BinOut {
 struct LearnedOut {
   int active;                // 0: exact numeric into C; 1: learned (fields below)
   const int32_t* ncap;       // per cluster: capacity for the cluster's output columns
-  const int64_t* slab_off;   // per position (cluster order), nrows+1: slab offsets
+  int64_t* slab_off;         // per position (cluster order): where the row was written in the slab
   int32_t* slab_col;
   void* slab_val;
   int64_t* cnt;              // per original row r: row count at cnt[r + 1]
   int32_t* flag;             // per cluster: 0 = done, 1 = overflow (exact path)
   int32_t* flist;            // overflow cluster list (appended) ...
   int32_t* flist_count;      // ... and its count
+  unsigned long long* pool;  // slab elements reserved so far (one atomic per cluster)
+  const int64_t* pool_cap;   // slab capacity (elements)
 };
+
+// Learned mode: reserves `total` slab elements; the pool offset, or -1 when the pool is exhausted.
+__device__ __forceinline__ int64_t pool_reserve(const LearnedOut& lo, int64_t total) {
+  const unsigned long long base = atomicAdd(lo.pool, (unsigned long long)total);
+  return (int64_t)base + total <= *lo.pool_cap ? (int64_t)base : (int64_t)-1;
+}
 
 struct Launch {
   cudaStream_t s;
@@ -116,17 +124,19 @@ cudaError_t add_offset_i64(const int64_t* src, int64_t* dst, int64_t n, int64_t 
 // k_learned.cu
 cudaError_t features_run(const AClusterView& A, const BView& B, float* X, int32_t* uc, int32_t* h_pos, int sms,
                          cudaStream_t s);
-cudaError_t targets_run(const int32_t* nout, int64_t ncl, float* y, int sms, cudaStream_t s);
+cudaError_t targets_run(const AClusterView& A, const int32_t* nout, const int64_t* c_rp, float* y, float* y_tot,
+                        int sms, cudaStream_t s);
 cudaError_t mlp_infer_run(const float* params, const float* X, int64_t n, float* yhat, int sms, cudaStream_t s);
 size_t mlp_train_smem();
 size_t mlp_train_ws_bytes(int B);
 cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, int64_t steps, int B, float lr,
                           const float* init, float* params_out, float* loss_out, int grad_only, float* grad_out,
                           void* ws, cudaStream_t s);
-cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const int32_t* ncap_in,
-                            float margin, float scale, const int32_t* uc, const int32_t* h_pos, int32_t* ncap_out,
-                            int64_t* capw, int32_t* flag, int32_t* flist, int32_t* flist_count, const BinOut& lb,
-                            int in_bytes, int acc_bytes, int bulk, int cl_load, int lean, int sms, cudaStream_t s);
+cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const float* yhat_tot,
+                            const int32_t* ncap_in, float margin, float margin_tot, float scale, const int32_t* uc,
+                            const int32_t* h_pos, int32_t* ncap_out, int64_t* tot_cap, int32_t* flag, int32_t* flist,
+                            int32_t* flist_count, const BinOut& lb, int in_bytes, int acc_bytes, int bulk, int cl_load,
+                            int lean, int sms, cudaStream_t s);
 cudaError_t compact_run(const AClusterView& A, const int32_t* flag, const int64_t* slab_off, const int32_t* slab_col,
                         const void* slab_val, int val_bytes, const int64_t* c_rp, int32_t* ccol, void* cval, int sms,
                         cudaStream_t s);

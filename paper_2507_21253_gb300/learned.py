@@ -1,10 +1,11 @@
-"""Training and checkpoints of the per-cluster output-column predictor.
+"""Training and checkpoints of the per-cluster output-size predictors.
 
 Orchestration only: each step calls the library (hierarchical clustering,
 CSR_Cluster build, symbolic phase, features, targets, the training kernel);
 the arithmetic runs in libsgc's kernels.  Training data are the symbolic
-phase's own per-cluster output-column counts on seeded smaller instances of
-the workload's generator.
+phase's own per-cluster counts on seeded smaller instances of the workload's
+generator: output columns (n_out, which sizes a cluster's table) and output
+nonzeros (nnz_c, which sizes the slab).
 """
 from __future__ import annotations
 
@@ -15,17 +16,17 @@ from . import sgc, synth
 
 def instance_data(A, jacc_th: float = sgc.JACC_TH, max_cluster: int = sgc.MAX_CLUSTER, device="cuda",
                   parallel: bool = False):
-    """(features [ncl, 8], targets [ncl]) of one instance, clustered hierarchically
-    (the serial merge, or the round-parallel one if `parallel`)."""
+    """(features [ncl, 8], log1p(n_out) [ncl], log1p(nnz_c) [ncl]) of one instance, clustered
+    hierarchically (the serial merge, or the round-parallel one if `parallel`)."""
     Ad = sgc.DeviceCsr.from_host(A, device)
     hc = sgc.hcluster_reorder_parallel if parallel else sgc.hcluster_reorder
     perm, cptr = hc(Ad, jacc_th, max_cluster)
     Acl = sgc.csr_cluster_build(Ad, perm, cptr, sgc.LAYOUT_MASKED)
     ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad), device)
-    sgc.spgemm_symbolic(Acl, Ad, ws)
+    rp, _ = sgc.spgemm_symbolic(Acl, Ad, ws)
     X = sgc.cluster_features(Acl, Ad)
-    y = sgc.nnz_predictor_targets(Acl, Ad, ws)
-    return X, y
+    y, yt = sgc.nnz_predictor_targets(Acl, Ad, ws, rp)
+    return X, y, yt
 
 
 def train(make_instance, seeds, epochs: int = 4, batch: int = 256, lr: float = 2e-3, init_seed: int = 1,
@@ -37,24 +38,28 @@ def train(make_instance, seeds, epochs: int = 4, batch: int = 256, lr: float = 2
 
 def train_on(instances, epochs: int = 4, batch: int = 256, lr: float = 2e-3, init_seed: int = 1, device="cuda",
              parallel: bool = False, info: dict | None = None):
-    """Trains on the given host matrices (each squared); returns (params, per-step loss).
-    `info`, when given, receives the number of samples (clusters) and of steps."""
-    feats, ys = [], []
+    """Trains both parameter sets on the given host matrices (each squared): set 0
+    predicts log1p(n_out) (the cluster's output columns: table and accumulator
+    capacity), set 1 log1p(nnz_c) (its output nonzeros: the slab).  Returns
+    (params = set 0 then set 1, per-step loss of set 0).  `info`, when given,
+    receives the number of samples (clusters) and of steps."""
+    feats, ys, yts = [], [], []
     for A in instances:
-        X, y = instance_data(A, device=device, parallel=parallel)
+        X, y, yt = instance_data(A, device=device, parallel=parallel)
         feats.append(X)
         ys.append(y)
+        yts.append(yt)
     X = torch.cat(feats)
-    y = torch.cat(ys)
     n = int(X.shape[0])
     order = synth.minibatch_order(n, epochs, init_seed)
     steps = order.size // batch
     order_d = torch.from_numpy(order[: steps * batch]).to(device)
     init = torch.from_numpy(synth.mlp_init(init_seed)).to(device)
-    params, loss = sgc.nnz_predictor_train(X, y, order_d, steps, batch, lr, init)
+    p_out, loss = sgc.nnz_predictor_train(X, torch.cat(ys), order_d, steps, batch, lr, init)
+    p_tot, _ = sgc.nnz_predictor_train(X, torch.cat(yts), order_d, steps, batch, lr, init, with_loss=False)
     if info is not None:
         info.update(samples=n, steps=steps)
-    return params, loss
+    return torch.cat([p_out, p_tot]), loss
 
 
 def save(path: str, params: torch.Tensor, meta: str = "") -> None:

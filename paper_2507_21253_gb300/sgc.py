@@ -55,7 +55,8 @@ class ClusterStruct(ctypes.Structure):
 
 
 class Predictor(ctypes.Structure):
-    _fields_ = [("params", vp), ("margin", ctypes.c_float), ("scale", ctypes.c_float), ("ncap", vp)]
+    _fields_ = [("params", vp), ("margin", ctypes.c_float), ("scale", ctypes.c_float), ("ncap", vp),
+                ("params_total", vp), ("margin_total", ctypes.c_float), ("reserved", i32)]
 
 
 class Options(ctypes.Structure):
@@ -106,7 +107,7 @@ _c = {
                                     vp),
     "cluster_features": _sig("cluster_features", P(ClusterStruct), P(CsrStruct), vp, vp),
     "nnz_predictor_targets": _sig("nnz_predictor_targets", P(ClusterStruct), P(CsrStruct), vp, ctypes.c_size_t, vp,
-                                  vp),
+                                  vp, vp, vp),
     "nnz_predictor_infer": _sig("nnz_predictor_infer", vp, vp, i64, vp, vp),
     "nnz_predictor_train_workspace_size": _sig("nnz_predictor_train_workspace_size", i32, P(ctypes.c_size_t)),
     "nnz_predictor_grad": _sig("nnz_predictor_grad", vp, vp, vp, vp, i32, vp, vp, vp, ctypes.c_size_t, vp),
@@ -495,12 +496,15 @@ def cluster_features(A: DeviceCsrCluster, B: DeviceCsr) -> torch.Tensor:
     return X
 
 
-def nnz_predictor_targets(A: DeviceCsrCluster, B: DeviceCsr, ws: Workspace) -> torch.Tensor:
-    """log1p(n_out) per cluster from a completed symbolic phase (-1 where not recorded)."""
+def nnz_predictor_targets(A: DeviceCsrCluster, B: DeviceCsr, ws: Workspace, c_row_ptr: torch.Tensor):
+    """From a completed symbolic phase (its workspace and row pointer): per cluster
+    log1p(n_out) (-1 where not recorded) and log1p(nnz_c), the cluster's output nonzeros."""
     y = torch.empty(A.nclusters, dtype=torch.float32, device=B.row_ptr.device)
+    yt = torch.empty(A.nclusters, dtype=torch.float32, device=B.row_ptr.device)
     a, b = A.struct(), B.struct()
-    _call("nnz_predictor_targets", ctypes.byref(a), ctypes.byref(b), ws.ptr, ws.nbytes, _ptr(y), _stream())
-    return y
+    _call("nnz_predictor_targets", ctypes.byref(a), ctypes.byref(b), ws.ptr, ws.nbytes, _ptr(c_row_ptr), _ptr(y),
+          _ptr(yt), _stream())
+    return y, yt
 
 
 def nnz_predictor_infer(params: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
@@ -569,15 +573,24 @@ class LearnedSpgemm:
     """The symbolic-free learned path: plan (capacities), phase 1 (slab + row counts), phase 2 (C)."""
 
     def __init__(self, A: DeviceCsrCluster, B: DeviceCsr, params=None, margin=1.25, scale=1.0, ncap=None,
-                 opt: Options | None = None):
+                 opt: Options | None = None, margin_total: float = 0.0):
+        """params: NPARAM values (the n_out predictor) or 2 * NPARAM (then also the nnz_c
+        predictor that sizes the slab); ncap: explicit per-cluster capacities instead."""
         self.A, self.B, self.opt = A, B, opt
         n = ctypes.c_size_t()
         a, b = A.struct(), B.struct()
         _call("spgemm_learned_workspace_size", ctypes.byref(a), ctypes.byref(b), _o(opt), ctypes.byref(n))
         self.ws = Workspace(n.value, B.row_ptr.device)
         self.params, self.ncap = params, ncap
-        self.pred = Predictor(_ptr(params) if params is not None else vp(0), float(margin), float(scale),
-                              _ptr(ncap) if ncap is not None else vp(0))
+        p_out = p_tot = vp(0)
+        if params is not None:
+            if params.numel() not in (NPARAM, 2 * NPARAM):
+                raise ValueError(f"params: {NPARAM} or {2 * NPARAM} values")
+            p_out = _ptr(params)
+            if params.numel() == 2 * NPARAM:
+                p_tot = vp(params.data_ptr() + 4 * NPARAM)
+        self.pred = Predictor(p_out, float(margin), float(scale), _ptr(ncap) if ncap is not None else vp(0), p_tot,
+                              float(margin_total), 0)
         self.c_row_ptr = torch.empty(A.nrows + 1, dtype=torch.int64, device=B.row_ptr.device)
         self.slab_col = self.slab_val = None
         self.plan()

@@ -101,16 +101,20 @@ def test_targets_are_union_counts(sgc):
     A = synth.planted_groups(2048, 4004)
     Ad, Acl, perm, cptr = clustered(sgc, A)
     ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad))
-    sgc.spgemm_symbolic(Acl, Ad, ws)
-    y = sgc.nnz_predictor_targets(Acl, Ad, ws).cpu().numpy()
+    crp, _ = sgc.spgemm_symbolic(Acl, Ad, ws)
+    y, yt = sgc.nnz_predictor_targets(Acl, Ad, ws, crp)
+    y, yt = y.cpu().numpy(), yt.cpu().numpy()
     rp, col, _, _ = og.spgemm(A, A, want_mag=False)
     rows = [col[rp[r]:rp[r + 1]] for r in range(A.nrows)]
     n_out = ol.union_counts(occ.build(A, perm, cptr), rows)
     K = np.diff(cptr)
-    assert np.all(y[K == 1] == -1)        # one-row clusters run in the row kernels
     ok = y >= 0
+    assert ok[K == 1].all()               # a one-row cluster's n_out is its row's count
     assert ok[K > 1].mean() > 0.9
     assert np.allclose(y[ok], np.log1p(n_out[ok]).astype(np.float32), rtol=1e-6)
+    counts = np.diff(rp)
+    nnz_c = np.array([counts[perm[cptr[c]:cptr[c + 1]]].sum() for c in range(K.size)])
+    assert np.allclose(yt, np.log1p(nnz_c).astype(np.float32), rtol=1e-6)
 
 
 LEARNED_CASES = [("planted_f64", lambda: synth.planted_groups(2048, 4005)),
@@ -137,9 +141,8 @@ def test_learned_explicit_caps_overflow_rule(sgc, name, make, kernel):
     L = sgc.LearnedSpgemm(Acl, Ad, ncap=torch.from_numpy(caps).cuda(), margin=1.0,
                           opt=sgc.options(cluster_kernel=kernel))
     C = L.run()
-    K = np.diff(cptr)
-    # clusters sent to the exact path: the overflowing ones, and every one-row cluster
-    expect_over = int((ol.overflowing_clusters(n_out, caps_eff) & (K > 1)).sum() + (K == 1).sum())
+    # clusters sent to the exact path: the overflowing ones (one-row clusters are planned too)
+    expect_over = int(ol.overflowing_clusters(n_out, caps_eff).sum())
     if name == "rmat_i64":
         assert L.n_overflow >= expect_over  # hub clusters too large for shared memory also take the exact path
     else:
@@ -178,7 +181,7 @@ def test_training_gain_over_untrained(sgc):
     assert loss[-20:].mean() < 0.2 * loss[:20].mean()
     A = synth.planted_groups(4096, 4100)
     Ad, Acl, perm, cptr = clustered(sgc, A, how="hc")
-    X, y = learned.instance_data(A)
+    X, y, _ = learned.instance_data(A)
     init = torch.from_numpy(synth.mlp_init(1)).cuda()
     ok = y >= 0
     err_t = (sgc.nnz_predictor_infer(params, X) - y)[ok].abs().mean().item()
@@ -189,10 +192,28 @@ def test_training_gain_over_untrained(sgc):
     Ct, Cu = Lt.run(), Lu.run()
     compare(Ct, A, A, exact_f64=True)
     compare(Cu, A, A, exact_f64=True)
-    K = np.diff(cptr)
-    single = int((K == 1).sum())            # one-row clusters always take the exact path
-    assert Lt.n_overflow - single < 0.1 * int((K > 1).sum())
+    assert Lt.n_overflow < 0.1 * Acl.nclusters
     assert Lt.n_overflow < Lu.n_overflow or Lt.slab_elems < Lu.slab_elems
+    # the trained nnz_c predictor sizes the slab close to nnz(C) (margin 1.25 here)
+    assert Lt.slab_elems <= 1.45 * Lt.nnz
+
+
+def test_pool_exhaustion_goes_to_the_exact_path(sgc):
+    """Exact column capacities but a slab predictor scaled far down: the slab pool runs
+    out, every cluster that finds it exhausted is computed by the exact path, C exact."""
+    import torch
+    A = synth.stencil27_3d(12, 11, 10, seed=8)
+    Ad, Acl, perm, cptr = clustered(sgc, A, how=8)
+    ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad))
+    crp, _ = sgc.spgemm_symbolic(Acl, Ad, ws)
+    y, _ = sgc.nnz_predictor_targets(Acl, Ad, ws, crp)
+    ncap = torch.expm1(y).round().to(torch.int32)
+    init = torch.from_numpy(synth.mlp_init(2)).cuda()
+    params = torch.cat([init, init])               # set 1 (the slab predictor) used at scale 0.01
+    L = sgc.LearnedSpgemm(Acl, Ad, params=params, ncap=ncap, margin=1.0, scale=0.01)
+    C = L.run()
+    compare(C, A, A, exact_f64=True)
+    assert L.n_overflow > 0 and L.slab_elems < 0.5 * L.nnz
 
 
 def test_checkpoint_round_trip(sgc, tmp_path):
@@ -210,15 +231,16 @@ def test_checkpoint_round_trip(sgc, tmp_path):
     assert torch.equal(back, params) and meta == "stencil27 epochs=2"
     X = sgc.cluster_features(*_clustered(sgc, synth.stencil27_3d(14, 14, 14, seed=9)))
     assert torch.equal(sgc.nnz_predictor_infer(back, X), sgc.nnz_predictor_infer(params, X))
-    two = torch.cat([params, params * 0.5])                       # two parameter sets in one file
-    sgc.nnz_predictor_save(f, two)
-    assert torch.equal(sgc.nnz_predictor_load(f)[0], two)
-    p = params.cpu().numpy()
+    assert params.numel() == 2 * sgc.NPARAM                       # the n_out and nnz_c sets
+    one = params[:sgc.NPARAM].contiguous()
+    sgc.nnz_predictor_save(f, one)
+    assert torch.equal(sgc.nnz_predictor_load(f)[0], one)
+    p = one.cpu().numpy()
     v1 = str(tmp_path / "v1.bin")
     with open(v1, "wb") as fh:                                    # one set, magic of the earlier format
         fh.write(b"SGCNNZP1" + struct.pack("<II", p.size, 3) + b"abc" + p.tobytes())
     back1, meta1 = sgc.nnz_predictor_load(v1)
-    assert torch.equal(back1, params) and meta1 == "abc"
+    assert torch.equal(back1, one) and meta1 == "abc"
     with open(v1, "r+b") as fh:
         fh.truncate(100)
     with pytest.raises(sgc.SgcError) as e:

@@ -64,8 +64,8 @@ def test_learned_wait_gives_up_then_recovers(sgc):
     A, Ad, Acl = _stencil(sgc)
     # capacities: the exact output-column counts from a symbolic run
     ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad))
-    sgc.spgemm_symbolic(Acl, Ad, ws)
-    y = sgc.nnz_predictor_targets(Acl, Ad, ws)
+    rp, _ = sgc.spgemm_symbolic(Acl, Ad, ws)
+    y, _ = sgc.nnz_predictor_targets(Acl, Ad, ws, rp)
     import torch
     ncap = torch.where(y >= 0, torch.expm1(y).round(), torch.full_like(y, 1.0)).to(torch.int32)
     bad = sgc.options(staging=sgc.STAGING_BULK, wait_polls=-1)
