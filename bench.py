@@ -582,11 +582,39 @@ def measure_product(cx: Ctx, name: str, A, B, train_mats, steps: int, warmup: in
     res["preprocess"] = {"hcluster_s": round(t_hc, 3), "csr_cluster_build_s": round(t_build, 4),
                          "in_steps": round((t_hc + t_build) / (head_ms * 1e-3), 1)}
     res["csr_cluster_bytes_over_csr"] = memory_overhead(cx, Ad, A, perm, cptr)
+    if square and A.nrows >= 1 << 20:      # the large workloads: does a cluster order by locality pay?
+        res["cluster_order_bfs"] = measure_order(cx, Ad, Bd, perm, cptr, opt, steps, warmup, step_ms,
+                                                 float(np.mean(num_ms)))
     res["_internal"] = {"Ad": Ad, "Bd": Bd, "perm": perm, "cptr": cptr, "opt": opt, "num_bytes": num_bytes,
                         "params": params, "exact_launches": exact_launches, "clk_exact": clk_exact,
                         "num_avg": num_avg, "launches": launches, "clk": clk, "head_ms": head_ms,
                         "step_ms": step_ms, "row_ms": row_ms, "nnz": nnz, "square": square}
     return res
+
+
+def measure_order(cx: Ctx, Ad, Bd, perm, cptr, opt, steps: int, warmup: int, exact_ms: float, num_ms: float) -> dict:
+    """The exact clustered step with the clusters reordered by BFS distance over A's graph
+    (cluster_order_bfs): does an order by locality pay on this GPU?"""
+    torch, sgc = cx.torch, cx.sgc
+    t0 = time.perf_counter()
+    p2, c2, levels = sgc.cluster_order_bfs(Ad, perm, cptr)
+    torch.cuda.synchronize()
+    t_order = time.perf_counter() - t0
+    Acl2 = sgc.csr_cluster_build(Ad, p2, c2, sgc.LAYOUT_MASKED)
+    ws2 = sgc.Workspace(sgc.spgemm_workspace_size(Acl2, Bd, opt), cx.dev)
+    rp2, nnz2 = sgc.spgemm_symbolic(Acl2, Bd, ws2, opt)
+    C2 = sgc.spgemm_numeric(Acl2, Bd, rp2, nnz2, ws2, opt)
+    f = [lambda: sgc.spgemm_symbolic(Acl2, Bd, ws2, opt, c_row_ptr=rp2, sync=False),
+         lambda: sgc.spgemm_numeric(Acl2, Bd, rp2, nnz2, ws2, opt, C=C2)]
+    cx.timed(f, warmup)
+    osym, onum = cx.timed(f, steps)
+    sgc.workspace_status(ws2)
+    o_ms = float(np.mean([a + b for a, b in zip(osym, onum)]))
+    del C2, ws2, Acl2
+    torch.cuda.empty_cache()
+    return {"levels": levels, "order_s": round(t_order, 3), "exact_ms": round(o_ms, 4),
+            "numeric_ms": round(float(np.mean(onum)), 4),
+            "speedup_vs_unordered": round(exact_ms / o_ms, 4), "numeric_speedup": round(num_ms / float(np.mean(onum)), 4)}
 
 
 def measure_batched(cx: Ctx, mats, steps: int, warmup: int) -> dict:
@@ -849,6 +877,7 @@ def run_ours(args, rank: int, world: int, local_rank: int, inputs: dict):
             "alternative_clustering": alt,
             "preprocess": res["preprocess"],
             "csr_cluster_bytes_over_csr": res["csr_cluster_bytes_over_csr"],
+            "cluster_order_bfs": res.get("cluster_order_bfs"),
             "configs": configs,
             "paper_context": PAPER_CONTEXT,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches or 0), "clocks": clocks,

@@ -349,6 +349,24 @@ int cluster_fixed_length(int64_t nrows, int32_t K, int32_t* perm, int64_t* clust
                          void* stream);
 int cluster_variable_length(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm,
                             int64_t* cluster_ptr, int64_t* nclusters_host, void* stream);
+/* Cluster ordering by locality (the question of Sec. 4.3, whether a reordering
+ * and the cluster-wise product compose, for the order in which clusters are
+ * processed): reorders the clusters given by perm / cluster_ptr (device,
+ * nrows and nclusters + 1 entries, as the hcluster_* calls return them) in
+ * place so that clusters near each other in A's graph come close together,
+ * for the B rows they share to hit in L2.  A must be square; its pattern is
+ * the graph.  A breadth-first search on the device from row perm[0] gives
+ * every row its distance (unique, so the result does not depend on timing);
+ * a cluster's key is the smallest distance of its rows (rows not reached rank
+ * last), and the clusters are sorted by key, ties in their previous order, on
+ * the host.  Rows inside a cluster keep their order; C does not depend on the
+ * order of clusters (build CSR_Cluster again after reordering).
+ * *nlevels_host (nullable) receives the number of BFS levels.  ws: device
+ * workspace of cluster_order_workspace_size(nrows, nclusters) bytes.
+ * Synchronises (once per BFS level). */
+int cluster_order_workspace_size(int64_t nrows, int64_t nclusters, size_t* bytes);
+int cluster_order_bfs(const sgc_csr* A, int32_t* perm, int64_t* cluster_ptr, int64_t nclusters, int32_t* nlevels_host,
+                      void* ws, size_t ws_bytes, void* stream);
 int hcluster_candidates(const sgc_csr* A, float jacc_th, int32_t topk, int32_t* cand_j, int32_t* cand_inter,
                         int32_t* cand_union, void* ws, size_t ws_bytes, void* stream);
 int hcluster_reorder(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm, int64_t* cluster_ptr,

@@ -416,13 +416,7 @@ size_t mlp_train_ws_bytes(int B) {
 cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, int64_t steps, int B, float lr,
                           const float* init, float* params_out, float* loss_out, int grad_only, float* grad_out,
                           void* ws, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int G = B / TR_S;
+  const int G = B / TR_S;  // the kernel's shared memory (about 35 KB) is within the default limit
   TrainWs* w = (TrainWs*)ws;
   float* partial = (float*)((char*)ws + 256);
   cudaError_t e = cudaMemsetAsync(w, 0, sizeof(TrainWs), s);

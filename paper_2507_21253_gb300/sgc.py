@@ -103,6 +103,8 @@ _c = {
     "hcluster_reorder_parallel": _sig("hcluster_reorder_parallel", P(CsrStruct), ctypes.c_float, i32, vp, vp,
                                       P(i64), vp, ctypes.c_size_t, vp),
     "cluster_fixed_length": _sig("cluster_fixed_length", i64, i32, vp, vp, P(i64), vp),
+    "cluster_order_workspace_size": _sig("cluster_order_workspace_size", i64, i64, P(ctypes.c_size_t)),
+    "cluster_order_bfs": _sig("cluster_order_bfs", P(CsrStruct), vp, vp, i64, P(i32), vp, ctypes.c_size_t, vp),
     "cluster_variable_length": _sig("cluster_variable_length", P(CsrStruct), ctypes.c_float, i32, vp, vp, P(i64),
                                     vp),
     "cluster_features": _sig("cluster_features", P(ClusterStruct), P(CsrStruct), vp, vp),
@@ -465,6 +467,21 @@ def cluster_fixed_length(nrows: int, K: int, device="cuda"):
     ncl = i64()
     _call("cluster_fixed_length", nrows, K, _ptr(perm), _ptr(cptr), ctypes.byref(ncl), _stream())
     return perm[:nrows], cptr[:ncl.value + 1]
+
+
+def cluster_order_bfs(A: DeviceCsr, perm: torch.Tensor, cluster_ptr: torch.Tensor):
+    """Clusters reordered by the BFS distance of their rows over A's graph: returns new
+    (perm, cluster_ptr) device tensors (the inputs are not modified) and the level count."""
+    perm2, cptr2 = perm.clone(), cluster_ptr.clone()
+    ncl = int(cptr2.numel()) - 1
+    n = ctypes.c_size_t()
+    _call("cluster_order_workspace_size", A.nrows, ncl, ctypes.byref(n))
+    ws = Workspace(n.value, A.row_ptr.device)
+    lv = i32()
+    a = A.struct()
+    _call("cluster_order_bfs", ctypes.byref(a), _ptr(perm2), _ptr(cptr2), ncl, ctypes.byref(lv), ws.ptr, ws.nbytes,
+          _stream())
+    return perm2, cptr2, lv.value
 
 
 def cluster_variable_length(A: DeviceCsr, jacc_th: float = JACC_TH, max_cluster: int = MAX_CLUSTER):
