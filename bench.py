@@ -483,6 +483,16 @@ def measure_product(cx: Ctx, name: str, A, B, train_mats, steps: int, warmup: in
     res["clustered_exact"] = {"ms_per_step": round(step_ms, 4), "gflops": round(job_gflops(flops, world, step_ms), 3),
                               "phases_ms": {"symbolic": round(float(np.mean(sym_ms)), 4),
                                             "numeric": round(float(np.mean(num_ms)), 4)}}
+    if headline and not args.fused_fma:   # the same step with fused multiply-adds (within the FP64 bound)
+        opt_f = sgc.options(fused_fma=1, cluster_load_pct=args.cluster_load, cluster_kernel=args.cluster_kernel,
+                            max_warps=args.max_warps)
+        fsym, fnum = cx.timed([lambda: sgc.spgemm_symbolic(Acl, Bd, ws, opt_f, c_row_ptr=rp, sync=False),
+                               lambda: sgc.spgemm_numeric(Acl, Bd, rp, nnz, ws, opt_f, C=C)], warmup + steps)
+        sgc.workspace_status(ws)
+        f_ms = float(np.mean([a + b for a, b in zip(fsym[warmup:], fnum[warmup:])]))
+        res["clustered_exact_fused_fma"] = {"ms_per_step": round(f_ms, 4),
+                                            "gflops": round(job_gflops(flops, world, f_ms), 3),
+                                            "numeric_ms": round(float(np.mean(fnum[warmup:])), 4)}
     del C
     torch.cuda.empty_cache()
 
@@ -860,7 +870,8 @@ def run_ours(args, rank: int, world: int, local_rank: int, inputs: dict):
             "config": workload_config(name, A, B),
             "method": "clustered+learned" if res["clustered_learned"] else "clustered (exact symbolic + numeric)",
             "nnz_C": res["nnz_C"], "nclusters": res["nclusters"], "one_row_clusters": res["one_row_clusters"],
-            "clustered_exact": res["clustered_exact"], "learned": res["clustered_learned"], "rowwise": res["rowwise"],
+            "clustered_exact": res["clustered_exact"], "clustered_exact_fused_fma": res.get("clustered_exact_fused_fma"),
+            "learned": res["clustered_learned"], "rowwise": res["rowwise"],
             "speedup_vs_rowwise": round(it["row_ms"] / head_ms, 4),
             "speedup_exact_vs_rowwise": round(it["row_ms"] / it["step_ms"], 4),
             "hbm": res["hbm"],

@@ -446,15 +446,16 @@ int spgemm_graph_destroy(sgc_graph* graph);
  *     table and accumulators; with params_total, nnz_hat_c = ceil(
  *     margin_total * scale * max(expm1(yhat_total), 0)), capped by the bound
  *     sum_l min(h_l, n_cap) (h_l = min(ub_l, ncols(B))), which is used instead
- *     when params_total is NULL.  The slab is one pool of sum_c nnz_hat_c
- *     elements, returned in *slab_elems_host.  Clusters of every size,
+ *     when params_total is NULL.  The slab holds sum_c nnz_hat_c elements,
+ *     returned in *slab_elems_host, split into 64 sub-pools: cluster c draws
+ *     from sub-pool c mod 64, which holds the summed nnz_hat of its clusters.  Clusters of every size,
  *     one-row clusters included, are planned this way; a cluster whose
  *     working set exceeds shared memory goes to the exact path.  Synchronises.
  *   phase1: one cluster-wise pass computes every planned cluster whose n_out
- *     <= n_cap, counts its rows, reserves their total from the pool with one
- *     atomic and writes the rows there (positions in the pool depend on
+ *     <= n_cap, counts its rows, reserves their total from its sub-pool with
+ *     one atomic and writes the rows there (positions in the slab depend on
  *     timing, C does not); a cluster with more output columns than n_cap
- *     (an under-prediction), or one that finds the pool exhausted, is
+ *     (an under-prediction), or one that finds its sub-pool exhausted, is
  *     flagged and its rows go through the exact symbolic pass; c_row_ptr
  *     (nrows+1) is C's row pointer; *c_nnz_host = nnz(C), *n_overflow_host =
  *     clusters sent to the exact path.  Synchronises.

@@ -785,8 +785,8 @@ struct LwWs {
   float* yhat_tot;
   int32_t *ncap, *flag, *flist, *flist_count, *flist_plan, *h_pos;
   int64_t* slab_off;  // per position: the row's place in the slab (written by the learned kernels)
-  int64_t* tot_cap;   // ncl + 1: prefix of the clusters' slab shares; tot_cap[ncl] = pool capacity
-  unsigned long long* pool;
+  int64_t* pool_base;       // NSUBPOOL + 1: slab ranges of the sub-pools; pool_base[NSUBPOOL] = slab size
+  unsigned long long* pool;  // NSUBPOOL reservation cursors
   size_t bytes;
 };
 LwWs carve_lw(void* base, size_t cap, int64_t nrows, int64_t ncl) {
@@ -810,8 +810,8 @@ LwWs carve_lw(void* base, size_t cap, int64_t nrows, int64_t ncl) {
   w.flist_plan = cv.take<int32_t>(1);
   w.h_pos = cv.take<int32_t>(nrows);
   w.slab_off = cv.take<int64_t>(nrows + 1);
-  w.tot_cap = cv.take<int64_t>(ncl + 1);
-  w.pool = cv.take<unsigned long long>(1);
+  w.pool_base = cv.take<int64_t>(NSUBPOOL + 1);
+  w.pool = cv.take<unsigned long long>(NSUBPOOL);
   w.bytes = cv.off + 256;
   return w;
 }
@@ -909,11 +909,11 @@ int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_pr
   const float mtot = pred->margin_total > 0.0f ? pred->margin_total : pred->margin;
   const int inb = dtype_bytes(A->dtype);
   SGC_CUDA(learned_bin_run(av, bv, w.yhat, tot ? w.yhat_tot : nullptr, pred->ncap, pred->margin, mtot, pred->scale,
-                           w.sp.bins.uc_rec, w.h_pos, w.ncap, w.tot_cap, w.flag, w.flist, w.flist_count, w.lb, inb, 8,
-                           mode, o.cl_load, o.lean, sms, s));
-  SGC_CUDA(inclusive_scan_i64(w.tot_cap + 1, A->nclusters, w.sp.scan_tmp, s));
+                           w.sp.bins.uc_rec, w.h_pos, w.ncap, w.pool_base, w.flag, w.flist, w.flist_count, w.lb, inb,
+                           8, mode, o.cl_load, o.lean, sms, s));
+  SGC_CUDA(inclusive_scan_i64(w.pool_base + 1, NSUBPOOL, w.sp.scan_tmp, s));
   SGC_CUDA(cudaMemcpyAsync(w.flist_plan, w.flist_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-  SGC_CUDA(cudaMemcpyAsync(slab_elems_host, w.tot_cap + A->nclusters, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SGC_CUDA(cudaMemcpyAsync(slab_elems_host, w.pool_base + NSUBPOOL, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   return sync_status(w.sp.status, s);
 }
 
@@ -933,12 +933,12 @@ int spgemm_learned_phase1(const sgc_csr_cluster* A, const sgc_csr* B, int32_t* s
   SGC_CUDA(cudaMemsetAsync(w.sp.status, 0, sizeof(DevStatus), s));
   SGC_CUDA(cudaMemsetAsync(c_row_ptr, 0, sizeof(int64_t), s));
   SGC_CUDA(cudaMemcpyAsync(w.flist_count, w.flist_plan, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-  SGC_CUDA(cudaMemsetAsync(w.pool, 0, sizeof(unsigned long long), s));
+  SGC_CUDA(cudaMemsetAsync(w.pool, 0, sizeof(unsigned long long) * NSUBPOOL, s));
   if (A->nrows > 0) {
     const AClusterView av = cview(A, true);
     const BView bv = bview(B, true);
     const LearnedOut lo{1,      w.ncap,        w.slab_off, slab_col, slab_val,
-                        c_row_ptr, w.flag,     w.flist,    w.flist_count, w.pool, w.tot_cap + A->nclusters};
+                        c_row_ptr, w.flag,     w.flist,    w.flist_count, w.pool, w.pool_base};
     switch (A->dtype) {
       case SGC_F32: SGC_CUDA(run_cluster_learned<SGC_F32>(av, bv, w.lb, lo, w.sp.status, L)); break;
       case SGC_F64: SGC_CUDA(run_cluster_learned<SGC_F64>(av, bv, w.lb, lo, w.sp.status, L)); break;

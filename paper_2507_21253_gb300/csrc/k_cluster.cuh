@@ -207,7 +207,7 @@ __device__ __forceinline__ int count_row(const uint8_t* fl, int n_out) {
 }
 
 template <bool SYM, int DT>
-__global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A, BView B, CView C, int64_t* c_rp_sym,
+__global__ void __launch_bounds__(CL_THREADS, 5) k_cluster_group(AClusterView A, BView B, CView C, int64_t* c_rp_sym,
                                                               const int32_t* items, const int32_t* count_ptr,
                                                               int32_t* nout_rec, const int32_t* uc_rec, int mode,
                                                               int region_bytes, int gw, int fused, int cl_load,
@@ -352,19 +352,19 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       for (int q = lane; q < n; q += 32) stage_c[dc + q] = B.col[s + q];
     }
     if (bulk) {
-      // Every warp of the group takes the same decision: each posts whether its
-      // wait completed, then all read the posts after one group barrier, so no
-      // warp is left waiting at a later group barrier for warps that returned.
-      const bool ok = __all_sync(FULL, mbar_wait_bounded(bar, phase, wait_limit));
-      if (lane == 0) hdr[1 + wg] = ok ? 0 : 1;
+      // One thread waits for the copies (bounded) and posts the outcome; the
+      // group barrier then orders the staged data before every thread of the
+      // group and hands all of them the same decision, so no warp is left
+      // waiting at a later group barrier for warps that returned.
+      if (gt == 0) hdr[1] = mbar_wait_bounded(bar, phase, wait_limit) ? 0 : 1;
       group_sync(gw, gid);
-      int gave_up = 0;
-      for (int q = 0; q < gw; ++q) gave_up |= hdr[1 + q];
-      if (gave_up) {
-        if (gt == 0) raise(st, DEV_TIMEOUT, 30, c);
-        // the group's copies may still be landing in its shared memory: wait for
-        // them (bounded) before the CTA may exit, then give up on the launch
-        mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+      if (hdr[1]) {
+        if (gt == 0) {
+          raise(st, DEV_TIMEOUT, 30, c);
+          // the group's copies may still be landing in its shared memory: wait
+          // for them (bounded) before the CTA may exit
+          mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+        }
         return;
       }
       phase ^= 1u;
@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
         if (gt == 0) {
           int64_t tot = 0;
           for (int q = 0; q < K; ++q) tot += rcnt[q];
-          const int64_t base = pool_reserve(lo, tot);
+          const int64_t base = pool_reserve(lo, c, tot);
           *sbase = base;
           if (base < 0) {  // pool exhausted: the exact path computes this cluster
             lo.flag[c] = 1;

@@ -138,9 +138,14 @@ __global__ void __launch_bounds__(256) k_cluster_lean(AClusterView A, BView B, C
     }
     auto await_a = [&]() -> bool {  // completes this cluster's A-value copy; false on timeout
       if (!win) return true;
-      const bool ok = __all_sync(FULL, mbar_wait_bounded(bar, phase, wait_limit));
-      // after a timeout the copy may still be landing: wait for it (bounded) before the warp returns
-      if (!ok) mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+      // lane 0 waits (bounded); the warp shares its outcome
+      bool ok = true;
+      if (lane == 0) {
+        ok = mbar_wait_bounded(bar, phase, wait_limit);
+        // after a timeout the copy may still be landing: wait for it (bounded) before the warp returns
+        if (!ok) mbar_wait_bounded(bar, phase, WAIT_LIMIT);
+      }
+      ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
       phase ^= 1u;
       return ok;
     };
@@ -380,7 +385,7 @@ __global__ void __launch_bounds__(256) k_cluster_lean(AClusterView A, BView B, C
       const int ex = warp_incl_scan(my) - my;
       const int tot = __shfl_sync(FULL, ex + my, 31);
       int64_t base = 0;
-      if (lane == 0) base = pool_reserve(lo, tot);
+      if (lane == 0) base = pool_reserve(lo, c, tot);
       base = __shfl_sync(FULL, base, 0);
       if (base < 0) {  // pool exhausted: the exact path computes this cluster
         if (lane == 0) {

@@ -304,7 +304,7 @@ __device__ __forceinline__ int32_t capacity_of(float yhat, int64_t bound, float 
 __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, const float* yhat, const float* yhat_tot,
                                                      const int32_t* ncap_in, float margin, float margin_tot,
                                                      float scale, const int32_t* uc, const int32_t* h_pos,
-                                                     int32_t* ncap_out, int64_t* tot_cap, int32_t* flag,
+                                                     int32_t* ncap_out, int64_t* pool_base, int32_t* flag,
                                                      int32_t* flist, int32_t* flist_count, BinOut lb, int in_bytes,
                                                      int acc_bytes, int bulk, int cl_load, int lean) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, co
     if (lane == 0) {
       int64_t share = hb;
       if (yhat_tot) share = min64(hb, (int64_t)capacity_of(yhat_tot[c], hb, margin_tot, scale));
-      tot_cap[c + 1] = take ? share : 0;
+      if (take && share > 0) atomicAdd((unsigned long long*)&pool_base[1 + c % NSUBPOOL], (unsigned long long)share);
       ncap_out[c] = ncap;
       flag[c] = take ? 0 : 1;
       if (lcls >= 0) {
@@ -437,18 +437,18 @@ cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, 
 
 cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const float* yhat_tot,
                             const int32_t* ncap_in, float margin, float margin_tot, float scale, const int32_t* uc,
-                            const int32_t* h_pos, int32_t* ncap_out, int64_t* tot_cap, int32_t* flag, int32_t* flist,
+                            const int32_t* h_pos, int32_t* ncap_out, int64_t* pool_base, int32_t* flag, int32_t* flist,
                             int32_t* flist_count, const BinOut& lb, int in_bytes, int acc_bytes, int bulk, int cl_load,
                             int lean, int sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(lb.count, 0, sizeof(int32_t) * NBIN_ALL, s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(flist_count, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(tot_cap, 0, sizeof(int64_t), s);
+  e = cudaMemsetAsync(pool_base, 0, sizeof(int64_t) * (NSUBPOOL + 1), s);
   if (e != cudaSuccess) return e;
   if (A.ncl <= 0) return cudaSuccess;
   k_learned_bin<<<grid_for(A.ncl, 8, sms, 8), 256, 0, s>>>(A, B, yhat, yhat_tot, ncap_in, margin, margin_tot, scale,
-                                                            uc, h_pos, ncap_out, tot_cap, flag, flist, flist_count, lb,
+                                                            uc, h_pos, ncap_out, pool_base, flag, flist, flist_count, lb,
                                                             in_bytes, acc_bytes, bulk, cl_load, lean);
   note_launches(1);
   return cudaGetLastError();

@@ -75,14 +75,22 @@ struct LearnedOut {
   int32_t* flag;             // per cluster: 0 = done, 1 = overflow (exact path)
   int32_t* flist;            // overflow cluster list (appended) ...
   int32_t* flist_count;      // ... and its count
-  unsigned long long* pool;  // slab elements reserved so far (one atomic per cluster)
-  const int64_t* pool_cap;   // slab capacity (elements)
+  unsigned long long* pool;  // NSUBPOOL cursors: slab elements reserved so far in each sub-pool
+  const int64_t* pool_base;  // NSUBPOOL + 1: sub-pool s is the slab range [pool_base[s], pool_base[s + 1])
 };
 
-// Learned mode: reserves `total` slab elements; the pool offset, or -1 when the pool is exhausted.
-__device__ __forceinline__ int64_t pool_reserve(const LearnedOut& lo, int64_t total) {
-  const unsigned long long base = atomicAdd(lo.pool, (unsigned long long)total);
-  return (int64_t)base + total <= *lo.pool_cap ? (int64_t)base : (int64_t)-1;
+// The slab is split into sub-pools, cluster c drawing from sub-pool c % NSUBPOOL
+// (each sized by the plan to the summed shares of its clusters), so that the
+// one reservation per cluster spreads its atomics over NSUBPOOL addresses.
+constexpr int NSUBPOOL = 64;
+
+// Learned mode: reserves `total` slab elements for cluster c; the slab offset,
+// or -1 when the cluster's sub-pool is exhausted.
+__device__ __forceinline__ int64_t pool_reserve(const LearnedOut& lo, int64_t c, int64_t total) {
+  const int s = (int)(c % NSUBPOOL);
+  const unsigned long long off = atomicAdd(lo.pool + s, (unsigned long long)total);
+  const int64_t b0 = lo.pool_base[s], b1 = lo.pool_base[s + 1];
+  return b0 + (int64_t)off + total <= b1 ? b0 + (int64_t)off : (int64_t)-1;
 }
 
 struct Launch {
@@ -134,7 +142,7 @@ cudaError_t mlp_train_run(const float* X, const float* y, const int32_t* order, 
                           void* ws, cudaStream_t s);
 cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* yhat, const float* yhat_tot,
                             const int32_t* ncap_in, float margin, float margin_tot, float scale, const int32_t* uc,
-                            const int32_t* h_pos, int32_t* ncap_out, int64_t* tot_cap, int32_t* flag, int32_t* flist,
+                            const int32_t* h_pos, int32_t* ncap_out, int64_t* pool_base, int32_t* flag, int32_t* flist,
                             int32_t* flist_count, const BinOut& lb, int in_bytes, int acc_bytes, int bulk, int cl_load,
                             int lean, int sms, cudaStream_t s);
 cudaError_t compact_run(const AClusterView& A, const int32_t* flag, const int64_t* slab_off, const int32_t* slab_col,
