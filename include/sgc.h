@@ -138,8 +138,17 @@ typedef struct sgc_options {
                                0 = default (2^22 polls, about 0.3 s); < 0 = give up without polling, which
                                exercises the timeout path.  After giving up, a kernel waits (with the
                                default limit) for the copies it has in flight before it returns. */
-  int32_t reserved[7];
+  int32_t accumulator;      /* cluster kernels' accumulator: 0 (default) = a shared-memory hash table of the
+                               cluster's output columns, ranked in column order; 1 = dense where it fits: a
+                               cluster whose output columns span at most SGC_DENSE_SPAN_MAX columns
+                               (smallest to largest column of the B rows it touches) and whose dense
+                               working set fits shared memory accumulates into per-row arrays over that
+                               span with presence bits (no hashing, no ranking); other clusters use the
+                               hash table */
+  int32_t reserved[6];
 } sgc_options;
+
+#define SGC_DENSE_SPAN_MAX 4096
 
 /* Version of this ABI (SGC_ABI_VERSION). */
 int sgc_abi_version(void);

@@ -46,6 +46,7 @@ ResolvedOptions resolve(const sgc_options* opt) {
   r.wait_limit = WAIT_POLLS_DEFAULT;
   if (opt && opt->wait_polls > 0) r.wait_limit = (uint32_t)opt->wait_polls;
   if (opt && opt->wait_polls < 0) r.wait_limit = 0;
+  r.dense = (opt && opt->accumulator == 1) ? 1 : 0;
   return r;
 }
 
@@ -73,6 +74,8 @@ SpWs carve_sp(void* base, size_t cap, int64_t nrows, int64_t ncl) {
   w.bins.heavy_items = cv.take<int64_t>(nrows);
   w.bins.uc_rec = cv.take<int32_t>(ncl);
   w.bins.nout_rec = cv.take<int32_t>(ncl);
+  w.bins.span_lo = cv.take<int32_t>(ncl);
+  w.bins.span_w = cv.take<int32_t>(ncl);
   w.bins.ncl = ncl;
   w.bins.nrows = nrows;
   w.scan_tmp = cv.take<int64_t>(scan_tmp_elems(nrows));
@@ -594,6 +597,7 @@ HcWs carve_hc(void* base, size_t cap, const sgc_csr* A, int topk) {
   w.bins.row_items = cv.take<int64_t>((int64_t)NRB * n);
   w.bins.heavy_items = cv.take<int64_t>(n);
   w.bins.uc_rec = w.bins.nout_rec = nullptr;
+  w.bins.span_lo = w.bins.span_w = nullptr;
   w.bins.ncl = 0;
   w.bins.nrows = n;
   w.scan_tmp = cv.take<int64_t>(scan_tmp_elems(n > m ? n : m));
@@ -800,6 +804,8 @@ LwWs carve_lw(void* base, size_t cap, int64_t nrows, int64_t ncl) {
   w.lb.ncl = ncl;
   w.lb.nrows = nrows;
   w.lb.uc_rec = w.sp.bins.uc_rec;
+  w.lb.span_lo = w.sp.bins.span_lo;
+  w.lb.span_w = w.sp.bins.span_w;
   w.X = cv.take<float>(ncl * 8);
   w.yhat = cv.take<float>(ncl);
   w.yhat_tot = cv.take<float>(ncl);
@@ -821,7 +827,7 @@ int cluster_features(const sgc_csr_cluster* A, const sgc_csr* B, float* features
   int rc = check_product(A, B, false);
   if (rc) return rc;
   if (A->nclusters > 0 && !features) SGC_FAIL(SGC_INVALID_ARG, "features is NULL");
-  SGC_CUDA(features_run(cview(A, false), bview(B, false), features, nullptr, nullptr, num_sms(),
+  SGC_CUDA(features_run(cview(A, false), bview(B, false), features, nullptr, nullptr, nullptr, nullptr, num_sms(),
                         (cudaStream_t)stream));
   return SGC_OK;
 }
@@ -902,14 +908,16 @@ int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_pr
   SGC_CUDA(cudaMemsetAsync(w.sp.status, 0, sizeof(DevStatus), s));
   const AClusterView av = cview(A, false);
   const BView bv = bview(B, false);
-  SGC_CUDA(features_run(av, bv, w.X, w.sp.bins.uc_rec, w.h_pos, sms, s));
+  BinOut lb = w.lb;  // span records only with the dense accumulator (else the kernels ignore them)
+  if (!o.dense) lb.span_lo = lb.span_w = nullptr;
+  SGC_CUDA(features_run(av, bv, w.X, w.sp.bins.uc_rec, w.h_pos, lb.span_lo, lb.span_w, sms, s));
   if (!pred->ncap) SGC_CUDA(mlp_infer_run(pred->params, w.X, A->nclusters, w.yhat, sms, s));
   const bool tot = pred->params_total != nullptr;
   if (tot) SGC_CUDA(mlp_infer_run(pred->params_total, w.X, A->nclusters, w.yhat_tot, sms, s));
   const float mtot = pred->margin_total > 0.0f ? pred->margin_total : pred->margin;
   const int inb = dtype_bytes(A->dtype);
   SGC_CUDA(learned_bin_run(av, bv, w.yhat, tot ? w.yhat_tot : nullptr, pred->ncap, pred->margin, mtot, pred->scale,
-                           w.sp.bins.uc_rec, w.h_pos, w.ncap, w.pool_base, w.flag, w.flist, w.flist_count, w.lb, inb,
+                           w.sp.bins.uc_rec, w.h_pos, w.ncap, w.pool_base, w.flag, w.flist, w.flist_count, lb, inb,
                            8, mode, o.cl_load, o.lean, sms, s));
   SGC_CUDA(inclusive_scan_i64(w.pool_base + 1, NSUBPOOL, w.sp.scan_tmp, s));
   SGC_CUDA(cudaMemcpyAsync(w.flist_plan, w.flist_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));

@@ -54,8 +54,10 @@ struct WarpLayout {
 // Layout of one cluster in a warp's region.  T union columns, U staged B
 // elements, nva value slots of the cluster, LH log2 hash slots, nout output
 // columns (numeric) or their bound (symbolic), K rows.
+// Dense accumulator (dense = true): no column table; nout is the output span
+// width, the accumulators (numeric) or row bitmaps (symbolic) run over it.
 __host__ __device__ inline WarpLayout warp_layout(bool sym, int64_t T, int64_t U, int64_t nva, int LH, int64_t nout,
-                                                  int K, int in_bytes, int acc_bytes, bool bulk) {
+                                                  int K, int in_bytes, int acc_bytes, bool bulk, bool dense = false) {
   WarpLayout L{};
   const int64_t pad_c = bulk ? 6 : 0;
   int64_t o = 512;  // group header: mbarrier, counters, scan partials, per-row counts, slab base
@@ -71,13 +73,13 @@ __host__ __device__ inline WarpLayout warp_layout(bool sym, int64_t T, int64_t U
     o = (o + 15) & ~15ll;
   }
   L.table = (int)o;
-  o += 4ll << LH;
+  if (!dense) o += 4ll << LH;
   if (sym) {
-    L.flags = (int)o;  // per-row bitmaps over hash slots
-    o += 4ll * K * (((1ll << LH) + 31) / 32);
+    L.flags = (int)o;  // per-row bitmaps over hash slots (dense: over the span)
+    o += 4ll * K * (((dense ? nout : (1ll << LH)) + 31) / 32);
   } else {
     L.sorted = (int)o;
-    o += 4 * nout;
+    if (!dense) o += 4 * nout;
     o = (o + 15) & ~15ll;
     // the ranking scratch (bucket starts, cursors, compacted keys, their slots:
     // 16 * nout + 16 bytes) is dead before the accumulators are zeroed: alias them
@@ -86,7 +88,7 @@ __host__ __device__ inline WarpLayout warp_layout(bool sym, int64_t T, int64_t U
     const int64_t accb = (int64_t)acc_bytes * K * nout;
     L.flags = (int)(o + accb);
     const int64_t region = accb + (int64_t)K * nout;
-    o += region > 16 * nout + 16 ? region : 16 * nout + 16;
+    o += (dense || region > 16 * nout + 16) ? region : 16 * nout + 16;
   }
   o = (o + 15) & ~15ll;
   L.total = o > (1 << 30) ? (1 << 30) : (int)o;
@@ -178,10 +180,12 @@ __device__ __forceinline__ uint64_t group_excl_scan64(uint64_t v, int gw, int gi
 // Row l of a cluster: its entries are the set flags fl[0..n_out) in rank (=
 // column) order; emit writes at most `cap` of them at out0 and returns the
 // row's count (warp-collective), count_row only counts.
+// srt: the column of each rank (hash table mode), or NULL: the dense
+// accumulator, whose local id x is column key0 + x.
 template <int DT>
 __device__ __forceinline__ int64_t emit_row(const typename VT<DT>::Acc* al, const uint8_t* fl, const int32_t* srt,
-                                           int n_out, int32_t* ocol, typename VT<DT>::In* oval, int64_t out0,
-                                           int64_t cap) {
+                                           int32_t key0, int n_out, int32_t* ocol, typename VT<DT>::In* oval,
+                                           int64_t out0, int64_t cap) {
   const unsigned lt = lanemask_lt();
   int64_t nn = 0;
   for (int x0 = 0; x0 < n_out; x0 += 32) {
@@ -190,7 +194,7 @@ __device__ __forceinline__ int64_t emit_row(const typename VT<DT>::Acc* al, cons
     const unsigned bal = __ballot_sync(FULL, f);
     const int64_t pos = nn + __popc(bal & lt);
     if (f && pos < cap) {
-      ocol[out0 + pos] = srt[x];
+      ocol[out0 + pos] = srt ? srt[x] : key0 + x;
       oval[out0 + pos] = VT<DT>::out(al[x]);
     }
     nn += __popc(bal);
@@ -207,9 +211,10 @@ __device__ __forceinline__ int count_row(const uint8_t* fl, int n_out) {
 }
 
 template <bool SYM, int DT>
-__global__ void __launch_bounds__(CL_THREADS, 5) k_cluster_group(AClusterView A, BView B, CView C, int64_t* c_rp_sym,
+__global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A, BView B, CView C, int64_t* c_rp_sym,
                                                               const int32_t* items, const int32_t* count_ptr,
-                                                              int32_t* nout_rec, const int32_t* uc_rec, int mode,
+                                                              int32_t* nout_rec, const int32_t* uc_rec,
+                                                              const int32_t* span_lo, const int32_t* span_w, int mode,
                                                               int region_bytes, int gw, int fused, int cl_load,
                                                               LearnedOut lo, uint32_t wait_limit, void* status) {
   using In = typename VT<DT>::In;
@@ -248,10 +253,15 @@ __global__ void __launch_bounds__(CL_THREADS, 5) k_cluster_group(AClusterView A,
     const int64_t u0 = A.uptr[c], T = A.uptr[c + 1] - u0;
     const int64_t v0 = A.vptr[c], nva = A.vptr[c + 1] - v0;
     const int64_t U = uc_rec[c];
-    // output columns: bound (symbolic), exact count (numeric) or predicted capacity (learned)
-    const int64_t nb = SYM ? min64(U, B.ncols) : (lo.active ? (int64_t)lo.ncap[c] : (int64_t)nout_rec[c]);
-    const int LH = cluster_table_log2(SYM, nb, cl_load);
-    const WarpLayout Ly = warp_layout(SYM, T, U, SYM ? 0 : nva, LH, nb, K, sizeof(In), sizeof(Acc), bulk);
+    // dense accumulator (binned so): local column ids over the span [dlo, dlo + dw)
+    const int32_t dw = span_w ? span_w[c] : 0;
+    const bool dense = dw > 0;
+    const int32_t dlo = dense ? span_lo[c] : 0;
+    // output columns: bound (symbolic), exact count (numeric), predicted capacity (learned), span (dense)
+    const int64_t nb = dense ? (int64_t)dw
+                             : (SYM ? min64(U, B.ncols) : (lo.active ? (int64_t)lo.ncap[c] : (int64_t)nout_rec[c]));
+    const int LH = dense ? 5 : cluster_table_log2(SYM, nb, cl_load);
+    const WarpLayout Ly = warp_layout(SYM, T, U, SYM ? 0 : nva, LH, nb, K, sizeof(In), sizeof(Acc), bulk, dense);
     if (Ly.total > region_bytes) {  // binned with other options than this launch's: refuse, do not overflow
       if (gt == 0) raise(st, DEV_INTERNAL, 35, c);
       continue;
@@ -332,7 +342,8 @@ __global__ void __launch_bounds__(CL_THREADS, 5) k_cluster_group(AClusterView A,
       }
     }
     // table init overlaps the copies in flight
-    for (int x = gt; x < TH; x += GT) table[x] = EMPTY_KEY;
+    if (!dense)
+      for (int x = gt; x < TH; x += GT) table[x] = EMPTY_KEY;
     if (gt == 0) {
       hdr[0] = 0;  // distinct output columns
       hdr[9] = 0;  // compaction cursor (numeric)
@@ -376,7 +387,7 @@ __global__ void __launch_bounds__(CL_THREADS, 5) k_cluster_group(AClusterView A,
       // for each union column t (split over the group's warps), each lane takes
       // one entry j of B row t, finds j's slot in the cluster table and sets
       // bit `slot` in the bitmap of every row l that has a_lt.
-      const int WPR = TH / 32;
+      const int WPR = dense ? (dw + 31) / 32 : TH / 32;
       uint32_t* rb = (uint32_t*)(my + Ly.flags);
       for (int x = gt; x < K * WPR; x += GT) rb[x] = 0;
       group_sync(gw, gid);
@@ -391,8 +402,12 @@ __global__ void __launch_bounds__(CL_THREADS, 5) k_cluster_group(AClusterView A,
           int slot = -1;
           bool nwk = false;
           if (q < n) {
-            slot = hash_find_or_insert(table, LH, stage_c[dc + q], &nwk);
-            if (slot < 0) full = true;
+            if (dense) {
+              slot = stage_c[dc + q] - dlo;  // the bit of column j in the span
+            } else {
+              slot = hash_find_or_insert(table, LH, stage_c[dc + q], &nwk);
+              if (slot < 0) full = true;
+            }
           }
           __syncwarp();  // reconverge after the probes: the bitmap updates issue once
           if (slot >= 0) {
@@ -418,139 +433,161 @@ __global__ void __launch_bounds__(CL_THREADS, 5) k_cluster_group(AClusterView A,
         cc = warp_sum(cc);
         if (lane == 0) c_rp_sym[A.perm[p0 + l] + 1] = cc;
       }
+      if (dense) {  // the cluster's output columns: the union of its rows' bitmaps
+        int cu = 0;
+        for (int x = gt; x < WPR; x += GT) {
+          uint32_t o = 0;
+          for (int l = 0; l < K; ++l) o |= rb[(size_t)l * WPR + x];
+          cu += __popc(o);
+        }
+        cu = warp_sum(cu);
+        if (lane == 0 && cu) atomicAdd(&hdr[0], cu);
+        group_sync(gw, gid);
+      }
       if (gt == 0) nout_rec[c] = hdr[0];
     } else {
-      // ---- 2. map staged column ids to slots ---------------------------------
-      bool full = false;
-      int newk = 0;
-      int32_t kmin = PAD_KEY, kmax = -1;  // range of the cluster's output columns
-      for (int64_t i = wg; i < T; i += gw) {
-        const int n = d.len[i];
-        const int dc = d.off_c[i] & 0x7fffffff;
-        for (int qb = 0; qb < n; qb += 32) {  // all lanes take every step
-          const int q = qb + lane;
-          int slot = -1;
-          bool nwk = false;
-          int32_t j = 0;
-          if (q < n) {
-            j = stage_c[dc + q];
-            slot = hash_find_or_insert(table, LH, j, &nwk);
-            if (slot < 0) full = true;
-          }
-          __syncwarp();
-          if (slot >= 0) {
-            newk += nwk;
-            kmin = min(kmin, j);
-            kmax = max(kmax, j);
-            stage_c[dc + q] = slot;
+      int n_out = (int)nb;
+      int32_t* srt = dense ? nullptr : (int32_t*)(my + Ly.sorted);
+      if (dense) {
+        // ---- 2d. dense accumulator: the local id of column j is j - dlo ------
+        for (int64_t i = wg; i < T; i += gw) {
+          const int n = d.len[i];
+          const int dc = d.off_c[i] & 0x7fffffff;
+          for (int q = lane; q < n; q += 32) stage_c[dc + q] -= dlo;
+        }
+        if (lo.active && gt == 0) lo.flag[c] = 0;  // the span always fits: no overflow
+      } else {
+        // ---- 2. map staged column ids to slots ---------------------------------
+        bool full = false;
+        int newk = 0;
+        int32_t kmin = PAD_KEY, kmax = -1;  // range of the cluster's output columns
+        for (int64_t i = wg; i < T; i += gw) {
+          const int n = d.len[i];
+          const int dc = d.off_c[i] & 0x7fffffff;
+          for (int qb = 0; qb < n; qb += 32) {  // all lanes take every step
+            const int q = qb + lane;
+            int slot = -1;
+            bool nwk = false;
+            int32_t j = 0;
+            if (q < n) {
+              j = stage_c[dc + q];
+              slot = hash_find_or_insert(table, LH, j, &nwk);
+              if (slot < 0) full = true;
+            }
+            __syncwarp();
+            if (slot >= 0) {
+              newk += nwk;
+              kmin = min(kmin, j);
+              kmax = max(kmax, j);
+              stage_c[dc + q] = slot;
+            }
           }
         }
-      }
-      newk = warp_sum(newk);
-      if (lane == 0 && newk) atomicAdd(&hdr[0], newk);
-      kmin = warp_min(kmin);
-      kmax = warp_max(kmax);
-      if (lane == 0) {
-        wmin[wg] = kmin;
-        wmax[wg] = kmax;
-      }
-      const bool anyfull = __any_sync(FULL, full);
-      if (anyfull && lane == 0) {
-        if (lo.active)
-          hdr[1 + wg] = -1;  // table full: more output columns than the capacity
-        else
-          raise(st, DEV_TABLE_FULL, 31, c);
-      } else if (lane == 0 && lo.active) {
-        hdr[1 + wg] = 0;
-      }
-      group_sync(gw, gid);
-      const int n_out = hdr[0];
-      if (lo.active) {
-        bool over = n_out > nb;
-        for (int q = 0; q < gw; ++q) over |= hdr[1 + q] != 0;
-        if (over) {  // overflow: leave the cluster to the exact path
-          if (gt == 0) {
-            lo.flag[c] = 1;
-            lo.flist[atomicAdd(lo.flist_count, 1)] = c;
+        newk = warp_sum(newk);
+        if (lane == 0 && newk) atomicAdd(&hdr[0], newk);
+        kmin = warp_min(kmin);
+        kmax = warp_max(kmax);
+        if (lane == 0) {
+          wmin[wg] = kmin;
+          wmax[wg] = kmax;
+        }
+        const bool anyfull = __any_sync(FULL, full);
+        if (anyfull && lane == 0) {
+          if (lo.active)
+            hdr[1 + wg] = -1;  // table full: more output columns than the capacity
+          else
+            raise(st, DEV_TABLE_FULL, 31, c);
+        } else if (lane == 0 && lo.active) {
+          hdr[1 + wg] = 0;
+        }
+        group_sync(gw, gid);
+        n_out = hdr[0];
+        if (lo.active) {
+          bool over = n_out > nb;
+          for (int q = 0; q < gw; ++q) over |= hdr[1 + q] != 0;
+          if (over) {  // overflow: leave the cluster to the exact path
+            if (gt == 0) {
+              lo.flag[c] = 1;
+              lo.flist[atomicAdd(lo.flist_count, 1)] = c;
+            }
+            group_sync(gw, gid);
+            continue;
           }
+          if (gt == 0) lo.flag[c] = 0;
+        } else if (n_out != nb) {
+          if (gt == 0) raise(st, DEV_INTERNAL, 32, c);
           group_sync(gw, gid);
           continue;
         }
-        if (gt == 0) lo.flag[c] = 0;
-      } else if (n_out != nb) {
-        if (gt == 0) raise(st, DEV_INTERNAL, 32, c);
-        group_sync(gw, gid);
-        continue;
-      }
-      // ---- 2b. rank the output columns in column order (group-parallel):
-      // compact the occupied slots, bucket the keys by an interpolated key
-      // (monotone in the key), scan the bucket counts, count smaller keys
-      // within a bucket.  table[slot] becomes the rank; srt[rank] the key.
-      int32_t* srt = (int32_t*)(my + Ly.sorted);
-      int32_t* bst = (int32_t*)(my + Ly.scratch);
-      int32_t* bcur = bst + nb;
-      int32_t* bkey = bcur + nb;
-      int32_t* kslot = bkey + nb;
-      {
-        // compaction of the occupied slots, in any order (the ranking sorts them):
-        // one cursor advance a warp step; the key range comes from the map phase
-        for (int x0 = wg * 32; x0 < TH; x0 += GT) {
-          const int x = x0 + lane;
-          const int32_t key = table[x];
-          const bool occ = key != EMPTY_KEY;
-          const unsigned bal = __ballot_sync(FULL, occ);
-          int base = 0;
-          if (lane == 0 && bal) base = atomicAdd(&hdr[9], __popc(bal));
-          base = __shfl_sync(FULL, base, 0);
-          if (occ) {
-            const int pos = base + __popc(bal & lt);
-            bkey[pos] = key;
-            kslot[pos] = x;
+        // ---- 2b. rank the output columns in column order (group-parallel):
+        // compact the occupied slots, bucket the keys by an interpolated key
+        // (monotone in the key), scan the bucket counts, count smaller keys
+        // within a bucket.  table[slot] becomes the rank; srt[rank] the key.
+        int32_t* bst = (int32_t*)(my + Ly.scratch);
+        int32_t* bcur = bst + nb;
+        int32_t* bkey = bcur + nb;
+        int32_t* kslot = bkey + nb;
+        {
+          // compaction of the occupied slots, in any order (the ranking sorts them):
+          // one cursor advance a warp step; the key range comes from the map phase
+          for (int x0 = wg * 32; x0 < TH; x0 += GT) {
+            const int x = x0 + lane;
+            const int32_t key = table[x];
+            const bool occ = key != EMPTY_KEY;
+            const unsigned bal = __ballot_sync(FULL, occ);
+            int base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&hdr[9], __popc(bal));
+            base = __shfl_sync(FULL, base, 0);
+            if (occ) {
+              const int pos = base + __popc(bal & lt);
+              bkey[pos] = key;
+              kslot[pos] = x;
+            }
           }
-        }
-        int32_t kmin = PAD_KEY, kmax = -1;
-        for (int q = 0; q < gw; ++q) {
-          kmin = min(kmin, wmin[q]);
-          kmax = max(kmax, wmax[q]);
-        }
-        for (int x = gt; x < n_out; x += GT) bst[x] = 0;
-        group_sync(gw, gid);
-        const Interp ip = interp_make(kmin, kmax, n_out);
-        for (int x = gt; x < n_out; x += GT) atomicAdd(&bst[interp_bucket(ip, bkey[x])], 1);
-        group_sync(gw, gid);
-        int carry = 0;
-        for (int x0 = 0; x0 < n_out; x0 += GT) {
-          const int x = x0 + gt;
-          const int v = x < n_out ? bst[x] : 0;
-          uint64_t tot;
-          const int ex = (int)group_excl_scan64((uint64_t)v, gw, gid, wg, red64, &tot);
-          if (x < n_out) {
-            bst[x] = carry + ex;  // bucket start
-            bcur[x] = carry + ex;
+          int32_t kmin = PAD_KEY, kmax = -1;
+          for (int q = 0; q < gw; ++q) {
+            kmin = min(kmin, wmin[q]);
+            kmax = max(kmax, wmax[q]);
           }
-          carry += (int)tot;
+          for (int x = gt; x < n_out; x += GT) bst[x] = 0;
+          group_sync(gw, gid);
+          const Interp ip = interp_make(kmin, kmax, n_out);
+          for (int x = gt; x < n_out; x += GT) atomicAdd(&bst[interp_bucket(ip, bkey[x])], 1);
+          group_sync(gw, gid);
+          int carry = 0;
+          for (int x0 = 0; x0 < n_out; x0 += GT) {
+            const int x = x0 + gt;
+            const int v = x < n_out ? bst[x] : 0;
+            uint64_t tot;
+            const int ex = (int)group_excl_scan64((uint64_t)v, gw, gid, wg, red64, &tot);
+            if (x < n_out) {
+              bst[x] = carry + ex;  // bucket start
+              bcur[x] = carry + ex;
+            }
+            carry += (int)tot;
+          }
+          group_sync(gw, gid);
+          for (int x = gt; x < n_out; x += GT)
+            srt[atomicAdd(&bcur[interp_bucket(ip, bkey[x])], 1)] = bkey[x];
+          group_sync(gw, gid);
+          for (int x = gt; x < n_out; x += GT) {
+            const int32_t key = bkey[x];
+            const int b = interp_bucket(ip, key);
+            const int bs = bst[b], be = bcur[b];
+            int r = bs;
+            for (int y = bs; y < be; ++y) r += srt[y] < key;
+            table[kslot[x]] = r;  // slot -> rank
+          }
+          group_sync(gw, gid);
+          for (int x = gt; x < n_out; x += GT) srt[table[kslot[x]]] = bkey[x];  // sorted keys
         }
-        group_sync(gw, gid);
-        for (int x = gt; x < n_out; x += GT)
-          srt[atomicAdd(&bcur[interp_bucket(ip, bkey[x])], 1)] = bkey[x];
-        group_sync(gw, gid);
-        for (int x = gt; x < n_out; x += GT) {
-          const int32_t key = bkey[x];
-          const int b = interp_bucket(ip, key);
-          const int bs = bst[b], be = bcur[b];
-          int r = bs;
-          for (int y = bs; y < be; ++y) r += srt[y] < key;
-          table[kslot[x]] = r;  // slot -> rank
+        // rewrite staged ids: slot -> rank
+        for (int64_t i = wg; i < T; i += gw) {
+          const int n = d.len[i];
+          const int dc = d.off_c[i] & 0x7fffffff;
+          for (int q = lane; q < n; q += 32) stage_c[dc + q] = table[stage_c[dc + q]];
         }
-        group_sync(gw, gid);
-        for (int x = gt; x < n_out; x += GT) srt[table[kslot[x]]] = bkey[x];  // sorted keys
-      }
-      // rewrite staged ids: slot -> rank
-      for (int64_t i = wg; i < T; i += gw) {
-        const int n = d.len[i];
-        const int dc = d.off_c[i] & 0x7fffffff;
-        for (int q = lane; q < n; q += 32) stage_c[dc + q] = table[stage_c[dc + q]];
-      }
+      }  // hash table mode
       group_sync(gw, gid);  // the ranking scratch is read up to here; the accumulators alias it
       Acc* acc = (Acc*)(my + Ly.acc);
       uint8_t* flg = (uint8_t*)(my + Ly.flags);
@@ -636,7 +673,7 @@ __global__ void __launch_bounds__(CL_THREADS, 5) k_cluster_group(AClusterView A,
         if (!lo.active) {
           const int64_t orow = A.perm[p0 + l];
           const int64_t out0 = C.rp[orow], expect = C.rp[orow + 1] - out0;
-          const int64_t nn = emit_row<DT>(al, fl, srt, n_out, C.col, (In*)C.val, out0, expect);
+          const int64_t nn = emit_row<DT>(al, fl, srt, dlo, n_out, C.col, (In*)C.val, out0, expect);
           if (nn != expect && lane == 0) raise(st, DEV_INTERNAL, 33, orow);
         } else {
           const int nn = count_row(fl, n_out);
@@ -663,7 +700,7 @@ __global__ void __launch_bounds__(CL_THREADS, 5) k_cluster_group(AClusterView A,
           for (int l = wg; l < K; l += gw) {
             int64_t off = base;
             for (int q = 0; q < l; ++q) off += rcnt[q];
-            const int64_t nn = emit_row<DT>(acc + l * n_out, flg + l * n_out, srt, n_out, lo.slab_col,
+            const int64_t nn = emit_row<DT>(acc + l * n_out, flg + l * n_out, srt, dlo, n_out, lo.slab_col,
                                             (In*)lo.slab_val, off, rcnt[l]);
             if (lane == 0) {
               const int64_t orow = A.perm[p0 + l];

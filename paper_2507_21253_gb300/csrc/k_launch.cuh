@@ -132,10 +132,10 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
   if (e != cudaSuccess) return e;
   const unsigned gb = grid_for(A.ncl, 8, L.sms, 8);
   if (SYM)
-    k_bin_cluster_sym<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, 1);
+    k_bin_cluster_sym<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, 1, L.o.dense);
   else
     k_bin_cluster_num<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, (int)sizeof(In),
-                                            (int)sizeof(Acc), L.o.cl_load, L.o.lean);
+                                            (int)sizeof(Acc), L.o.cl_load, L.o.lean, L.o.dense);
   note_launches(1);
   auto kd = k_cluster_group<SYM, DT>;
   static bool attr = false;
@@ -152,7 +152,8 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
     const int occ = occupancy(kd, threads, smem);
     const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
     kd<<<grid, threads, smem, L.s>>>(A, B, C, c_rp, bins.dense_items + (int64_t)b * bins.ncl, bins.count + b,
-                                      bins.nout_rec, bins.uc_rec, L.mode, rbytes, gw, L.o.fused, L.o.cl_load,
+                                      bins.nout_rec, bins.uc_rec, L.o.dense ? bins.span_lo : nullptr,
+                                      L.o.dense ? bins.span_w : nullptr, L.mode, rbytes, gw, L.o.fused, L.o.cl_load,
                                       LearnedOut{}, L.o.wait_limit, status);
     note_launches(1);
   }
@@ -184,7 +185,8 @@ cudaError_t run_cluster_learned(const AClusterView& A, const BView& B, const Bin
     const int occ = occupancy(kd, threads, smem);
     const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
     kd<<<grid, threads, smem, L.s>>>(A, B, CView{}, nullptr, lbins.dense_items + (int64_t)b * lbins.ncl,
-                                      lbins.count + b, nullptr, lbins.uc_rec, L.mode, rbytes, gw, L.o.fused,
+                                      lbins.count + b, nullptr, lbins.uc_rec, L.o.dense ? lbins.span_lo : nullptr,
+                                      L.o.dense ? lbins.span_w : nullptr, L.mode, rbytes, gw, L.o.fused,
                                       L.o.cl_load, lo, L.o.wait_limit, status);
     note_launches(1);
   }

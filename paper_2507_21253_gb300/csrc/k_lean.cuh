@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(256) k_cluster_lean(AClusterView A, BView B, C
       for (int l = 0; l < K; ++l) {
         const int64_t orow = A.perm[p0 + l];
         const int64_t out0 = C.rp[orow], expect = C.rp[orow + 1] - out0;
-        const int64_t nn = emit_row<DT>(acc + l * n_out, flg + l * n_out, srt, n_out, C.col, (In*)C.val, out0, expect);
+        const int64_t nn = emit_row<DT>(acc + l * n_out, flg + l * n_out, srt, 0, n_out, C.col, (In*)C.val, out0, expect);
         if (nn != expect && lane == 0) raise(st, DEV_INTERNAL, 42, orow);
       }
     } else {
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(256) k_cluster_lean(AClusterView A, BView B, C
         for (int l = 0; l < K; ++l) {
           const int64_t off = base + __shfl_sync(FULL, ex, l);
           const int n = __shfl_sync(FULL, my, l);
-          emit_row<DT>(acc + l * n_out, flg + l * n_out, srt, n_out, lo.slab_col, (In*)lo.slab_val, off, n);
+          emit_row<DT>(acc + l * n_out, flg + l * n_out, srt, 0, n_out, lo.slab_col, (In*)lo.slab_val, off, n);
           if (lane == 0) {
             lo.slab_off[p0 + l] = off;
             lo.cnt[A.perm[p0 + l] + 1] = n;

@@ -23,7 +23,7 @@ namespace {
 // features: warp per cluster
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_features(AClusterView A, BView B, float* X, int32_t* uc_out,
-                                                  int32_t* h_pos) {
+                                                  int32_t* h_pos, int32_t* span_lo, int32_t* span_w) {
   __shared__ unsigned long long s_ub[8][32];
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) k_features(AClusterView A, BView B, float
     s_ub[w][lane] = 0;
     __syncwarp();
     int64_t U = 0, nA = 0, ubr = 0;
-    int32_t first = 0, last = 0;
+    int32_t first = 0, last = 0, jl = PAD_KEY, jh = -1;
     for (int64_t tb = u0; tb < u1; tb += 32) {  // warp-uniform trip count
       const int64_t t = tb + lane;
       int32_t k = 0;
@@ -42,8 +42,10 @@ __global__ void __launch_bounds__(256) k_features(AClusterView A, BView B, float
       uint32_t m = 0;
       if (t < u1) {
         k = A.ucol[t];
-        len = B.rp[k + 1] - B.rp[k];
+        const int64_t bs = B.rp[k], be = B.rp[k + 1];
+        len = be - bs;
         m = A.mask[t];
+        if (span_w) span_add(B, bs, be, &jl, &jh);
       }
       U += len;
       nA += __popc(m);
@@ -53,6 +55,14 @@ __global__ void __launch_bounds__(256) k_features(AClusterView A, BView B, float
     }
     U = warp_sum(U);
     nA = warp_sum(nA);
+    if (span_w) {  // the dense accumulator's span (width 0: too wide)
+      jl = warp_min(jl);
+      jh = warp_max(jh);
+      if (lane == 0) {
+        span_w[c] = span_width(jl, jh);
+        span_lo[c] = jl;
+      }
+    }
     __syncwarp();
     const int64_t ub = lane < K ? (K == 1 ? U : ubr + (int64_t)s_ub[w][lane]) : 0;
     const int64_t sub = warp_sum(ub), mub = warp_max(ub);
@@ -318,11 +328,22 @@ __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, co
     const int64_t bound = min64(U, B.ncols);
     const int32_t ncap = ncap_in ? (int32_t)min64(ncap_in[c], bound) : capacity_of(yhat[c], bound, margin, scale);
     int cls = -1, lcls = -1;
+    int32_t dw = lb.span_w ? lb.span_w[c] : 0;
     if (U < (1ll << 28) && T < (1ll << 24)) {  // clusters of every size, one-row clusters included
-      const int LH = cluster_table_log2(false, ncap, cl_load);
-      if (lean) lcls = lean_class(lean_layout(T, nva, LH, ncap, K, in_bytes, acc_bytes).total);
-      if (lcls < 0) cls = warp_class(warp_layout(false, T, U, nva, LH, ncap, K, in_bytes, acc_bytes, bulk != 0).total);
+      if (dw > 0) {  // the dense accumulator when the output span is small and it fits
+        cls = warp_class(warp_layout(false, T, U, nva, 5, dw, K, in_bytes, acc_bytes, bulk != 0, true).total);
+        if (cls < 0) dw = 0;
+      }
+      if (dw == 0) {
+        const int LH = cluster_table_log2(false, ncap, cl_load);
+        if (lean) lcls = lean_class(lean_layout(T, nva, LH, ncap, K, in_bytes, acc_bytes).total);
+        if (lcls < 0)
+          cls = warp_class(warp_layout(false, T, U, nva, LH, ncap, K, in_bytes, acc_bytes, bulk != 0).total);
+      }
+    } else {
+      dw = 0;
     }
+    if (lane == 0 && lb.span_w) lb.span_w[c] = dw;
     const bool take = cls >= 0 || lcls >= 0;
     // the cluster's share of the slab: its predicted nnz, capped by the bound sum_l min(h_l, n_cap)
     int64_t hb = lane < K ? min64((int64_t)h_pos[p0 + lane], (int64_t)ncap) : 0;
@@ -383,10 +404,10 @@ __global__ void __launch_bounds__(256) k_compact(AClusterView A, const int32_t* 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t features_run(const AClusterView& A, const BView& B, float* X, int32_t* uc, int32_t* h_pos, int sms,
-                         cudaStream_t s) {
+cudaError_t features_run(const AClusterView& A, const BView& B, float* X, int32_t* uc, int32_t* h_pos,
+                         int32_t* span_lo, int32_t* span_w, int sms, cudaStream_t s) {
   if (A.ncl <= 0) return cudaSuccess;
-  k_features<<<grid_for(A.ncl, 8, sms, 8), 256, 0, s>>>(A, B, X, uc, h_pos);
+  k_features<<<grid_for(A.ncl, 8, sms, 8), 256, 0, s>>>(A, B, X, uc, h_pos, span_lo, span_w);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -68,6 +68,7 @@ struct ResolvedOptions {
   int cl_load;  // numeric cluster-table fill limit, percent
   int lean;     // numeric: 1 = warp-per-cluster kernel where it fits
   uint32_t wait_limit;  // mbarrier polls before a bounded wait gives up
+  int dense;            // 1: cluster kernels use the dense accumulator where the output span fits
 };
 ResolvedOptions resolve(const sgc_options* opt);
 

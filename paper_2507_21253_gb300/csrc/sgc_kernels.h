@@ -58,6 +58,8 @@ struct BinOut {
   int64_t* heavy_items;  // nrows
   int32_t* uc_rec;       // ncl: staged B elements per cluster
   int32_t* nout_rec;     // ncl: output-column union size (-1: rows handled row-level)
+  int32_t* span_lo;      // ncl: dense accumulator: smallest output column of the cluster
+  int32_t* span_w;       // ncl: dense accumulator: span width; 0 = the cluster uses the hash table
   int64_t ncl, nrows;
   const int32_t* clist;        // optional: only these clusters (device ids) ...
   const int32_t* clist_count;  // ... and their count (device); both NULL = all clusters
@@ -130,8 +132,8 @@ cudaError_t add_offset_i32(const int32_t* src, int32_t* dst, int64_t n, int32_t 
 cudaError_t add_offset_i64(const int64_t* src, int64_t* dst, int64_t n, int64_t add, cudaStream_t s);
 
 // k_learned.cu
-cudaError_t features_run(const AClusterView& A, const BView& B, float* X, int32_t* uc, int32_t* h_pos, int sms,
-                         cudaStream_t s);
+cudaError_t features_run(const AClusterView& A, const BView& B, float* X, int32_t* uc, int32_t* h_pos,
+                         int32_t* span_lo, int32_t* span_w, int sms, cudaStream_t s);
 cudaError_t targets_run(const AClusterView& A, const int32_t* nout, const int64_t* c_rp, float* y, float* y_tot,
                         int sms, cudaStream_t s);
 cudaError_t mlp_infer_run(const float* params, const float* X, int64_t n, float* yhat, int sms, cudaStream_t s);

@@ -264,3 +264,52 @@ def test_fused_fma_mode(sgc, name, A):
     if A.val.dtype == np.float32:
         Cu = sgc.spgemm(Acl, Ad, sgc.options(fused_fma=0))
         assert np.array_equal(Cf.val.cpu().numpy(), Cu.val.cpu().numpy())
+
+
+def dense_cases():
+    yield "stencil_natural", synth.stencil27_3d(14, 13, 12, seed=5, permute=False)
+    yield "laplacian_natural", synth.laplacian_2d(40, 37).with_values(synth.Stream(4, 1).normal(40 * 37 * 5 - 2 * 77))
+    yield "rand_f32", random_sparse(257, 257, 0.05, 8, "f32")
+    yield "rand_i64", random_sparse(333, 333, 0.04, 9, "i64")
+    yield "stencil_permuted", synth.stencil27_3d(14, 13, 12, seed=5)      # wide spans: hash table
+
+
+DENSE_CASES = list(dense_cases())
+
+
+@pytest.mark.parametrize("layout", [0, 1], ids=["padded", "masked"])
+@pytest.mark.parametrize("staging", [1, 2], ids=["bulk", "ldg"])
+@pytest.mark.parametrize("name,A", DENSE_CASES, ids=[c[0] for c in DENSE_CASES])
+def test_dense_accumulator(sgc, name, A, staging, layout):
+    """Clusters whose output span is at most SGC_DENSE_SPAN_MAX columns accumulate densely
+    over it (no hash table, no ranking); C is the oracle's, FP64 bit-identical."""
+    perm, cptr = synth.fixed_clusters(A.nrows, 8)
+    Ad = dev(sgc, A)
+    Acl = sgc.csr_cluster_build(Ad, perm, cptr, layout)
+    C = sgc.spgemm(Acl, Ad, sgc.options(staging=staging, accumulator=1))
+    compare(C, A, A, exact_f64=(A.val.dtype == np.float64))
+
+
+@pytest.mark.parametrize("name,A", DENSE_CASES[:2], ids=[c[0] for c in DENSE_CASES[:2]])
+def test_dense_accumulator_learned(sgc, name, A):
+    """The learned path with the dense accumulator: a dense cluster never overflows."""
+    import torch
+    perm, cptr = synth.fixed_clusters(A.nrows, 8)
+    Ad = dev(sgc, A)
+    Acl = sgc.csr_cluster_build(Ad, perm, cptr, 1)
+    ncap = torch.ones(Acl.nclusters, dtype=torch.int32, device="cuda")   # capacities far too small
+    L = sgc.LearnedSpgemm(Acl, Ad, ncap=ncap, margin=1.0, opt=sgc.options(accumulator=1))
+    C = L.run()
+    compare(C, A, A, exact_f64=True)
+    assert L.n_overflow == 0
+
+
+def test_dense_accumulator_tall_skinny(sgc):
+    """Square x tall-skinny: every cluster's output lies in B's 96 columns."""
+    G = synth.rmat(11, 8, 0.57, 0.19, 0.19, 7, "f64")
+    B = synth.bfs_frontiers(G, 96, 2, 7)
+    Ad, Bd = dev(sgc, G), dev(sgc, B)
+    perm, cptr = sgc.hcluster_reorder_parallel(Ad)
+    Acl = sgc.csr_cluster_build(Ad, perm, cptr)
+    C = sgc.spgemm(Acl, Bd, sgc.options(accumulator=1))
+    compare(C, G, B, exact_f64=True)
