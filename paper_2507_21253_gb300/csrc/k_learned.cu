@@ -346,7 +346,9 @@ __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, co
     if (lane == 0 && lb.span_w) lb.span_w[c] = dw;
     const bool take = cls >= 0 || lcls >= 0;
     // the cluster's share of the slab: its predicted nnz, capped by the bound sum_l min(h_l, n_cap)
-    int64_t hb = lane < K ? min64((int64_t)h_pos[p0 + lane], (int64_t)ncap) : 0;
+    // (a dense cluster: n_cap is its span, which always holds its output columns)
+    const int64_t rowcap = dw > 0 ? (int64_t)dw : (int64_t)ncap;
+    int64_t hb = lane < K ? min64((int64_t)h_pos[p0 + lane], rowcap) : 0;
     hb = warp_sum(hb);
     if (lane == 0) {
       int64_t share = hb;
