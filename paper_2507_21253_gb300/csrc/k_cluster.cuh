@@ -60,7 +60,7 @@ __host__ __device__ inline WarpLayout warp_layout(bool sym, int64_t T, int64_t U
                                                   int K, int in_bytes, int acc_bytes, bool bulk, bool dense = false) {
   WarpLayout L{};
   const int64_t pad_c = bulk ? 6 : 0;
-  int64_t o = 512;  // group header: mbarrier, counters, scan partials, per-row counts, slab base
+  int64_t o = 256;  // group header: mbarrier, counters, scan partials
   L.desc = (int)o;  // numeric: int64 B row start per column, then four int32 arrays
   o += (sym ? 16 : 24) * T;
   o = (o + 15) & ~15ll;
@@ -226,14 +226,11 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
   unsigned char* my = sm + (size_t)gid * region_bytes;
   uint64_t* bar = (uint64_t*)my;
   // group header: [0,8) mbarrier; [8,72) ints: [0] distinct count, [1..8] per-warp flags, [9] cursor;
-  // [72,104) / [104,136) per-warp key min / max; [136,200) per-warp 64-bit scan partials;
-  // [256,384) per-row counts (learned); [384,392) the cluster's slab offset (learned)
+  // [72,104) / [104,136) per-warp key min / max; [136,200) per-warp 64-bit scan partials
   int* hdr = (int*)(my + 8);
   int* wmin = (int*)(my + 72);
   int* wmax = (int*)(my + 104);
   uint64_t* red64 = (uint64_t*)(my + 136);
-  int32_t* rcnt = (int32_t*)(my + 256);  // learned: per-row counts of the cluster
-  int64_t* sbase = (int64_t*)(my + 384);  // learned: the cluster's slab pool offset
   DevStatus* st = (DevStatus*)status;
   const bool bulk = mode == 1;
   if (bulk) {
@@ -676,36 +673,20 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
           const int64_t nn = emit_row<DT>(al, fl, srt, dlo, n_out, C.col, (In*)C.val, out0, expect);
           if (nn != expect && lane == 0) raise(st, DEV_INTERNAL, 33, orow);
         } else {
+          // learned: the row's count, its slab space from the cluster's sub-pool, then
+          // the row there; a row that finds the sub-pool exhausted sends the whole
+          // cluster to the exact path (flagged once)
           const int nn = count_row(fl, n_out);
-          if (lane == 0) rcnt[l] = nn;
-        }
-      }
-      if (lo.active) {
-        // learned: one reservation from the slab pool for the whole cluster, then
-        // each row at the pool offset plus the counts of the rows before it
-        group_sync(gw, gid);
-        if (gt == 0) {
-          int64_t tot = 0;
-          for (int q = 0; q < K; ++q) tot += rcnt[q];
-          const int64_t base = pool_reserve(lo, c, tot);
-          *sbase = base;
-          if (base < 0) {  // pool exhausted: the exact path computes this cluster
-            lo.flag[c] = 1;
-            lo.flist[atomicAdd(lo.flist_count, 1)] = c;
-          }
-        }
-        group_sync(gw, gid);
-        const int64_t base = *sbase;
-        if (base >= 0) {
-          for (int l = wg; l < K; l += gw) {
-            int64_t off = base;
-            for (int q = 0; q < l; ++q) off += rcnt[q];
-            const int64_t nn = emit_row<DT>(acc + l * n_out, flg + l * n_out, srt, dlo, n_out, lo.slab_col,
-                                            (In*)lo.slab_val, off, rcnt[l]);
+          int64_t off = 0;
+          if (lane == 0) off = pool_reserve(lo, c, nn);
+          off = __shfl_sync(FULL, off, 0);
+          if (off < 0) {
+            if (lane == 0 && atomicExch(&lo.flag[c], 1) == 0) lo.flist[atomicAdd(lo.flist_count, 1)] = c;
+          } else {
+            emit_row<DT>(al, fl, srt, dlo, n_out, lo.slab_col, (In*)lo.slab_val, off, nn);
             if (lane == 0) {
-              const int64_t orow = A.perm[p0 + l];
               lo.slab_off[p0 + l] = off;
-              lo.cnt[orow + 1] = nn;
+              lo.cnt[A.perm[p0 + l] + 1] = nn;
             }
           }
         }
