@@ -80,7 +80,7 @@ WORKLOADS = {
                  "FP64, seeded symmetric permutation; hierarchical clustering + CSR_Cluster",
 }
 # the other configurations measured beside the headline, in the order of their definitions
-CONFIGS = ("laplacian64", "rmat16_f32", "rmat16_i64", "batched256", "planted1m")
+CONFIGS = ("laplacian64", "rmat16_f32", "rmat16_i64", "batched256", "planted1m", "tallskinny_rmat18")
 
 
 # ---------------------------------------------------------------------------
@@ -493,6 +493,18 @@ def measure_product(cx: Ctx, name: str, A, B, train_mats, steps: int, warmup: in
         res["clustered_exact_fused_fma"] = {"ms_per_step": round(f_ms, 4),
                                             "gflops": round(job_gflops(flops, world, f_ms), 3),
                                             "numeric_ms": round(float(np.mean(fnum[warmup:])), 4)}
+    if not headline and B.ncols <= 1 << 16:   # the dense accumulator where output spans can be small
+        opt_d = sgc.options(fused_fma=args.fused_fma, cluster_load_pct=args.cluster_load,
+                            cluster_kernel=args.cluster_kernel, max_warps=args.max_warps, accumulator=1)
+        dsym, dnum = cx.timed([lambda: sgc.spgemm_symbolic(Acl, Bd, ws, opt_d, c_row_ptr=rp, sync=False),
+                               lambda: sgc.spgemm_numeric(Acl, Bd, rp, nnz, ws, opt_d, C=C)], warmup + steps)
+        sgc.workspace_status(ws)
+        d_ms = float(np.mean([a + b for a, b in zip(dsym[warmup:], dnum[warmup:])]))
+        res["clustered_exact_dense"] = {"ms_per_step": round(d_ms, 4),
+                                        "gflops": round(job_gflops(flops, world, d_ms), 3),
+                                        "phases_ms": {"symbolic": round(float(np.mean(dsym[warmup:])), 4),
+                                                      "numeric": round(float(np.mean(dnum[warmup:])), 4)},
+                                        "accumulator": "dense over output spans of at most 4096 columns"}
     del C
     torch.cuda.empty_cache()
 
@@ -569,6 +581,8 @@ def measure_product(cx: Ctx, name: str, A, B, train_mats, steps: int, warmup: in
     head_ms = learned["ms_per_step"] if learned else step_ms
     res["speedup_vs_rowwise"] = {"learned": round(row_ms / learned["ms_per_step"], 4) if learned else None,
                                  "exact": round(row_ms / step_ms, 4)}
+    if "clustered_exact_dense" in res:
+        res["speedup_vs_rowwise"]["exact_dense"] = round(row_ms / res["clustered_exact_dense"]["ms_per_step"], 4)
 
     # ---- algorithmic bytes of the numeric launch and its roofline
     ucol = Acl.ucol.cpu().numpy()

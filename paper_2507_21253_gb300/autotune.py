@@ -11,7 +11,9 @@ times each candidate configuration on the batch itself and keeps the fastest:
 * row-hash table fill limit (the size threshold that bins rows into table
   classes) 50% or 75%;
 * threads per cluster: warps per cluster group of the cluster kernel (and per
-  CTA of the row kernels), 8, 4 or 2.
+  CTA of the row kernels), 8, 4 or 2;
+* accumulator type of the cluster kernels: the hash table of output columns,
+  or dense arrays over the output span where it is at most 4096 columns.
 
 The search is coordinate-wise from the library defaults (each dimension swept
 with the others at the best values found so far), so its cost grows with the
@@ -37,9 +39,11 @@ CLUSTERINGS = ("phc8", "hc8", "hc4", "fixed1", "fixed4", "fixed8")
 STAGINGS = (sgc.STAGING_BULK, sgc.STAGING_LDG)
 LOADS = (50, 75)
 WARPS = (8, 4, 2)            # warps per cluster group / per row CTA: threads per cluster
+ACCUMULATORS = (0, 1)        # cluster kernels: hash table (0) or dense over a small output span (1)
 
 # the search space, one dimension at a time; the first value of each is the library default
-SPACE = {"clustering": CLUSTERINGS, "staging": STAGINGS, "load_pct": tuple(reversed(LOADS)), "max_warps": WARPS}
+SPACE = {"clustering": CLUSTERINGS, "staging": STAGINGS, "load_pct": tuple(reversed(LOADS)), "max_warps": WARPS,
+         "accumulator": ACCUMULATORS}
 DEFAULT = {k: v[0] for k, v in SPACE.items()}
 
 
@@ -77,7 +81,7 @@ def time_graph(g: sgc.SpgemmGraph, reps: int) -> float:
 
 def options_of(config: dict) -> sgc.Options:
     return sgc.options(staging=config["staging"], load_pct=config["load_pct"], fused_fma=config.get("fused_fma", 0),
-                       max_warps=config.get("max_warps", 0))
+                       max_warps=config.get("max_warps", 0), accumulator=config.get("accumulator", 0))
 
 
 def tune(packed: sgc.DeviceCsr, reps: int = 3, cache_path: str | None = None, fused_fma: int = 0, space=None,

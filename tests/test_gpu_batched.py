@@ -68,12 +68,13 @@ def test_autotuner_picks_a_valid_config(sgc, tmp_path):
     P, row_off, col_off = sgc.csr_batch_pack([sgc.DeviceCsr.from_host(A) for A in mats])
     cache = str(tmp_path / "tune.json")
     space = {"clustering": ("hc8", "fixed4"), "staging": (sgc.STAGING_BULK, sgc.STAGING_LDG), "load_pct": (75,),
-             "max_warps": (8, 2)}
+             "max_warps": (8, 2), "accumulator": (0, 1)}
     res = autotune.tune(P, reps=2, cache_path=cache, space=space)
     # coordinate search: the start, then one new trial per other value of each dimension
-    assert len(res["trials"]) == 4 and res["best"]["ms"] == min(t["ms"] for t in res["trials"])
+    assert len(res["trials"]) == 5 and res["best"]["ms"] == min(t["ms"] for t in res["trials"])
     assert res["default"] == res["trials"][0]
     assert {t["max_warps"] for t in res["trials"]} == {8, 2}
+    assert {t["accumulator"] for t in res["trials"]} == {0, 1}
     again = autotune.tune(P, reps=2, cache_path=cache, space=space)       # served from the cache
     assert again["best"] == res["best"]
     best = res["best"]
