@@ -201,6 +201,78 @@ __device__ __forceinline__ int64_t emit_row(const typename VT<DT>::Acc* al, cons
   }
   return nn;
 }
+// Step 3 for row l of a cluster: the row's union columns in ascending order
+// (Algorithm 1's loop order).  Each lane loads the descriptor and a_lt of one
+// union column of a chunk of 32; the columns the row has are then taken one
+// by one, lanes over the entries of B row t (local ids from shared memory,
+// values from L2), with the next column's first 32 values loaded while the
+// current one is applied.  Within one B row the ids are distinct, so lanes
+// never collide; each (l, j) is accumulated in ascending k.  A B row of at
+// most 32 entries (the common case) takes one pass without a loop.
+template <int DT, bool FUSED>
+__device__ __forceinline__ void accumulate_row(const WDesc& d, int T32, int l, int K, bool padded,
+                                               const typename VT<DT>::In* av, const typename VT<DT>::In* bval,
+                                               const int32_t* stage_c, typename VT<DT>::Acc* al, uint8_t* fl) {
+  using In = typename VT<DT>::In;
+  const int lane = lane_id();
+  const uint32_t below = (1u << l) - 1u;
+  for (int tb = 0; tb < T32; tb += 32) {
+    const int t = tb + lane;
+    const uint32_t mm = t < T32 ? d.mask[t] : 0u;
+    const bool has = (mm >> l) & 1u;
+    int tn = 0, tc = 0;
+    long long tp = 0;  // the B row's values
+    In ta{};
+    if (has) {
+      tn = d.len[t];
+      tc = d.off_c[t] & 0x7fffffff;
+      tp = (long long)(bval + d.bs[t]);
+      ta = padded ? av[t * K + l] : av[d.aoff[t] + __popc(mm & below)];
+    }
+    unsigned bits = __ballot_sync(FULL, has);
+    if (!bits) continue;
+    int src = __ffs(bits) - 1;
+    int n = __shfl_sync(FULL, tn, src), dc = __shfl_sync(FULL, tc, src);
+    const In* bp = (const In*)__shfl_sync(FULL, tp, src);
+    In a = __shfl_sync(FULL, ta, src);
+    In bv = lane < n ? bp[lane] : In{};
+    while (bits) {
+      bits &= bits - 1;
+      int n2 = 0, dc2 = 0;
+      const In* bp2 = nullptr;
+      In a2{}, bv2{};
+      if (bits) {  // warp-uniform: the next column's descriptor and first values
+        src = __ffs(bits) - 1;
+        n2 = __shfl_sync(FULL, tn, src);
+        dc2 = __shfl_sync(FULL, tc, src);
+        bp2 = (const In*)__shfl_sync(FULL, tp, src);
+        a2 = __shfl_sync(FULL, ta, src);
+        if (lane < n2) bv2 = bp2[lane];
+      }
+      if (n <= 32) {
+        if (lane < n) {
+          const int lid = stage_c[dc + lane];
+          al[lid] = VT<DT>::madd(al[lid], a, bv, FUSED);
+          fl[lid] = 1;
+        }
+      } else {
+        for (int q = lane; q < n; q += 32) {
+          const In b = q < 32 ? bv : bp[q];
+          const int lid = stage_c[dc + q];
+          al[lid] = VT<DT>::madd(al[lid], a, b, FUSED);
+          fl[lid] = 1;
+        }
+      }
+      __syncwarp();  // the next column's lanes read what these lanes wrote
+      n = n2;
+      dc = dc2;
+      bp = bp2;
+      a = a2;
+      bv = bv2;
+    }
+  }
+}
+
 __device__ __forceinline__ int count_row(const uint8_t* fl, int n_out) {
   int nn = 0;
   for (int x0 = 0; x0 < n_out; x0 += 32) {
@@ -609,63 +681,10 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       for (int l = wg; l < K; l += gw) {
         Acc* al = acc + l * n_out;
         uint8_t* fl = flg + l * n_out;
-        const uint32_t below = (1u << l) - 1u;
-        for (int tb = 0; tb < T32; tb += 32) {
-          const int t = tb + lane;
-          const uint32_t mm = t < T32 ? d.mask[t] : 0u;
-          const bool has = (mm >> l) & 1u;
-          int tn = 0, tc = 0;
-          int64_t ts = 0;
-          In ta{};
-          if (has) {
-            tn = d.len[t];
-            tc = d.off_c[t] & 0x7fffffff;
-            ts = d.bs[t];
-            ta = padded ? av[t * K + l] : av[d.aoff[t] + __popc(mm & below)];
-          }
-          unsigned bits = __ballot_sync(FULL, has);
-          if (!bits) continue;
-          int src = __ffs(bits) - 1;
-          int n = __shfl_sync(FULL, tn, src), dc = __shfl_sync(FULL, tc, src);
-          int64_t bs = __shfl_sync(FULL, ts, src);
-          In a = __shfl_sync(FULL, ta, src);
-          In bv = lane < n ? bval[bs + lane] : In{};
-          while (bits) {
-            bits &= bits - 1;
-            int n2 = 0, dc2 = 0;
-            int64_t bs2 = 0;
-            In a2{}, bv2{};
-            if (bits) {  // warp-uniform: the next column's descriptor and first values
-              src = __ffs(bits) - 1;
-              n2 = __shfl_sync(FULL, tn, src);
-              dc2 = __shfl_sync(FULL, tc, src);
-              bs2 = __shfl_sync(FULL, ts, src);
-              a2 = __shfl_sync(FULL, ta, src);
-              if (lane < n2) bv2 = bval[bs2 + lane];
-            }
-            if (fused) {  // kernel-uniform: one arithmetic form per launch
-              for (int q = lane; q < n; q += 32) {
-                const In b = q < 32 ? bv : bval[bs + q];
-                const int lid = stage_c[dc + q];
-                al[lid] = VT<DT>::madd(al[lid], a, b, true);
-                fl[lid] = 1;
-              }
-            } else {
-              for (int q = lane; q < n; q += 32) {
-                const In b = q < 32 ? bv : bval[bs + q];
-                const int lid = stage_c[dc + q];
-                al[lid] = VT<DT>::madd(al[lid], a, b, false);
-                fl[lid] = 1;
-              }
-            }
-            __syncwarp();  // the next column's lanes read what these lanes wrote
-            n = n2;
-            dc = dc2;
-            bs = bs2;
-            a = a2;
-            bv = bv2;
-          }
-        }
+        if (fused)  // kernel-uniform: one arithmetic form per launch
+          accumulate_row<DT, true>(d, T32, l, K, padded, av, bval, stage_c, al, fl);
+        else
+          accumulate_row<DT, false>(d, T32, l, K, padded, av, bval, stage_c, al, fl);
         // ---- 4. emit row l in column order (exact); learned: count it ---------
         if (!lo.active) {
           const int64_t orow = A.perm[p0 + l];
