@@ -222,10 +222,36 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
         if (slot >= 0) vals[slot] = VT<DT>::madd(vals[slot], a, v, FUSED);
       }
     };
+    // Packed step: 32 products of several B rows at once, lane x taking product
+    // p0 + x of the chunk in entry order (ok: it exists).  Lanes may then share
+    // an output column (different B rows), so the numeric updates of one
+    // column are applied in lane order, which is ascending k: lanes with the
+    // same slot take turns, the lowest first.
+    auto process_packed = [&](bool ok, int32_t j, In v, In a) {
+      int slot = -1;
+      bool nw = false;
+      if (ok) {
+        slot = hash_find_or_insert(keys, log2T, j, &nw);
+        if (slot < 0) full = true;
+      }
+      if constexpr (SYM) {
+        cnt += (slot >= 0 && nw);
+      } else {
+        __syncwarp();
+        const unsigned peers = __match_any_sync(FULL, slot);
+        const int turn = __popc(peers & lanemask_lt());
+        if (slot >= 0 && turn == 0) vals[slot] = VT<DT>::madd(vals[slot], a, v, FUSED);
+        for (int r = 1; __any_sync(FULL, slot >= 0 && turn >= r); ++r) {
+          __syncwarp();
+          if (slot >= 0 && turn == r) vals[slot] = VT<DT>::madd(vals[slot], a, v, FUSED);
+        }
+      }
+    };
     // One chunk of up to 32 entries (k, a_ik) of the row, one per lane, B row
-    // [s, e).  The chunk's B rows are prefetched into L2 at once; the entries are
-    // then applied in order, the next entry's first 32 elements in flight while
-    // the current one is hashed.
+    // [s, e).  The chunk's B rows are prefetched into L2 at once.  Chunks of
+    // short B rows (under 16 elements on average) are taken 32 products a step
+    // across B rows; the others one B row at a time, in order, the next
+    // entry's first 32 elements in flight while the current one is hashed.
     auto run_chunk = [&](bool valid, int64_t s, int64_t e, In a) {
       const bool has = valid && e > s;
       if (pf && has) {
@@ -234,6 +260,28 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
       }
       unsigned bits = __ballot_sync(FULL, has);
       if (!bits) return;
+      const int len = has ? (int)min64(e - s, 1 << 24) : 0;
+      const int incl = warp_incl_scan(len);
+      const int P = __shfl_sync(FULL, incl, 31);
+      if (P < 16 * __popc(bits)) {  // warp-uniform
+        const int pre = incl - len;
+        for (int p0 = 0; p0 < P; p0 += 32) {
+          const int p = p0 + lane;
+          // the entry of product p: the last lane whose exclusive prefix is <= p
+          int i = 0;
+#pragma unroll
+          for (int b = 16; b; b >>= 1)
+            if (__shfl_sync(FULL, pre, i + b) <= p) i += b;
+          const int64_t si = __shfl_sync(FULL, s, i);
+          const int pi = __shfl_sync(FULL, pre, i);
+          const In ai = __shfl_sync(FULL, a, i);
+          const bool ok = p < P;
+          const int64_t q = si + (p - pi);
+          process_packed(ok, ok ? B.col[q] : 0, (ok && !SYM) ? ((const In*)B.val)[q] : In{}, ai);
+        }
+        __syncwarp();
+        return;
+      }
       int src = __ffs(bits) - 1;
       int64_t sn = __shfl_sync(FULL, s, src), en = __shfl_sync(FULL, e, src);
       int32_t jn = 0;
@@ -356,6 +404,7 @@ constexpr int HEAVY_SYM_WORDS = 16384;  // 64 KB bitmap: 524288 columns per pass
 constexpr int HEAVY_NUM_W = 16384;      // columns per numeric pass (128 KB of FP64)
 constexpr int HEAVY_CACHE = 2048;       // numeric: a row with at most this many entries keeps them in shared
                                         // memory with a cursor per B row across the column windows
+constexpr int HEAVY_LONG = 64;          // numeric, cached: B rows longer than this are walked by a warp
 
 template <int DT>
 __device__ __forceinline__ void gather_chunk(const ACsrView& Ac, const AClusterView& Acl, int src, int64_t item,
@@ -657,33 +706,46 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
     }
     const bool cached = !SYM && nent <= HEAVY_CACHE;
     const bool pf = ((reinterpret_cast<uintptr_t>(B.col) | reinterpret_cast<uintptr_t>(B.val)) & 15u) == 0;
-    // ---- pass 0: column range of the row's products (and the entry cache)
+    // ---- pass 0: column range of the row's products (and the entry cache).
+    // Cached entries are split by the length of their B row: short rows go
+    // to the front of the cache (one thread walks each), long rows to the back
+    // (one warp walks each, 32 elements a step), so a long B row is never a
+    // chain of dependent loads on one thread.
     int32_t lo = PAD_KEY, hi = -1;
-    int ncache = 0;
+    int nshort = 0, nlong = 0;
     if (tid == 0) *s_run = 0;
     __syncthreads();
     for (int64_t cb = 0; cb < nent; cb += blockDim.x) {
       gather_chunk<DT>(Ac, Acl, SRC, item, cb, s_k, s_a, tmp, s_n, s_run);
-      const int n = *s_n;
-      for (int i = tid; i < n; i += blockDim.x) {
-        const int32_t k = s_k[i];
-        const int64_t s = B.rp[k], e = B.rp[k + 1];
+      const int n = *s_n;  // at most blockDim: one entry a thread
+      int64_t s = 0, e = 0;
+      if (tid < n) {
+        const int32_t k = s_k[tid];
+        s = B.rp[k];
+        e = B.rp[k + 1];
         if (e > s) {
           lo = min(lo, B.col[s]);
           hi = max(hi, B.col[e - 1]);
         }
-        if (cached) {
-          c_a[ncache + i] = s_a[i];
-          c_pos[ncache + i] = s;
-          c_end[ncache + i] = e;
-          c_next[ncache + i] = e > s ? B.col[s] : -1;
+      }
+      if (cached) {
+        const bool isl = tid < n && e - s > HEAVY_LONG, iss = tid < n && !isl;
+        int64_t tot;
+        const int64_t ex = block_excl_scan<int64_t>((int64_t)iss | ((int64_t)isl << 32), tmp, &tot);
+        if (tid < n) {
+          const int idx = iss ? nshort + (int)(ex & 0xffffffff) : HEAVY_CACHE - 1 - (nlong + (int)(ex >> 32));
+          c_a[idx] = s_a[tid];
+          c_pos[idx] = s;
+          c_end[idx] = e;
+          c_next[idx] = e > s ? B.col[s] : -1;
           if (pf && e > s) {  // the windows walk these B rows: bring them into L2 now
             bulk_prefetch_row(B.col, s, e - s, 4, B.nnz);
             bulk_prefetch_row(B.val, s, e - s, (int)sizeof(In), B.nnz);
           }
         }
+        nshort += (int)(tot & 0xffffffff);
+        nlong += (int)(tot >> 32);
       }
-      ncache += n;
       __syncthreads();
     }
     lo = warp_min(lo);
@@ -717,11 +779,11 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
       if (tid == 0) *s_run = 0;
       __syncthreads();
       if (cached) {
-        // thread per cached entry: its B row from the cursor to the window's end.  The
-        // column at the cursor is kept in shared memory, so an entry with nothing in
-        // this window costs no global load; the value of the current column and the
-        // next column id are loaded together.
-        for (int i = tid; i < ncache; i += blockDim.x) {
+        // short entries, thread per entry: its B row from the cursor to the
+        // window's end.  The column at the cursor is kept in shared memory, so
+        // an entry with nothing in this window costs no global load; the value
+        // of the current column and the next column id are loaded together.
+        for (int i = tid; i < nshort; i += blockDim.x) {
           int32_t j = c_next[i];
           if (j < 0 || j >= wend) continue;
           int64_t q = c_pos[i];
@@ -739,6 +801,38 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
           }
           c_pos[i] = q;
           c_next[i] = j;
+        }
+        // long entries, warp per entry: 32 consecutive elements from the cursor a
+        // step; the columns are ascending, so the ones in the window are a prefix
+        for (int x = w; x < nlong; x += nw) {
+          const int i = HEAVY_CACHE - 1 - x;
+          const int32_t j0 = c_next[i];
+          if (j0 < 0 || j0 >= wend) continue;
+          int64_t q = c_pos[i];
+          const int64_t e = c_end[i];
+          const In a = c_a[i];
+          int32_t jn = -1;
+          for (;;) {
+            const int64_t qq = q + lane;
+            const int32_t j = qq < e ? B.col[qq] : PAD_KEY;
+            const bool in = qq < e && j < wend;
+            if (in) {
+              const int o = (int)(j - base);
+              atomicOr(&bits[o >> 5], 1u << (o & 31));
+              VT<DT>::atomic_add(&acc[o], VT<DT>::mul(a, ((const In*)B.val)[qq]));
+            }
+            const int nin = __popc(__ballot_sync(FULL, in));
+            const int32_t jx = __shfl_sync(FULL, j, nin & 31);
+            q += nin;
+            if (nin < 32) {
+              jn = q < e ? jx : -1;
+              break;
+            }
+          }
+          if (lane == 0) {
+            c_pos[i] = q;
+            c_next[i] = jn;
+          }
         }
         __syncthreads();
       }
