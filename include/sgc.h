@@ -26,7 +26,7 @@
  *    structure of Sec. 2.2).  FP32 products are accumulated in FP64 and
  *    rounded once; FP64 accumulates in ascending k per (i, j), without FMA
  *    unless sgc_options.fused_fma = 1, except rows computed row by row with
- *    more than 768 outputs (see SGC_HEAVY_ROW_OUTPUTS); int64 wraps modulo 2^64.
+ *    more than SGC_WARP_ROW_OUTPUTS outputs; int64 wraps modulo 2^64.
  *  - Errors: SGC_INVALID_ARG (null pointer, negative or inconsistent size),
  *    SGC_UNSUPPORTED (dtype mismatch, cluster larger than 32 rows),
  *    SGC_WORKSPACE_TOO_SMALL, SGC_CUDA_ERROR (a CUDA call failed; the CUDA
@@ -76,13 +76,16 @@ enum {
 };
 
 /* Rows computed row by row (the row-wise method, and rows of clusters too
- * large for the cluster kernel) use one warp and a per-warp hash table up to
- * 768 outputs; above that one CTA and a CTA-wide hash table updated with
- * shared-memory atomics; above SGC_HEAVY_ROW_OUTPUTS outputs (4x that many
- * possible outputs in the symbolic phase) a heavy-row CTA with a dense
- * accumulator over column windows, also with atomics.  FP64 values of rows
- * with more than 768 outputs therefore depend on the order of atomic adds,
- * within the FP64 bound; int64 stays exact. */
+ * large for the cluster kernel) use one warp and a per-warp hash table of at
+ * most 1024 slots filled to at most min(load_pct, 66)% (numeric), that is up
+ * to SGC_WARP_ROW_OUTPUTS outputs at the default load_pct; above that one CTA
+ * and a CTA-wide hash table updated with shared-memory atomics; above
+ * SGC_HEAVY_ROW_OUTPUTS outputs (4x that many possible outputs in the
+ * symbolic phase) a heavy-row CTA with a dense accumulator over column
+ * windows, also with atomics.  FP64 values of rows with more outputs than
+ * the warp tables take therefore depend on the order of atomic adds, within
+ * the FP64 bound; int64 stays exact. */
+#define SGC_WARP_ROW_OUTPUTS 675
 #define SGC_HEAVY_ROW_OUTPUTS 6144
 
 /* CSR matrix (Sec. 2.1: row-id / col-id / value arrays). */

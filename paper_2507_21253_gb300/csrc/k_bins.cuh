@@ -12,37 +12,74 @@
 
 namespace sgc {
 
-__device__ __forceinline__ void push_dense(const BinOut& o, int b, int32_t c) {
-  const int32_t idx = atomicAdd(&o.count[b], 1);
-  o.dense_items[(int64_t)b * o.ncl + idx] = c;
-}
-__device__ __forceinline__ void push_lean(const BinOut& o, int b, int32_t c) {
-  const int32_t idx = atomicAdd(&o.count[BIN_LEAN0 + b], 1);
-  o.lean_items[(int64_t)b * o.ncl + idx] = c;
-}
-__device__ __forceinline__ void push_row(const BinOut& o, int lg, int64_t item) {
-  const int b = lg - LOG2T_MIN;
-  const int32_t idx = atomicAdd(&o.count[NDB + b], 1);
-  o.row_items[(int64_t)b * o.nrows + idx] = item;
-}
-__device__ __forceinline__ void push_heavy(const BinOut& o, int64_t item) {
-  const int32_t idx = atomicAdd(&o.count[BIN_HEAVY], 1);
-  o.heavy_items[idx] = item;
+// Bin of one row (an index into o.count: a table-size bin or BIN_HEAVY) by its
+// bound h (symbolic) or exact count (numeric); h > 0.  Numeric rows that a warp
+// takes get a table at most ROW_NUM_LOAD full, so that the ranking scratch fits
+// in the table's free slots (k_row_hash); larger rows keep load_pct and go to
+// the CTA-per-row kernel.
+constexpr int ROW_NUM_LOAD = 66;
+__device__ __forceinline__ int row_bin(int64_t h, int64_t heavy_limit, int load_pct, int lg_max, bool num) {
+  if (h > heavy_limit) return BIN_HEAVY;
+  int lg = table_log2(h, num && load_pct > ROW_NUM_LOAD ? ROW_NUM_LOAD : load_pct);
+  if (num && lg > WARP_LG_MAX) {
+    lg = table_log2(h, load_pct);
+    if (lg <= WARP_LG_MAX) lg = WARP_LG_MAX + 1;
+  }
+  return lg > lg_max ? BIN_HEAVY : NDB + (lg - LOG2T_MIN);
 }
 
-// Classify one row by its bound h (symbolic) or exact count (numeric); h > 0.
-__device__ __forceinline__ void classify_row(const BinOut& o, int64_t item, int64_t h, int64_t heavy_limit,
-                                             int load_pct, int lg_max) {
-  if (h > heavy_limit) {
-    push_heavy(o, item);
-    return;
-  }
-  const int lg = table_log2(h, load_pct);
-  if (lg > lg_max)
-    push_heavy(o, item);
+// Warp-collective push of the lanes' items (ok: this lane has one) into their
+// bins (an index into o.count): one atomic per bin and warp, the lanes of one
+// bin taking consecutive slots.  Cluster classes hold cluster ids, row bins
+// row items.
+__device__ __forceinline__ void push_items(const BinOut& o, bool ok, int bin, int64_t item) {
+  if (!__any_sync(FULL, ok)) return;
+  const unsigned peers = __match_any_sync(FULL, ok ? bin : -1);
+  if (!ok) return;
+  const int leader = __ffs(peers) - 1;
+  int32_t base = 0;
+  if (lane_id() == leader) base = atomicAdd(&o.count[bin], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  const int32_t idx = base + __popc(peers & lanemask_lt());
+  if (bin < NDB)
+    o.dense_items[(int64_t)bin * o.ncl + idx] = (int32_t)item;
+  else if (bin < BIN_HEAVY)
+    o.row_items[(int64_t)(bin - NDB) * o.nrows + idx] = item;
+  else if (bin == BIN_HEAVY)
+    o.heavy_items[idx] = item;
   else
-    push_row(o, lg, item);
+    o.lean_items[(int64_t)(bin - BIN_LEAN0) * o.ncl + idx] = (int32_t)item;
 }
+__device__ __forceinline__ void push_rows(const BinOut& o, bool ok, int bin, int64_t item) {
+  push_items(o, ok, bin, item);
+}
+
+// A warp's single pushes (one per cluster: its class, or the row of a one-row
+// cluster) wait in lane j of the warp for the warp's j-th cluster and go out
+// together every 32 clusters.
+struct DeferredPush {
+  int n = 0;
+  bool ok = false;
+  int bin = 0;
+  int64_t item = 0;
+  __device__ __forceinline__ void add(int b, int64_t it) {  // warp-uniform call
+    if (lane_id() == n) {
+      ok = true;
+      bin = b;
+      item = it;
+    }
+    ++n;
+  }
+  __device__ __forceinline__ void skip() { ++n; }
+  __device__ __forceinline__ void flush_if_full(const BinOut& o) {
+    if (n == 32) flush(o);
+  }
+  __device__ __forceinline__ void flush(const BinOut& o) {
+    push_items(o, ok, bin, item);
+    ok = false;
+    n = 0;
+  }
+};
 
 // ---- cluster path, symbolic: warp per cluster ------------------------------
 // Output span of the cluster's B rows (their first and last columns), warp-reduced.
@@ -64,6 +101,7 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   const int64_t nitems = o.clist ? (int64_t)*o.clist_count : A.ncl;
+  DeferredPush dp;
   for (int64_t q = gw; q < nitems; q += nwarps) {
     const int64_t c = o.clist ? (int64_t)o.clist[q] : q;
     const int64_t p0 = A.cptr[c];
@@ -118,18 +156,36 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
         o.span_w[c] = dw;
         o.span_lo[c] = dw > 0 ? jl : 0;
       }
-      if (cls >= 0) push_dense(o, cls, (int32_t)c);
     }
-    if (cls < 0 && lane < K) {
-      const int64_t ub = K == 1 ? U : ubr + (int64_t)s_ub[w][lane];
-      const int64_t row = A.perm[p0 + lane];
-      if (ub == 0)
-        c_rp[row + 1] = 0;
-      else
-        classify_row(o, (c << 5) | lane, min64(ub, B.ncols), HEAVY_SYM, load_pct, SYM_LG_MAX);
+    if (cls >= 0) {
+      dp.add(cls, c);
+    } else if (K == 1) {  // the row of a one-row cluster: its bound is U
+      if (U == 0) {
+        if (lane == 0) c_rp[A.perm[p0] + 1] = 0;
+        dp.skip();
+      } else {
+        dp.add(row_bin(min64(U, B.ncols), HEAVY_SYM, load_pct, SYM_LG_MAX, false), c << 5);
+      }
+    } else {
+      bool ok = false;
+      int bin = 0;
+      if (lane < K) {
+        const int64_t ub = ubr + (int64_t)s_ub[w][lane];
+        const int64_t row = A.perm[p0 + lane];
+        if (ub == 0) {
+          c_rp[row + 1] = 0;
+        } else {
+          ok = true;
+          bin = row_bin(min64(ub, B.ncols), HEAVY_SYM, load_pct, SYM_LG_MAX, false);
+        }
+      }
+      push_rows(o, ok, bin, (c << 5) | lane);
+      dp.skip();
     }
+    dp.flush_if_full(o);
     __syncwarp();
   }
+  dp.flush(o);
 }
 
 // ---- cluster path, numeric: warp per cluster -------------------------------
@@ -139,6 +195,7 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, 
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   const int64_t nitems = o.clist ? (int64_t)*o.clist_count : A.ncl;
+  DeferredPush dp;
   for (int64_t q = gw; q < nitems; q += nwarps) {
     const int64_t c = o.clist ? (int64_t)o.clist[q] : q;
     const int64_t p0 = A.cptr[c];
@@ -179,44 +236,73 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, 
       o.span_w[c] = dw;
       o.span_lo[c] = dw > 0 ? jl : 0;
     }
+    // (warp-uniform branches: lcls and cls are)
     if (lcls >= 0) {
-      if (lane == 0) push_lean(o, lcls, (int32_t)c);
+      dp.add(BIN_LEAN0 + lcls, c);
     } else if (cls >= 0) {
-      if (lane == 0) push_dense(o, cls, (int32_t)c);
-    } else if (lane < K) {
-      const int64_t row = A.perm[p0 + lane];
+      dp.add(cls, c);
+    } else if (K == 1) {
+      const int64_t row = A.perm[p0];
       const int64_t cnt = c_rp[row + 1] - c_rp[row];
-      if (cnt > 0) classify_row(o, (c << 5) | lane, cnt, HEAVY_NUM, load_pct, NUM_LG_MAX);
+      if (cnt > 0)
+        dp.add(row_bin(cnt, HEAVY_NUM, load_pct, NUM_LG_MAX, true), c << 5);
+      else
+        dp.skip();
+    } else {
+      bool ok = false;
+      int bin = 0;
+      if (lane < K) {
+        const int64_t row = A.perm[p0 + lane];
+        const int64_t cnt = c_rp[row + 1] - c_rp[row];
+        ok = cnt > 0;
+        if (ok) bin = row_bin(cnt, HEAVY_NUM, load_pct, NUM_LG_MAX, true);
+      }
+      push_rows(o, ok, bin, (c << 5) | lane);
+      dp.skip();
     }
+    dp.flush_if_full(o);
   }
+  dp.flush(o);
 }
 
 // ---- row-wise path, symbolic: warp per row ---------------------------------
 static __global__ void __launch_bounds__(256) k_bin_rows_sym(ACsrView A, BView B, int64_t* c_rp, BinOut o, int load_pct,
                                                               int64_t heavy_limit, int lg_max) {
+  // a warp takes 32 consecutive rows: their bounds one row at a time (lanes over
+  // the row's entries), then the 32 rows are binned together
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
-  for (int64_t r = gw; r < A.nrows; r += nwarps) {
-    int64_t ub = 0;
-    for (int64_t p = A.rp[r] + lane; p < A.rp[r + 1]; p += 32) {
-      const int32_t k = A.col[p];
-      ub += B.rp[k + 1] - B.rp[k];
+  for (int64_t r0 = gw * 32; r0 < A.nrows; r0 += nwarps * 32) {
+    const int nr = (int)min64(32, A.nrows - r0);
+    int64_t mine = 0, rs = 0, re = 0;
+    if (lane < nr) {
+      rs = A.rp[r0 + lane];
+      re = A.rp[r0 + lane + 1];
     }
-    ub = warp_sum(ub);
-    if (lane == 0) {
-      if (ub == 0)
-        c_rp[r + 1] = 0;
-      else
-        classify_row(o, r, min64(ub, B.ncols), heavy_limit, load_pct, lg_max);
+    for (int i = 0; i < nr; ++i) {
+      const int64_t s = __shfl_sync(FULL, rs, i), e = __shfl_sync(FULL, re, i);
+      int64_t ub = 0;
+      for (int64_t p = s + lane; p < e; p += 32) {
+        const int32_t k = A.col[p];
+        ub += B.rp[k + 1] - B.rp[k];
+      }
+      ub = warp_sum(ub);
+      if (lane == i) mine = ub;
     }
+    const bool ok = lane < nr && mine > 0;
+    if (lane < nr && mine == 0) c_rp[r0 + lane + 1] = 0;
+    push_rows(o, ok, ok ? row_bin(min64(mine, B.ncols), heavy_limit, load_pct, lg_max, false) : 0, r0 + lane);
   }
 }
 
 // ---- row-wise path, numeric: thread per row --------------------------------
 static __global__ void __launch_bounds__(256) k_bin_rows_num(int64_t nrows, const int64_t* c_rp, BinOut o, int load_pct) {
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t cnt = c_rp[r + 1] - c_rp[r];
-    if (cnt > 0) classify_row(o, r, cnt, HEAVY_NUM, load_pct, NUM_LG_MAX);
+  // whole warps step together (push_rows is warp-collective)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t rb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); rb < nrows; rb += stride) {
+    const int64_t r = rb + lane_id();
+    const int64_t cnt = r < nrows ? c_rp[r + 1] - c_rp[r] : 0;
+    push_rows(o, cnt > 0, cnt > 0 ? row_bin(cnt, HEAVY_NUM, load_pct, NUM_LG_MAX, true) : 0, r);
   }
 }
 

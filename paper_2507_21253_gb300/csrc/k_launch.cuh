@@ -35,13 +35,17 @@ cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const B
                             int64_t* c_rp, const BinOut& bins, void* status, const Launch& L) {
   using Acc = typename VT<DT>::Acc;
   auto kh = L.o.fused ? k_row_hash<SYM, DT, SRC, true> : k_row_hash<SYM, DT, SRC, false>;
-  auto kb = k_row_block<SYM, DT, SRC>;
+  auto kb256 = k_row_block<SYM, DT, SRC, 256>;
+  auto kb512 = k_row_block<SYM, DT, SRC, 512>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = allow_smem(k_row_hash<SYM, DT, SRC, true>);
     if (e == cudaSuccess) e = allow_smem(k_row_hash<SYM, DT, SRC, false>);
-    if (e == cudaSuccess) e = allow_smem(kb);
+    if (e == cudaSuccess) e = allow_smem(kb256);
+    if (e == cudaSuccess) e = allow_smem(kb512);
+    if (e == cudaSuccess) e = allow_smem(k_row_heavy<SYM, DT, SRC>);
     if (e != cudaSuccess) return e;
+    attr = true;
   }
   const int lg_top = SYM ? SYM_LG_MAX : NUM_LG_MAX;
   for (int lg = LOG2T_MIN; lg <= lg_top; ++lg) {
@@ -50,28 +54,42 @@ cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const B
     const int32_t* cnt = bins.count + NDB + b;
     if (lg > WARP_LG_MAX) {
       const size_t smem = row_block_smem(lg, SYM, sizeof(Acc));
-      const int occ = occupancy(kb, BLOCK_ROW_THREADS, smem);
+      const int nt = block_row_threads(lg, SYM);
+      auto kb = nt == 256 ? kb256 : kb512;
+      const int occ = occupancy(kb, nt, smem);
       const unsigned grid = grid_for(bins.nrows, 1, L.sms, occ);
-      kb<<<grid, BLOCK_ROW_THREADS, smem, L.s>>>(Ac, Acl, B, C, c_rp, items, cnt, lg, status);
+      kb<<<grid, nt, smem, L.s>>>(Ac, Acl, B, C, c_rp, items, cnt, lg, status);
       note_launches(1);
       continue;
     }
+    // warps a CTA: the most resident warps per SM, at most max_warps a CTA
+    // (several small CTAs fill an SM's shared memory more closely than one large)
+    // (cached per kernel form, table size and cap: the queries cost host time)
     const size_t per_warp = row_hash_smem(1, lg, SYM, sizeof(Acc));
-    int warps = L.o.max_warps;
-    while (warps > 1 && (size_t)warps * per_warp > (size_t)SMEM_MAX) --warps;
+    static int pick_w[2][LOG2T_MAX + 1][9], pick_o[2][LOG2T_MAX + 1][9];
+    const int fz = L.o.fused ? 1 : 0, mw = L.o.max_warps < 1 ? 1 : (L.o.max_warps > 8 ? 8 : L.o.max_warps);
+    if (pick_w[fz][lg][mw] == 0) {
+      int bw = 1, bo = 1, best = 0;
+      for (int wc = mw; wc >= 1; --wc) {
+        if ((size_t)wc * per_warp > (size_t)SMEM_MAX) continue;
+        const int o = occupancy(kh, wc * 32, (size_t)wc * per_warp);
+        if (o * wc > best) {
+          best = o * wc;
+          bw = wc;
+          bo = o;
+        }
+      }
+      pick_o[fz][lg][mw] = bo;
+      pick_w[fz][lg][mw] = bw;
+    }
+    const int warps = pick_w[fz][lg][mw], occ = pick_o[fz][lg][mw];
     const size_t smem = (size_t)warps * per_warp;
-    const int occ = occupancy(kh, warps * 32, smem);
     const unsigned grid = grid_for(bins.nrows, warps, L.sms, occ);
     kh<<<grid, warps * 32, smem, L.s>>>(Ac, Acl, B, C, c_rp, items, cnt, lg, L.o.fused, L.mode == 1, status);
     note_launches(1);
   }
   auto kv = k_row_heavy<SYM, DT, SRC>;
   const size_t hsmem = row_heavy_smem(SYM, sizeof(Acc));
-  if (!attr) {
-    cudaError_t e = allow_smem(kv);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   const int occ = occupancy(kv, HEAVY_THREADS, hsmem);
   const unsigned grid = grid_for(bins.nrows, 1, L.sms, occ);
   kv<<<grid, HEAVY_THREADS, hsmem, L.s>>>(Ac, Acl, B, C, c_rp, bins.heavy_items, bins.count + BIN_HEAVY, status);

@@ -117,42 +117,41 @@ __device__ __forceinline__ int interp_bucket(const Interp& ip, int32_t key) {
   return b < ip.n - 1 ? b : ip.n - 1;
 }
 
-__device__ __forceinline__ Interp warp_rank_prepare(const int32_t* keys, int n, int32_t* bst, int32_t* bcur,
-                                                    int32_t* srt) {
+// Warp ranking of the n distinct keys[0, n) with nb buckets: bend[0, nb) and
+// srt[0, n) of scratch.  After the call bucket b holds srt[bend[b-1], bend[b])
+// (bend[-1] = 0), the keys of bucket b in any order.
+__device__ __forceinline__ Interp warp_rank_prepare(const int32_t* keys, int n, int nb, int32_t* bend, int32_t* srt) {
   const int lane = lane_id();
   int32_t kmin = PAD_KEY, kmax = -1;
   for (int x = lane; x < n; x += 32) {
     kmin = min(kmin, keys[x]);
     kmax = max(kmax, keys[x]);
-    bst[x] = 0;
   }
+  for (int x = lane; x < nb; x += 32) bend[x] = 0;
   kmin = warp_min(kmin);
   kmax = warp_max(kmax);
-  const Interp ip = interp_make(kmin, kmax, n);
+  const Interp ip = interp_make(kmin, kmax, nb);
   __syncwarp();
-  for (int x = lane; x < n; x += 32) atomicAdd(&bst[interp_bucket(ip, keys[x])], 1);
+  for (int x = lane; x < n; x += 32) atomicAdd(&bend[interp_bucket(ip, keys[x])], 1);
   __syncwarp();
-  int carry = 0;
-  for (int x0 = 0; x0 < n; x0 += 32) {
+  int carry = 0;  // bucket starts
+  for (int x0 = 0; x0 < nb; x0 += 32) {
     const int x = x0 + lane;
-    const int v = x < n ? bst[x] : 0;
-    const int ex = warp_incl_scan(v) - v;
-    if (x < n) {
-      bst[x] = carry + ex;
-      bcur[x] = carry + ex;
-    }
-    carry += __shfl_sync(FULL, ex + v, 31);
+    const int v = x < nb ? bend[x] : 0;
+    const int incl = warp_incl_scan(v);
+    if (x < nb) bend[x] = carry + incl - v;
+    carry += __shfl_sync(FULL, incl, 31);
   }
   __syncwarp();
-  for (int x = lane; x < n; x += 32) srt[atomicAdd(&bcur[interp_bucket(ip, keys[x])], 1)] = keys[x];
+  // placement: the cursors run from each bucket's start to its end
+  for (int x = lane; x < n; x += 32) srt[atomicAdd(&bend[interp_bucket(ip, keys[x])], 1)] = keys[x];
   __syncwarp();
   return ip;
 }
 
-__device__ __forceinline__ int warp_rank_of(int32_t key, const Interp& ip, const int32_t* bst, const int32_t* bcur,
-                                            const int32_t* srt) {
+__device__ __forceinline__ int warp_rank_of(int32_t key, const Interp& ip, const int32_t* bend, const int32_t* srt) {
   const int b = interp_bucket(ip, key);
-  const int bs = bst[b], be = bcur[b];
+  const int bs = b > 0 ? bend[b - 1] : 0, be = bend[b];
   int r = bs;
   for (int y = bs; y < be; ++y) r += srt[y] < key;
   return r;
@@ -171,8 +170,9 @@ __device__ __forceinline__ void bulk_prefetch_row(const void* base, int64_t s, i
 // The bounds of the B rows of 32 entries of the A row are loaded at once, so
 // the warp has 32 independent loads in flight instead of one B row at a time.
 // items: int64 row items of one bin; count at *count_ptr.
-// Shared memory per warp: keys[T], and for numeric vals[T] plus 3*T ints of
-// ranking scratch.
+// Shared memory per warp: keys[T], and for numeric vals[T].  The numeric
+// ranking scratch lives in the table's free slots after compaction (the table
+// is binned at most ROW_NUM_LOAD full, so they hold it).
 // ---------------------------------------------------------------------------
 template <bool SYM, int DT, int SRC, bool FUSED>
 __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl, BView B, CView C,
@@ -187,7 +187,6 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
   const int w = threadIdx.x >> 5, lane = lane_id();
   int32_t* keys = (int32_t*)sm + (size_t)w * T;
   Acc* vals = SYM ? nullptr : (Acc*)(sm + (size_t)warps * T * 4) + (size_t)w * T;
-  int32_t* scr = SYM ? nullptr : (int32_t*)(sm + (size_t)warps * T * (4 + sizeof(Acc))) + (size_t)w * 3 * T;
   DevStatus* st = (DevStatus*)status;
   const int32_t count = *count_ptr;
   for (int64_t it = (int64_t)blockIdx.x * warps + w; it < count; it += (int64_t)gridDim.x * warps) {
@@ -373,12 +372,18 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
         if (lane == 0) raise(st, DEV_INTERNAL, 11, row);
         continue;
       }
-      int32_t* bst = scr;
-      int32_t* bcur = scr + T;
-      int32_t* srt = scr + 2 * T;
-      const Interp ip = warp_rank_prepare(keys, n, bst, bcur, srt);
+      // scratch in the free slots: bucket ends over keys[n, n + nb), the bucketed
+      // keys over vals[n, T) (8 bytes a slot hold two ints)
+      if (n > 2 * (T - n) || T - n < 2) {  // binned with a fuller table: refuse, do not overflow
+        if (lane == 0) raise(st, DEV_INTERNAL, 14, row);
+        continue;
+      }
+      const int nb = max(1, min(n >> 1, T - n - 1));
+      int32_t* bend = keys + n;
+      int32_t* srt = (int32_t*)(vals + n);
+      const Interp ip = warp_rank_prepare(keys, n, nb, bend, srt);
       for (int x = lane; x < n; x += 32) {
-        const int r = warp_rank_of(keys[x], ip, bst, bcur, srt);
+        const int r = warp_rank_of(keys[x], ip, bend, srt);
         C.col[out0 + r] = keys[x];
         ((In*)C.val)[out0 + r] = VT<DT>::out(vals[x]);
       }
@@ -388,8 +393,7 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
 }
 
 inline size_t row_hash_smem(int warps, int log2T, bool sym, int acc_bytes) {
-  return (size_t)warps * ((size_t)4 << log2T) +
-         (sym ? 0 : (size_t)warps * ((size_t)(acc_bytes + 12) << log2T));
+  return (size_t)warps * ((size_t)(sym ? 4 : 4 + acc_bytes) << log2T);
 }
 
 // ---------------------------------------------------------------------------
@@ -469,15 +473,20 @@ __device__ __forceinline__ void gather_chunk(const ACsrView& Ac, const AClusterV
 // Shared memory: header (scan scratch, chunk keys, values, prefix, offsets),
 // keys[T], and for numeric vals[T] plus 3*T ints of ranking scratch.
 // ---------------------------------------------------------------------------
-constexpr int BLOCK_ROW_THREADS = 512;
+// Threads a CTA: 256 while four CTAs of 256 fit an SM's shared memory (more
+// rows in flight per SM), 512 above.
 constexpr int BLOCK_ROW_SPT = 16;  // table slots a thread ranks (numeric T <= 16 * threads)
-constexpr size_t BLOCK_ROW_HEAD = 512 + (size_t)BLOCK_ROW_THREADS * (4 + 8) + 8 * (size_t)(BLOCK_ROW_THREADS + 8) +
-                                  8 * (size_t)BLOCK_ROW_THREADS;
+__host__ __device__ constexpr int block_row_threads(int log2T, bool sym) {
+  return log2T <= (sym ? 14 : 11) ? 256 : 512;
+}
+__host__ __device__ constexpr size_t block_row_head(int nt) {
+  return 512 + (size_t)nt * (4 + 8) + 8 * (size_t)(nt + 8) + 8 * (size_t)nt;
+}
 
-template <bool SYM, int DT, int SRC>
-__global__ void __launch_bounds__(BLOCK_ROW_THREADS, 2) k_row_block(ACsrView Ac, AClusterView Acl, BView B, CView C,
-                                                                 int64_t* c_rp_sym, const int64_t* items,
-                                                                 const int32_t* count_ptr, int log2T, void* status) {
+template <bool SYM, int DT, int SRC, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_row_block(ACsrView Ac, AClusterView Acl, BView B, CView C,
+                                                             int64_t* c_rp_sym, const int64_t* items,
+                                                             const int32_t* count_ptr, int log2T, void* status) {
   using In = typename VT<DT>::In;
   using Acc = typename VT<DT>::Acc;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -485,18 +494,20 @@ __global__ void __launch_bounds__(BLOCK_ROW_THREADS, 2) k_row_block(ACsrView Ac,
   int* s_misc = (int*)(sm + 34 * 8);                // [0] chunk size, [1] table full, [2] kmin, [3] kmax
   int64_t* s_run = (int64_t*)(sm + 34 * 8 + 16);    // running MASKED offset
   int32_t* s_k = (int32_t*)(sm + 512);
-  In* s_a = (In*)(sm + 512 + 4 * BLOCK_ROW_THREADS);
-  int64_t* s_pre = (int64_t*)(sm + 512 + 12 * BLOCK_ROW_THREADS);
-  int64_t* s_off = s_pre + BLOCK_ROW_THREADS + 8;
+  In* s_a = (In*)(sm + 512 + 4 * NT);
+  int64_t* s_pre = (int64_t*)(sm + 512 + 12 * NT);
+  int64_t* s_off = s_pre + NT + 8;
+  constexpr size_t HEAD = block_row_head(NT);
   const int T = 1 << log2T;
-  int32_t* keys = (int32_t*)(sm + BLOCK_ROW_HEAD);
-  Acc* vals = (Acc*)(sm + BLOCK_ROW_HEAD + 4 * (size_t)T);
-  int32_t* bst = (int32_t*)(sm + BLOCK_ROW_HEAD + (4 + sizeof(Acc)) * (size_t)T);
+  int32_t* keys = (int32_t*)(sm + HEAD);
+  Acc* vals = (Acc*)(sm + HEAD + 4 * (size_t)T);
+  int32_t* bst = (int32_t*)(sm + HEAD + (4 + sizeof(Acc)) * (size_t)T);
   int32_t* bcur = bst + T;
   int32_t* srt = bcur + T;
   const int tid = threadIdx.x, nt = blockDim.x;
   DevStatus* st = (DevStatus*)status;
   const int32_t count = *count_ptr;
+  const bool pf = ((reinterpret_cast<uintptr_t>(B.col) | reinterpret_cast<uintptr_t>(B.val)) & 15u) == 0;
   for (int64_t it = blockIdx.x; it < count; it += gridDim.x) {
     const int64_t item = items[it];
     const int64_t row = item_row<SRC>(Acl, item);
@@ -528,6 +539,10 @@ __global__ void __launch_bounds__(BLOCK_ROW_THREADS, 2) k_row_block(ACsrView Ac,
         const int32_t k = s_k[tid];
         bs = B.rp[k];
         len = B.rp[k + 1] - bs;
+        if (pf && len > 0) {  // the products below read these B rows: bring them into L2 now
+          bulk_prefetch_row(B.col, bs, len, 4, B.nnz);
+          if (!SYM) bulk_prefetch_row(B.val, bs, len, (int)sizeof(In), B.nnz);
+        }
       }
       int64_t P;
       const int64_t pre = block_excl_scan<int64_t>(len, tmp, &P);
@@ -666,7 +681,8 @@ __global__ void __launch_bounds__(BLOCK_ROW_THREADS, 2) k_row_block(ACsrView Ac,
 }
 
 inline size_t row_block_smem(int log2T, bool sym, int acc_bytes) {
-  return BLOCK_ROW_HEAD + ((size_t)4 << log2T) + (sym ? 0 : ((size_t)(acc_bytes + 12) << log2T));
+  return block_row_head(block_row_threads(log2T, sym)) + ((size_t)4 << log2T) +
+         (sym ? 0 : ((size_t)(acc_bytes + 12) << log2T));
 }
 
 template <bool SYM, int DT, int SRC>

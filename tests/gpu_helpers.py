@@ -6,7 +6,7 @@ from oracle import gustavson as og
 
 TOL_F64 = 1e-12   # |c - c_ref| <= TOL * (|A||B|)_ij
 TOL_F32 = 2e-6
-WARP_ROW_OUTPUTS = 768   # row kernels: warp tables up to this many outputs, atomics above
+WARP_ROW_OUTPUTS = 675   # row kernels: warp tables up to this many outputs (SGC_WARP_ROW_OUTPUTS), atomics above
 
 
 def lib():

@@ -11,7 +11,7 @@ clusters (Algorithm 3), and the row-wise method.  Every row of every result is
 compared with the CPU oracle (the plain serial Gustavson product, Sec. 2.2),
 computed once per block of rows over all host cores: the structure exactly,
 int64 values exactly, FP64 values bit-identical to the oracle except rows
-computed row by row with more than 768 outputs (which stay within
+computed row by row with more than 675 outputs (which stay within
 1e-12 * (|A||B|)_ij), FP32 within 2e-6 * (|A||B|)_ij of the FP64 oracle.
 At 160^3 the numeric phase that stores C straight into pinned host memory
 (4.0 GB of values) and the learned path's compaction into pinned host memory
