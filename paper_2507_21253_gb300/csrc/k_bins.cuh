@@ -102,88 +102,131 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   const int64_t nitems = o.clist ? (int64_t)*o.clist_count : A.ncl;
   DeferredPush dp;
-  for (int64_t q = gw; q < nitems; q += nwarps) {
-    const int64_t c = o.clist ? (int64_t)o.clist[q] : q;
-    const int64_t p0 = A.cptr[c];
-    const int K = (int)(A.cptr[c + 1] - p0);
-    const int64_t u0 = A.uptr[c], u1 = A.uptr[c + 1];
-    s_ub[w][lane] = 0;
-    __syncwarp();
-    int64_t U = 0, ubr = 0;
-    int32_t jl = PAD_KEY, jh = -1;
-    for (int64_t tb = u0; tb < u1; tb += 32) {  // warp-uniform trip count
-      const int64_t t = tb + lane;
-      int64_t len = 0;
-      uint32_t m = 0;
-      if (t < u1) {
-        const int32_t k = A.ucol[t];
-        const int64_t bs = B.rp[k], be = B.rp[k + 1];
-        len = be - bs;
-        m = A.mask[t];
-        if (dense) span_add(B, bs, be, &jl, &jh);
-      }
-      U += len;
-      if (K > 1) add_row_bounds(m, len, K, lane, &ubr, s_ub[w]);  // one row: its bound is U
+  // a warp takes 32 consecutive clusters; one-row clusters of at most 32 union
+  // columns are binned by their lane alone (the row's bound is U), the others
+  // one at a time by the whole warp
+  for (int64_t q0 = gw * 32; q0 < nitems; q0 += nwarps * 32) {
+    const int64_t qq = q0 + lane;
+    int64_t cl = -1, p0l = 0, u0l = 0, u1l = 0;
+    int Kl = 0;
+    if (qq < nitems) {
+      cl = o.clist ? (int64_t)o.clist[qq] : qq;
+      p0l = A.cptr[cl];
+      Kl = (int)(A.cptr[cl + 1] - p0l);
+      u0l = A.uptr[cl];
+      u1l = A.uptr[cl + 1];
     }
-    U = warp_sum(U);
-    __syncwarp();
-    const int64_t T = u1 - u0;
-    int cls = -1;
-    int32_t dw = 0;
-    if (dense) {  // warp-collective: every lane takes part
-      jl = warp_min(jl);
-      jh = warp_max(jh);
-    }
-    // a cluster of one row gains nothing from staging: its row goes to the row kernels
-    if (use_dense && K > 1 && U < (1ll << 28) && T < (1ll << 24)) {
-      if (dense) {  // the dense accumulator when the output span is small and its bitmaps fit
-        dw = span_width(jl, jh);
-        if (dw > 0) {
-          cls = warp_class(warp_layout(true, T, U, 0, 5, dw, K, 4, 8, bulk != 0, true).total);
-          if (cls < 0) dw = 0;
-        }
-      }
-      if (dw == 0) {
-        const int64_t nb = min64(U, B.ncols);
-        const WarpLayout L = warp_layout(true, T, U, 0, cluster_table_log2(true, nb, 0), nb, K, 4, 8, bulk != 0);
-        cls = warp_class(L.total);
-      }
-    }
-    if (lane == 0) {
-      o.uc_rec[c] = (int32_t)min64(U, 0x7fffffff);
-      o.nout_rec[c] = -1;
-      if (o.span_w) {
-        o.span_w[c] = dw;
-        o.span_lo[c] = dw > 0 ? jl : 0;
-      }
-    }
-    if (cls >= 0) {
-      dp.add(cls, c);
-    } else if (K == 1) {  // the row of a one-row cluster: its bound is U
-      if (U == 0) {
-        if (lane == 0) c_rp[A.perm[p0] + 1] = 0;
-        dp.skip();
-      } else {
-        dp.add(row_bin(min64(U, B.ncols), HEAVY_SYM, load_pct, SYM_LG_MAX, false), c << 5);
-      }
-    } else {
+    const bool solo = cl >= 0 && Kl == 1 && u1l - u0l <= 32;
+    {
       bool ok = false;
       int bin = 0;
-      if (lane < K) {
-        const int64_t ub = ubr + (int64_t)s_ub[w][lane];
-        const int64_t row = A.perm[p0 + lane];
-        if (ub == 0) {
-          c_rp[row + 1] = 0;
+      if (solo) {
+        int64_t U = 0;
+#pragma unroll 4
+        for (int64_t t = u0l; t < u1l; ++t) {
+          const int32_t k = A.ucol[t];
+          U += B.rp[k + 1] - B.rp[k];
+        }
+        o.uc_rec[cl] = (int32_t)min64(U, 0x7fffffff);
+        o.nout_rec[cl] = -1;
+        if (o.span_w) {
+          o.span_w[cl] = 0;
+          o.span_lo[cl] = 0;
+        }
+        if (U == 0) {
+          c_rp[A.perm[p0l] + 1] = 0;
         } else {
           ok = true;
-          bin = row_bin(min64(ub, B.ncols), HEAVY_SYM, load_pct, SYM_LG_MAX, false);
+          bin = row_bin(min64(U, B.ncols), HEAVY_SYM, load_pct, SYM_LG_MAX, false);
         }
       }
-      push_rows(o, ok, bin, (c << 5) | lane);
-      dp.skip();
+      push_items(o, ok, bin, cl << 5);
     }
-    dp.flush_if_full(o);
-    __syncwarp();
+    unsigned rest = __ballot_sync(FULL, cl >= 0 && !solo);
+    while (rest) {
+      const int src = __ffs(rest) - 1;
+      rest &= rest - 1;
+      const int64_t c = __shfl_sync(FULL, cl, src), p0 = __shfl_sync(FULL, p0l, src);
+      const int K = __shfl_sync(FULL, Kl, src);
+      const int64_t u0 = __shfl_sync(FULL, u0l, src), u1 = __shfl_sync(FULL, u1l, src);
+      s_ub[w][lane] = 0;
+      __syncwarp();
+      int64_t U = 0, ubr = 0;
+      int32_t jl = PAD_KEY, jh = -1;
+      for (int64_t tb = u0; tb < u1; tb += 32) {  // warp-uniform trip count
+        const int64_t t = tb + lane;
+        int64_t len = 0;
+        uint32_t m = 0;
+        if (t < u1) {
+          const int32_t k = A.ucol[t];
+          const int64_t bs = B.rp[k], be = B.rp[k + 1];
+          len = be - bs;
+          m = A.mask[t];
+          if (dense) span_add(B, bs, be, &jl, &jh);
+        }
+        U += len;
+        if (K > 1) add_row_bounds(m, len, K, lane, &ubr, s_ub[w]);  // one row: its bound is U
+      }
+      U = warp_sum(U);
+      __syncwarp();
+      const int64_t T = u1 - u0;
+      int cls = -1;
+      int32_t dw = 0;
+      if (dense) {  // warp-collective: every lane takes part
+        jl = warp_min(jl);
+        jh = warp_max(jh);
+      }
+      // a cluster of one row gains nothing from staging: its row goes to the row kernels
+      if (use_dense && K > 1 && U < (1ll << 28) && T < (1ll << 24)) {
+        if (dense) {  // the dense accumulator when the output span is small and its bitmaps fit
+          dw = span_width(jl, jh);
+          if (dw > 0) {
+            cls = warp_class(warp_layout(true, T, U, 0, 5, dw, K, 4, 8, bulk != 0, true).total);
+            if (cls < 0) dw = 0;
+          }
+        }
+        if (dw == 0) {
+          const int64_t nb = min64(U, B.ncols);
+          const WarpLayout L = warp_layout(true, T, U, 0, cluster_table_log2(true, nb, 0), nb, K, 4, 8, bulk != 0);
+          cls = warp_class(L.total);
+        }
+      }
+      if (lane == 0) {
+        o.uc_rec[c] = (int32_t)min64(U, 0x7fffffff);
+        o.nout_rec[c] = -1;
+        if (o.span_w) {
+          o.span_w[c] = dw;
+          o.span_lo[c] = dw > 0 ? jl : 0;
+        }
+      }
+      if (cls >= 0) {
+        dp.add(cls, c);
+      } else if (K == 1) {  // the row of a one-row cluster: its bound is U
+        if (U == 0) {
+          if (lane == 0) c_rp[A.perm[p0] + 1] = 0;
+          dp.skip();
+        } else {
+          dp.add(row_bin(min64(U, B.ncols), HEAVY_SYM, load_pct, SYM_LG_MAX, false), c << 5);
+        }
+      } else {
+        bool ok = false;
+        int bin = 0;
+        if (lane < K) {
+          const int64_t ub = ubr + (int64_t)s_ub[w][lane];
+          const int64_t row = A.perm[p0 + lane];
+          if (ub == 0) {
+            c_rp[row + 1] = 0;
+          } else {
+            ok = true;
+            bin = row_bin(min64(ub, B.ncols), HEAVY_SYM, load_pct, SYM_LG_MAX, false);
+          }
+        }
+        push_rows(o, ok, bin, (c << 5) | lane);
+        dp.skip();
+      }
+      dp.flush_if_full(o);
+      __syncwarp();
+    }
   }
   dp.flush(o);
 }
@@ -196,71 +239,104 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, 
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   const int64_t nitems = o.clist ? (int64_t)*o.clist_count : A.ncl;
   DeferredPush dp;
-  for (int64_t q = gw; q < nitems; q += nwarps) {
-    const int64_t c = o.clist ? (int64_t)o.clist[q] : q;
-    const int64_t p0 = A.cptr[c];
-    const int K = (int)(A.cptr[c + 1] - p0);
-    const int64_t T = A.uptr[c + 1] - A.uptr[c];
-    const int32_t nout = o.nout_rec[c];
-    int cls = -1, lcls = -1;
-    int32_t dw = 0, jl = PAD_KEY, jh = -1;
-    if (dense) {  // the output span of the cluster's B rows (warp-collective)
-      const int64_t u0 = A.uptr[c];
-      for (int64_t tb = 0; tb < T; tb += 32) {
-        if (tb + lane < T) {
-          const int32_t k = A.ucol[u0 + tb + lane];
-          span_add(B, B.rp[k], B.rp[k + 1], &jl, &jh);
-        }
-      }
-      jl = warp_min(jl);
-      jh = warp_max(jh);
+  // a warp takes 32 consecutive clusters; one-row clusters left to the row
+  // kernels are binned by their lane alone, the others one at a time by the
+  // whole warp
+  for (int64_t q0 = gw * 32; q0 < nitems; q0 += nwarps * 32) {
+    const int64_t qq = q0 + lane;
+    int64_t cl = -1, p0l = 0;
+    int Kl = 0;
+    int32_t noutl = -1;
+    if (qq < nitems) {
+      cl = o.clist ? (int64_t)o.clist[qq] : qq;
+      p0l = A.cptr[cl];
+      Kl = (int)(A.cptr[cl + 1] - p0l);
+      noutl = o.nout_rec[cl];
     }
-    if (nout >= 0) {
-      const int64_t nva = A.vptr[c + 1] - A.vptr[c];
-      if (dense) {  // the dense accumulator when the output span is small and it fits
-        dw = span_width(jl, jh);
-        if (dw > 0) {
-          cls = warp_class(warp_layout(false, T, o.uc_rec[c], nva, 5, dw, K, in_bytes, acc_bytes, bulk != 0, true)
-                               .total);
-          if (cls < 0) dw = 0;
-        }
-      }
-      if (dw == 0) {
-        const int LH = cluster_table_log2(false, nout, cl_load);
-        if (lean && o.lean_items) lcls = lean_class(lean_layout(T, nva, LH, nout, K, in_bytes, acc_bytes).total);
-        if (lcls < 0) cls = warp_class(warp_layout(false, T, o.uc_rec[c], nva, LH, nout, K, in_bytes, acc_bytes,
-                                                   bulk != 0).total);
-      }
-    }
-    if (lane == 0 && o.span_w) {
-      o.span_w[c] = dw;
-      o.span_lo[c] = dw > 0 ? jl : 0;
-    }
-    // (warp-uniform branches: lcls and cls are)
-    if (lcls >= 0) {
-      dp.add(BIN_LEAN0 + lcls, c);
-    } else if (cls >= 0) {
-      dp.add(cls, c);
-    } else if (K == 1) {
-      const int64_t row = A.perm[p0];
-      const int64_t cnt = c_rp[row + 1] - c_rp[row];
-      if (cnt > 0)
-        dp.add(row_bin(cnt, HEAVY_NUM, load_pct, NUM_LG_MAX, true), c << 5);
-      else
-        dp.skip();
-    } else {
+    const bool solo = cl >= 0 && Kl == 1 && noutl < 0;
+    {
       bool ok = false;
       int bin = 0;
-      if (lane < K) {
-        const int64_t row = A.perm[p0 + lane];
+      if (solo) {
+        if (o.span_w) {
+          o.span_w[cl] = 0;
+          o.span_lo[cl] = 0;
+        }
+        const int64_t row = A.perm[p0l];
         const int64_t cnt = c_rp[row + 1] - c_rp[row];
         ok = cnt > 0;
         if (ok) bin = row_bin(cnt, HEAVY_NUM, load_pct, NUM_LG_MAX, true);
       }
-      push_rows(o, ok, bin, (c << 5) | lane);
-      dp.skip();
+      push_items(o, ok, bin, cl << 5);
     }
-    dp.flush_if_full(o);
+    unsigned rest = __ballot_sync(FULL, cl >= 0 && !solo);
+    while (rest) {
+      const int src = __ffs(rest) - 1;
+      rest &= rest - 1;
+      const int64_t c = __shfl_sync(FULL, cl, src), p0 = __shfl_sync(FULL, p0l, src);
+      const int K = __shfl_sync(FULL, Kl, src);
+      const int64_t T = A.uptr[c + 1] - A.uptr[c];
+      const int32_t nout = __shfl_sync(FULL, noutl, src);
+      int cls = -1, lcls = -1;
+      int32_t dw = 0, jl = PAD_KEY, jh = -1;
+      if (dense) {  // the output span of the cluster's B rows (warp-collective)
+        const int64_t u0 = A.uptr[c];
+        for (int64_t tb = 0; tb < T; tb += 32) {
+          if (tb + lane < T) {
+            const int32_t k = A.ucol[u0 + tb + lane];
+            span_add(B, B.rp[k], B.rp[k + 1], &jl, &jh);
+          }
+        }
+        jl = warp_min(jl);
+        jh = warp_max(jh);
+      }
+      if (nout >= 0) {
+        const int64_t nva = A.vptr[c + 1] - A.vptr[c];
+        if (dense) {  // the dense accumulator when the output span is small and it fits
+          dw = span_width(jl, jh);
+          if (dw > 0) {
+            cls = warp_class(warp_layout(false, T, o.uc_rec[c], nva, 5, dw, K, in_bytes, acc_bytes, bulk != 0, true)
+                                 .total);
+            if (cls < 0) dw = 0;
+          }
+        }
+        if (dw == 0) {
+          const int LH = cluster_table_log2(false, nout, cl_load);
+          if (lean && o.lean_items) lcls = lean_class(lean_layout(T, nva, LH, nout, K, in_bytes, acc_bytes).total);
+          if (lcls < 0) cls = warp_class(warp_layout(false, T, o.uc_rec[c], nva, LH, nout, K, in_bytes, acc_bytes,
+                                                     bulk != 0).total);
+        }
+      }
+      if (lane == 0 && o.span_w) {
+        o.span_w[c] = dw;
+        o.span_lo[c] = dw > 0 ? jl : 0;
+      }
+      // (warp-uniform branches: lcls and cls are)
+      if (lcls >= 0) {
+        dp.add(BIN_LEAN0 + lcls, c);
+      } else if (cls >= 0) {
+        dp.add(cls, c);
+      } else if (K == 1) {
+        const int64_t row = A.perm[p0];
+        const int64_t cnt = c_rp[row + 1] - c_rp[row];
+        if (cnt > 0)
+          dp.add(row_bin(cnt, HEAVY_NUM, load_pct, NUM_LG_MAX, true), c << 5);
+        else
+          dp.skip();
+      } else {
+        bool ok = false;
+        int bin = 0;
+        if (lane < K) {
+          const int64_t row = A.perm[p0 + lane];
+          const int64_t cnt = c_rp[row + 1] - c_rp[row];
+          ok = cnt > 0;
+          if (ok) bin = row_bin(cnt, HEAVY_NUM, load_pct, NUM_LG_MAX, true);
+        }
+        push_rows(o, ok, bin, (c << 5) | lane);
+        dp.skip();
+      }
+      dp.flush_if_full(o);
+    }
   }
   dp.flush(o);
 }
