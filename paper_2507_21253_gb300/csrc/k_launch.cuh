@@ -37,12 +37,14 @@ cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const B
   auto kh = L.o.fused ? k_row_hash<SYM, DT, SRC, true> : k_row_hash<SYM, DT, SRC, false>;
   auto kb256 = k_row_block<SYM, DT, SRC, 256>;
   auto kb512 = k_row_block<SYM, DT, SRC, 512>;
+  auto kb1024 = k_row_block<SYM, DT, SRC, 1024>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = allow_smem(k_row_hash<SYM, DT, SRC, true>);
     if (e == cudaSuccess) e = allow_smem(k_row_hash<SYM, DT, SRC, false>);
     if (e == cudaSuccess) e = allow_smem(kb256);
     if (e == cudaSuccess) e = allow_smem(kb512);
+    if (e == cudaSuccess) e = allow_smem(kb1024);
     if (e == cudaSuccess) e = allow_smem(k_row_heavy<SYM, DT, SRC>);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -55,7 +57,7 @@ cudaError_t launch_row_bins(const ACsrView& Ac, const AClusterView& Acl, const B
     if (lg > WARP_LG_MAX) {
       const size_t smem = row_block_smem(lg, SYM, sizeof(Acc));
       const int nt = block_row_threads(lg, SYM);
-      auto kb = nt == 256 ? kb256 : kb512;
+      auto kb = nt == 256 ? kb256 : (nt == 512 ? kb512 : kb1024);
       const int occ = occupancy(kb, nt, smem);
       const unsigned grid = grid_for(bins.nrows, 1, L.sms, occ);
       kb<<<grid, nt, smem, L.s>>>(Ac, Acl, B, C, c_rp, items, cnt, lg, status);

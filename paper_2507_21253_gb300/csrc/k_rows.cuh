@@ -403,7 +403,7 @@ inline size_t row_hash_smem(int warps, int log2T, bool sym, int acc_bytes) {
 // shared-memory atomics.  The numeric output of a window is emitted in
 // column order by scanning its presence bitmap.
 // ---------------------------------------------------------------------------
-constexpr int HEAVY_THREADS = 512;
+constexpr int HEAVY_THREADS = 1024;
 constexpr int HEAVY_SYM_WORDS = 16384;  // 64 KB bitmap: 524288 columns per pass
 constexpr int HEAVY_NUM_W = 16384;      // columns per numeric pass (128 KB of FP64)
 constexpr int HEAVY_CACHE = 2048;       // numeric: a row with at most this many entries keeps them in shared
@@ -474,10 +474,11 @@ __device__ __forceinline__ void gather_chunk(const ACsrView& Ac, const AClusterV
 // keys[T], and for numeric vals[T] plus 3*T ints of ranking scratch.
 // ---------------------------------------------------------------------------
 // Threads a CTA: 256 while four CTAs of 256 fit an SM's shared memory (more
-// rows in flight per SM), 512 above.
+// rows in flight per SM), 1024 for the largest tables (one CTA an SM: all its
+// warps on the one row), 512 between.
 constexpr int BLOCK_ROW_SPT = 16;  // table slots a thread ranks (numeric T <= 16 * threads)
 __host__ __device__ constexpr int block_row_threads(int log2T, bool sym) {
-  return log2T <= (sym ? 14 : 11) ? 256 : 512;
+  return log2T <= (sym ? 14 : 11) ? 256 : (log2T >= (sym ? 15 : 13) ? 1024 : 512);
 }
 __host__ __device__ constexpr size_t block_row_head(int nt) {
   return 512 + (size_t)nt * (4 + 8) + 8 * (size_t)(nt + 8) + 8 * (size_t)nt;
@@ -766,20 +767,20 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
     }
     lo = warp_min(lo);
     hi = warp_max(hi);
-    if (lane == 0) {
-      tmp[w] = lo;
-      tmp[16 + w] = hi;
-    }
+    // one int64 a warp (up to 32 warps): hi in the upper, lo in the lower half
+    if (lane == 0) tmp[w] = (int64_t)(((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo);
     __syncthreads();
     if (tid == 0) {
-      for (int i = 1; i < nw; ++i) {
-        tmp[0] = min(tmp[0], tmp[i]);
-        tmp[16] = max(tmp[16], tmp[16 + i]);
+      int32_t l0 = PAD_KEY, h0 = -1;
+      for (int i = 0; i < nw; ++i) {
+        l0 = min(l0, (int32_t)(uint32_t)((uint64_t)tmp[i] & 0xffffffffu));
+        h0 = max(h0, (int32_t)(uint32_t)((uint64_t)tmp[i] >> 32));
       }
+      tmp[32] = (int64_t)(((uint64_t)(uint32_t)h0 << 32) | (uint32_t)l0);
     }
     __syncthreads();
-    lo = (int32_t)tmp[0];
-    hi = (int32_t)tmp[16];
+    lo = (int32_t)(uint32_t)((uint64_t)tmp[32] & 0xffffffffu);
+    hi = (int32_t)(uint32_t)((uint64_t)tmp[32] >> 32);
     __syncthreads();
     int64_t total = 0;
     int64_t out0 = 0, expect = 0;
@@ -885,14 +886,15 @@ __global__ void __launch_bounds__(HEAVY_THREADS) k_row_heavy(ACsrView Ac, AClust
         block_excl_scan<int64_t>(c, tmp, &tot);
         total += tot;
       } else {
-        // each thread owns WWORDS / blockDim consecutive words
-        constexpr int WPT = WWORDS / HEAVY_THREADS;
+        // each thread owns WPT consecutive words (threads past the window: none)
+        constexpr int WPT = WWORDS >= HEAVY_THREADS ? WWORDS / HEAVY_THREADS : 1;
+        const int nwp = tid * WPT < WWORDS ? WPT : 0;
         int c = 0;
-        for (int i = 0; i < WPT; ++i) c += __popc(bits[tid * WPT + i]);
+        for (int i = 0; i < nwp; ++i) c += __popc(bits[tid * WPT + i]);
         int64_t tot;
         int64_t pos = block_excl_scan<int64_t>(c, tmp, &tot);
         if (total + tot <= expect) {
-          for (int i = 0; i < WPT; ++i) {
+          for (int i = 0; i < nwp; ++i) {
             uint32_t b = bits[tid * WPT + i];
             while (b) {
               const int bit = __ffs(b) - 1;
