@@ -148,7 +148,12 @@ typedef struct sgc_options {
                                working set fits shared memory accumulates into per-row arrays over that
                                span with presence bits (no hashing, no ranking); other clusters use the
                                hash table */
-  int32_t reserved[6];
+  int32_t spread_max;       /* numeric phase: a cluster whose output-column union times its row count is
+                               more than spread_max times its rows' total output count (its per-row
+                               accumulators would stay mostly empty) has its rows computed by the row
+                               kernels; 0 = default 3; < 0 = never (every cluster that fits shared memory
+                               runs in the cluster kernels) */
+  int32_t reserved[5];
 } sgc_options;
 
 #define SGC_DENSE_SPAN_MAX 4096

@@ -47,6 +47,7 @@ ResolvedOptions resolve(const sgc_options* opt) {
   if (opt && opt->wait_polls > 0) r.wait_limit = (uint32_t)opt->wait_polls;
   if (opt && opt->wait_polls < 0) r.wait_limit = 0;
   r.dense = (opt && opt->accumulator == 1) ? 1 : 0;
+  r.spread_max = !opt || opt->spread_max == 0 ? SPREAD_MAX_DEFAULT : (opt->spread_max < 0 ? 0 : opt->spread_max);
   return r;
 }
 

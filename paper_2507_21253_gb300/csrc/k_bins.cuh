@@ -232,10 +232,9 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_sym(AClusterView A, 
 }
 
 // ---- cluster path, numeric: warp per cluster -------------------------------
-constexpr int64_t SPREAD_MAX = 3;
 static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, BView B, const int64_t* c_rp, BinOut o,
                                                          int load_pct, int bulk, int in_bytes, int acc_bytes,
-                                                         int cl_load, int lean, int dense) {
+                                                         int cl_load, int lean, int dense, int spread_max) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
   const int64_t nitems = o.clist ? (int64_t)*o.clist_count : A.ncl;
@@ -292,15 +291,15 @@ static __global__ void __launch_bounds__(256) k_bin_cluster_num(AClusterView A, 
         jh = warp_max(jh);
       }
       // per-row accumulators over the cluster's output union that would stay
-      // mostly empty (the union more than SPREAD_MAX times the rows' mean output
-      // count): the rows go to the row kernels instead
+      // mostly empty (the union more than spread_max times the rows' mean output
+      // count; 0: no limit): the rows go to the row kernels instead
       int64_t rows_out = 0;
       if (nout >= 0 && lane < K) {
         const int64_t row = A.perm[p0 + lane];
         rows_out = c_rp[row + 1] - c_rp[row];
       }
       rows_out = warp_sum(rows_out);
-      if (nout >= 0 && (int64_t)K * nout <= SPREAD_MAX * rows_out) {
+      if (nout >= 0 && (spread_max <= 0 || (int64_t)K * nout <= (int64_t)spread_max * rows_out)) {
         const int64_t nva = A.vptr[c + 1] - A.vptr[c];
         if (dense) {  // the dense accumulator when the output span is small and it fits
           dw = span_width(jl, jh);

@@ -155,7 +155,7 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
     k_bin_cluster_sym<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, 1, L.o.dense);
   else
     k_bin_cluster_num<<<gb, 256, 0, L.s>>>(A, B, c_rp, bins, L.o.load_pct, L.mode == 1, (int)sizeof(In),
-                                            (int)sizeof(Acc), L.o.cl_load, L.o.lean, L.o.dense);
+                                            (int)sizeof(Acc), L.o.cl_load, L.o.lean, L.o.dense, L.o.spread_max);
   note_launches(1);
   auto kd = k_cluster_group<SYM, DT>;
   static bool attr = false;

@@ -337,25 +337,36 @@ __global__ void __launch_bounds__(256) k_row_hash(ACsrView Ac, AClusterView Acl,
       int64_t run = 0;  // MASKED: value slots before this chunk of union columns
       for (int64_t tb = u0; tb < u1; tb += 32) {
         const int64_t t = tb + lane;
-        uint32_t m = 0;
-        int32_t k = 0;
-        if (t < u1) {
-          m = Acl.mask[t];
-          k = Acl.ucol[t];
-        }
-        const int pc = __popc(m);
-        const int excl = warp_incl_scan(pc) - pc;
-        const bool mine = (m >> l) & 1u;
         In a{};
         int64_t s = 0, e = 0;
-        if (mine) {
-          const int64_t vi = Acl.layout == SGC_LAYOUT_PADDED ? v0 + (t - u0) * K + l
-                                                             : v0 + run + excl + __popc(m & below);
-          if (Acl.val) a = ((const In*)Acl.val)[vi];
-          s = B.rp[k];
-          e = B.rp[k + 1];
+        bool mine;
+        if (K == 1) {  // one row: every union column is the row's, value slot v0 + position
+          mine = t < u1;
+          if (mine) {
+            const int32_t k = Acl.ucol[t];
+            if (Acl.val) a = ((const In*)Acl.val)[v0 + (t - u0)];
+            s = B.rp[k];
+            e = B.rp[k + 1];
+          }
+        } else {  // (warp-uniform branch)
+          uint32_t m = 0;
+          int32_t k = 0;
+          if (t < u1) {
+            m = Acl.mask[t];
+            k = Acl.ucol[t];
+          }
+          const int pc = __popc(m);
+          const int excl = warp_incl_scan(pc) - pc;
+          mine = (m >> l) & 1u;
+          if (mine) {
+            const int64_t vi = Acl.layout == SGC_LAYOUT_PADDED ? v0 + (t - u0) * K + l
+                                                               : v0 + run + excl + __popc(m & below);
+            if (Acl.val) a = ((const In*)Acl.val)[vi];
+            s = B.rp[k];
+            e = B.rp[k + 1];
+          }
+          run += __shfl_sync(FULL, excl + pc, 31);
         }
-        run += __shfl_sync(FULL, excl + pc, 31);
         run_chunk(mine, s, e, a);
       }
     }
@@ -421,20 +432,34 @@ __device__ __forceinline__ void gather_chunk(const ACsrView& Ac, const AClusterV
   int keep = 0;
   int32_t k = 0;
   In a{};
+  // a CSR row, or the row of a one-row cluster (every union column is the
+  // row's, value slot v0 + position in both layouts): the chunk is contiguous
   if (src == SRC_CSR) {
     const int64_t s = Ac.rp[item], e = Ac.rp[item + 1];
     const int64_t p = s + cb + tid;
     if (p < e) {
-      keep = 1;
-      k = Ac.col[p];
-      if (Ac.val) a = ((const In*)Ac.val)[p];
+      s_k[tid] = Ac.col[p];
+      s_a[tid] = Ac.val ? ((const In*)Ac.val)[p] : In{};
     }
-  } else {
+    if (tid == 0) *n_out = (int)min64(e - s - cb, (int64_t)blockDim.x);
+    __syncthreads();
+    return;
+  }
+  {
     const int64_t c = item >> 5;
     const int l = (int)(item & 31);
     const int K = (int)(Acl.cptr[c + 1] - Acl.cptr[c]);
     const int64_t u0 = Acl.uptr[c], u1 = Acl.uptr[c + 1], v0 = Acl.vptr[c];
     const int64_t t = u0 + cb + tid;
+    if (K == 1) {
+      if (t < u1) {
+        s_k[tid] = Acl.ucol[t];
+        s_a[tid] = Acl.val ? ((const In*)Acl.val)[v0 + (t - u0)] : In{};
+      }
+      if (tid == 0) *n_out = (int)min64(u1 - u0 - cb, (int64_t)blockDim.x);
+      __syncthreads();
+      return;
+    }
     uint32_t m = 0;
     if (t < u1) m = Acl.mask[t];
     int64_t tot;

@@ -56,6 +56,7 @@ constexpr int64_t TOPK_HEAVY = 6144;
 constexpr int TOPK_LG_MAX = 13;
 constexpr int NUM_TABLE_LOAD = 50;  // default fill limit of the numeric cluster table
 constexpr uint32_t WAIT_POLLS_DEFAULT = 1u << 22;  // mbarrier polls before a wait gives up (~0.3 s)
+constexpr int SPREAD_MAX_DEFAULT = 3;  // numeric binning: see sgc_options.spread_max
 
 struct ResolvedOptions {
   int staging;
@@ -69,6 +70,8 @@ struct ResolvedOptions {
   int lean;     // numeric: 1 = warp-per-cluster kernel where it fits
   uint32_t wait_limit;  // mbarrier polls before a bounded wait gives up
   int dense;            // 1: cluster kernels use the dense accumulator where the output span fits
+  int spread_max;       // numeric binning: union x rows above this many times the rows' outputs -> row kernels
+                        // (0: never)
 };
 ResolvedOptions resolve(const sgc_options* opt);
 

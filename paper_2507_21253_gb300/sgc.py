@@ -62,7 +62,7 @@ class Predictor(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("staging", i32), ("validate", i32), ("stage_elems", i32), ("max_warps", i32),
                 ("load_pct", i32), ("fused_fma", i32), ("cluster_load_pct", i32), ("cluster_kernel", i32),
-                ("wait_polls", i32), ("accumulator", i32), ("reserved", i32 * 6)]
+                ("wait_polls", i32), ("accumulator", i32), ("spread_max", i32), ("reserved", i32 * 5)]
 
 
 def _sig(name, *args):
@@ -161,12 +161,12 @@ def _ptr(t):
 
 
 def options(staging=STAGING_AUTO, validate=0, stage_elems=0, max_warps=0, load_pct=0, fused_fma=0,
-            cluster_load_pct=0, cluster_kernel=0, wait_polls=0, accumulator=0) -> Options:
+            cluster_load_pct=0, cluster_kernel=0, wait_polls=0, accumulator=0, spread_max=0) -> Options:
     o = Options()
     _call("sgc_default_options", ctypes.byref(o))
     o.staging, o.validate, o.stage_elems, o.max_warps, o.load_pct = staging, validate, stage_elems, max_warps, load_pct
     o.fused_fma, o.cluster_load_pct, o.cluster_kernel = fused_fma, cluster_load_pct, cluster_kernel
-    o.wait_polls, o.accumulator = wait_polls, accumulator
+    o.wait_polls, o.accumulator, o.spread_max = wait_polls, accumulator, spread_max
     return o
 
 

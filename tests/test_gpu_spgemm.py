@@ -58,9 +58,22 @@ def test_clusterwise(sgc, name, A, clus, staging, layout):
         perm, cptr = synth.random_clusters(A.nrows, 11, kmax=32)
     Ad = dev(sgc, A)
     Acl = sgc.csr_cluster_build(Ad, perm, cptr, layout)
-    opt = sgc.options(staging=staging)
+    opt = sgc.options(staging=staging, spread_max=-1)   # every cluster that fits runs in the cluster kernels
     C = sgc.spgemm(Acl, Ad, opt)
     compare(C, A, A, exact_f64=(A.val.dtype == np.float64))
+
+
+@pytest.mark.parametrize("name,A", CASES[:4], ids=[c[0] for c in CASES[:4]])
+def test_spread_rule(sgc, name, A):
+    """Clusters of rows with little output overlap (fixed clusters of a permuted
+    matrix) go to the row kernels by default (spread_max); C is the same either way,
+    the oracle's."""
+    perm, cptr = synth.fixed_clusters(A.nrows, 8)
+    Ad = dev(sgc, A)
+    Acl = sgc.csr_cluster_build(Ad, perm, cptr, 1)
+    exact = A.val.dtype == np.float64
+    for spread in (0, -1, 1, 100):
+        compare(sgc.spgemm(Acl, Ad, sgc.options(spread_max=spread)), A, A, exact_f64=exact)
 
 
 KERNEL_CASES = [c for c in CASES if c[0] in ("laplacian64", "rand_f32", "rand_i64", "rmat12_f32", "planted",
@@ -286,7 +299,7 @@ def test_dense_accumulator(sgc, name, A, staging, layout):
     perm, cptr = synth.fixed_clusters(A.nrows, 8)
     Ad = dev(sgc, A)
     Acl = sgc.csr_cluster_build(Ad, perm, cptr, layout)
-    C = sgc.spgemm(Acl, Ad, sgc.options(staging=staging, accumulator=1))
+    C = sgc.spgemm(Acl, Ad, sgc.options(staging=staging, accumulator=1, spread_max=-1))
     compare(C, A, A, exact_f64=(A.val.dtype == np.float64))
 
 

@@ -35,10 +35,12 @@ def _stencil(sgc):
 @pytest.mark.parametrize("kernel", [0, 1], ids=["warp_groups", "warp_per_cluster"])
 def test_numeric_wait_gives_up_then_recovers(sgc, kernel):
     A, Ad, Acl = _stencil(sgc)
-    good = sgc.options(staging=sgc.STAGING_BULK, cluster_kernel=kernel)
+    # spread_max < 0: every cluster runs in the cluster kernels (whose waits are tested),
+    # however little its rows' outputs overlap
+    good = sgc.options(staging=sgc.STAGING_BULK, cluster_kernel=kernel, spread_max=-1)
     ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad, good))
     rp, nnz = sgc.spgemm_symbolic(Acl, Ad, ws, good)
-    bad = sgc.options(staging=sgc.STAGING_BULK, cluster_kernel=kernel, wait_polls=-1)
+    bad = sgc.options(staging=sgc.STAGING_BULK, cluster_kernel=kernel, wait_polls=-1, spread_max=-1)
     sgc.spgemm_numeric(Acl, Ad, rp, nnz, ws, bad)          # asynchronous: the status word records it
     with pytest.raises(sgc.SgcError) as e:
         sgc.workspace_status(ws)
