@@ -919,7 +919,7 @@ int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_pr
   const int inb = dtype_bytes(A->dtype);
   SGC_CUDA(learned_bin_run(av, bv, w.yhat, tot ? w.yhat_tot : nullptr, pred->ncap, pred->margin, mtot, pred->scale,
                            w.sp.bins.uc_rec, w.h_pos, w.ncap, w.pool_base, w.flag, w.flist, w.flist_count, lb, inb,
-                           8, mode, o.cl_load, o.lean, sms, s));
+                           8, mode, o.cl_load, o.lean, o.spread_max, sms, s));
   SGC_CUDA(inclusive_scan_i64(w.pool_base + 1, NSUBPOOL, w.sp.scan_tmp, s));
   SGC_CUDA(cudaMemcpyAsync(w.flist_plan, w.flist_count, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   SGC_CUDA(cudaMemcpyAsync(slab_elems_host, w.pool_base + NSUBPOOL, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

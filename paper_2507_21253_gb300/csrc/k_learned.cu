@@ -311,14 +311,30 @@ __device__ __forceinline__ int32_t capacity_of(float yhat, int64_t bound, float 
   return (int32_t)min64(bound, cap);
 }
 
+// Warp-collective append of the lanes' items (ok: this lane has one) to a list:
+// one atomic a warp.
+__device__ __forceinline__ void push_list(int32_t* list, int32_t* count, bool ok, int32_t item) {
+  const unsigned b = __ballot_sync(FULL, ok);
+  if (!b) return;
+  int32_t base = 0;
+  if (lane_id() == 0) base = atomicAdd(count, __popc(b));
+  base = __shfl_sync(FULL, base, 0);
+  if (ok) list[base + __popc(b & lanemask_lt())] = item;
+}
+
 __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, const float* yhat, const float* yhat_tot,
                                                      const int32_t* ncap_in, float margin, float margin_tot,
                                                      float scale, const int32_t* uc, const int32_t* h_pos,
                                                      int32_t* ncap_out, int64_t* pool_base, int32_t* flag,
                                                      int32_t* flist, int32_t* flist_count, BinOut lb, int in_bytes,
-                                                     int acc_bytes, int bulk, int cl_load, int lean) {
+                                                     int acc_bytes, int bulk, int cl_load, int lean, int spread_max) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * 8 + w, nwarps = (int64_t)gridDim.x * 8;
+  // a warp's single pushes (one per cluster) wait in lane j for its j-th cluster
+  // and go out together every 32 clusters
+  DeferredPush dp;
+  bool fl_ok = false;
+  int32_t fl_item = 0;
   for (int64_t c = gw; c < A.ncl; c += nwarps) {
     const int64_t p0 = A.cptr[c];
     const int K = (int)(A.cptr[c + 1] - p0);
@@ -343,30 +359,43 @@ __global__ void __launch_bounds__(256) k_learned_bin(AClusterView A, BView B, co
     } else {
       dw = 0;
     }
-    if (lane == 0 && lb.span_w) lb.span_w[c] = dw;
-    const bool take = cls >= 0 || lcls >= 0;
     // the cluster's share of the slab: its predicted nnz, capped by the bound sum_l min(h_l, n_cap)
     // (a dense cluster: n_cap is its span, which always holds its output columns)
     const int64_t rowcap = dw > 0 ? (int64_t)dw : (int64_t)ncap;
     int64_t hb = lane < K ? min64((int64_t)h_pos[p0 + lane], rowcap) : 0;
     hb = warp_sum(hb);
+    int64_t share = hb;
+    if (yhat_tot) share = min64(hb, (int64_t)capacity_of(yhat_tot[c], hb, margin_tot, scale));
+    // per-row accumulators over the predicted union that would stay mostly empty
+    // (see k_bin_cluster_num): the cluster goes to the exact path, whose binning
+    // gives its rows to the row kernels
+    if (dw == 0 && spread_max > 0 && K > 1 && (int64_t)K * ncap > (int64_t)spread_max * share) cls = lcls = -1;
+    if (lane == 0 && lb.span_w) lb.span_w[c] = cls >= 0 ? dw : 0;
+    const bool take = cls >= 0 || lcls >= 0;
     if (lane == 0) {
-      int64_t share = hb;
-      if (yhat_tot) share = min64(hb, (int64_t)capacity_of(yhat_tot[c], hb, margin_tot, scale));
       if (take && share > 0) atomicAdd((unsigned long long*)&pool_base[1 + c % NSUBPOOL], (unsigned long long)share);
       ncap_out[c] = ncap;
       flag[c] = take ? 0 : 1;
-      if (lcls >= 0) {
-        const int32_t idx = atomicAdd(&lb.count[BIN_LEAN0 + lcls], 1);
-        lb.lean_items[(int64_t)lcls * lb.ncl + idx] = (int32_t)c;
-      } else if (cls >= 0) {
-        const int32_t idx = atomicAdd(&lb.count[cls], 1);
-        lb.dense_items[(int64_t)cls * lb.ncl + idx] = (int32_t)c;
-      } else {
-        flist[atomicAdd(flist_count, 1)] = (int32_t)c;
+    }
+    if (lcls >= 0) {
+      dp.add(BIN_LEAN0 + lcls, c);
+    } else if (cls >= 0) {
+      dp.add(cls, c);
+    } else {
+      if (lane == dp.n) {
+        fl_ok = true;
+        fl_item = (int32_t)c;
       }
+      dp.skip();
+    }
+    if (dp.n == 32) {
+      push_list(flist, flist_count, fl_ok, fl_item);
+      fl_ok = false;
+      dp.flush(lb);
     }
   }
+  push_list(flist, flist_count, fl_ok, fl_item);
+  dp.flush(lb);
 }
 
 // copy the slab rows of clusters that did not overflow into C (warp per cluster)
@@ -462,7 +491,7 @@ cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* 
                             const int32_t* ncap_in, float margin, float margin_tot, float scale, const int32_t* uc,
                             const int32_t* h_pos, int32_t* ncap_out, int64_t* pool_base, int32_t* flag, int32_t* flist,
                             int32_t* flist_count, const BinOut& lb, int in_bytes, int acc_bytes, int bulk, int cl_load,
-                            int lean, int sms, cudaStream_t s) {
+                            int lean, int spread_max, int sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(lb.count, 0, sizeof(int32_t) * NBIN_ALL, s);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(flist_count, 0, sizeof(int32_t), s);
@@ -472,7 +501,7 @@ cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* 
   if (A.ncl <= 0) return cudaSuccess;
   k_learned_bin<<<grid_for(A.ncl, 8, sms, 8), 256, 0, s>>>(A, B, yhat, yhat_tot, ncap_in, margin, margin_tot, scale,
                                                             uc, h_pos, ncap_out, pool_base, flag, flist, flist_count, lb,
-                                                            in_bytes, acc_bytes, bulk, cl_load, lean);
+                                                            in_bytes, acc_bytes, bulk, cl_load, lean, spread_max);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -146,7 +146,7 @@ cudaError_t learned_bin_run(const AClusterView& A, const BView& B, const float* 
                             const int32_t* ncap_in, float margin, float margin_tot, float scale, const int32_t* uc,
                             const int32_t* h_pos, int32_t* ncap_out, int64_t* pool_base, int32_t* flag, int32_t* flist,
                             int32_t* flist_count, const BinOut& lb, int in_bytes, int acc_bytes, int bulk, int cl_load,
-                            int lean, int sms, cudaStream_t s);
+                            int lean, int spread_max, int sms, cudaStream_t s);
 cudaError_t compact_run(const AClusterView& A, const int32_t* flag, const int64_t* slab_off, const int32_t* slab_col,
                         const void* slab_val, int val_bytes, const int64_t* c_rp, int32_t* ccol, void* cval, int sms,
                         cudaStream_t s);

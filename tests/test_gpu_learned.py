@@ -138,8 +138,10 @@ def test_learned_explicit_caps_overflow_rule(sgc, name, make, kernel):
     U = np.array([int(np.sum(np.diff(A.row_ptr)[cc["ucol"][cc["ucol_ptr"][c]:cc["ucol_ptr"][c + 1]]]))
                   for c in range(cc["nclusters"])])
     caps_eff = np.minimum(caps, np.minimum(U, A.ncols))
+    # spread_max < 0: the plan sends no cluster to the exact path for its spread, only
+    # for overflow (and, on R-MAT, for a footprint too large for shared memory)
     L = sgc.LearnedSpgemm(Acl, Ad, ncap=torch.from_numpy(caps).cuda(), margin=1.0,
-                          opt=sgc.options(cluster_kernel=kernel))
+                          opt=sgc.options(cluster_kernel=kernel, spread_max=-1))
     C = L.run()
     # clusters sent to the exact path: the overflowing ones (one-row clusters are planned too)
     expect_over = int(ol.overflowing_clusters(n_out, caps_eff).sum())
@@ -148,6 +150,12 @@ def test_learned_explicit_caps_overflow_rule(sgc, name, make, kernel):
     else:
         assert L.n_overflow == expect_over
     compare(C, A, A, exact_f64=(A.val.dtype == np.float64))
+    # the default plan may also send clusters of little output overlap to the exact path
+    L2 = sgc.LearnedSpgemm(Acl, Ad, ncap=torch.from_numpy(caps).cuda(), margin=1.0,
+                           opt=sgc.options(cluster_kernel=kernel))
+    C2 = L2.run()
+    assert L2.n_overflow >= expect_over
+    compare(C2, A, A, exact_f64=(A.val.dtype == np.float64))
 
 
 @pytest.mark.parametrize("scale", [1.0, 0.05])
