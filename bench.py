@@ -729,13 +729,15 @@ def fp64_floor(cx: Ctx, flops: int) -> dict:
 def e2e_learned(cx: Ctx, A, B, internal: dict, train_params, steps: int) -> dict:
     """The headline method end to end through the public API: H2D of A from pinned host
     memory, csr_cluster_build (clusters reused from preprocessing), learned plan, slab
-    pass, exact fallback and compaction with C stored into pinned host memory."""
+    pass, exact fallback and compaction into device memory, then D2H of C into pinned
+    host memory by the copy engines (193 GB/s measured, against 120 GB/s for the
+    compaction storing C straight into host memory)."""
     torch, sgc, args = cx.torch, cx.sgc, cx.args
     Ad, Bd, square = internal["Ad"], internal["Bd"], internal["square"]
     opt = internal["opt"]
     pin = lambda x: torch.from_numpy(x).pin_memory()  # noqa: E731
     h_rp, h_col, h_val = pin(A.row_ptr), pin(A.col), pin(A.val)
-    h_out = None
+    h_out, c_dev = None, None
     times, stages = [], []
     for s in range(steps + 1):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
@@ -751,20 +753,24 @@ def e2e_learned(cx: Ctx, A, B, internal: dict, train_params, steps: int) -> dict
         L = sgc.LearnedSpgemm(Acl2, Bd, params=train_params, margin=args.margin, opt=opt)
         L.phase1()
         ev[3].record(cx.stream)
-        if h_out is None:
+        if h_out is None or h_out[1].numel() != L.nnz:
             h_out = (torch.empty(A.nrows + 1, dtype=torch.int64, pin_memory=True),
                      torch.empty(L.nnz, dtype=torch.int32, pin_memory=True),
                      torch.empty(L.nnz, dtype=Ad.val.dtype, pin_memory=True))
-        h_out[0].copy_(L.c_row_ptr, non_blocking=True)
-        L.phase2_to_host(h_out[1], h_out[2])
+            c_dev = (torch.empty(L.nnz, dtype=torch.int32, device=cx.dev),
+                     torch.empty(L.nnz, dtype=Ad.val.dtype, device=cx.dev))
+        C = L.phase2(sgc.DeviceCsr(A.nrows, B.ncols, L.c_row_ptr, c_dev[0], c_dev[1]))
         ev[4].record(cx.stream)
+        h_out[0].copy_(L.c_row_ptr, non_blocking=True)
+        h_out[1].copy_(C.col, non_blocking=True)
+        h_out[2].copy_(C.val, non_blocking=True)
         ev[5].record(cx.stream)
         sgc.workspace_status(L.ws)
         torch.cuda.synchronize()
         if s > 0:
             times.append(time.perf_counter() - t)
-            stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
-        del L, Acl2
+            stages.append([ev[i].elapsed_time(ev[i + 1]) for i in range(5)])
+        del L, Acl2, C
     e_s = max_over_ranks(float(np.mean(times)), cx.world, cx.dev)
     h2d = int(h_rp.numel() * 8 + h_col.numel() * 4 + h_val.numel() * h_val.element_size())
     d2h = int(h_out[0].numel() * 8 + h_out[1].numel() * 4 + h_out[2].numel() * h_out[2].element_size())
@@ -774,9 +780,10 @@ def e2e_learned(cx: Ctx, A, B, internal: dict, train_params, steps: int) -> dict
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e_s * 1e3, 2),
             "stages_ms": {"h2d": round(float(st[0]), 2), "csr_cluster_build": round(float(st[1]), 2),
                           "learned_plan_and_slab_pass": round(float(st[2]), 2),
-                          "compaction_into_host_memory": round(float(st[3]), 2)},
+                          "compaction": round(float(st[3]), 2), "d2h": round(float(st[4]), 2)},
             "step": "H2D of A (CSR) from pinned host memory, csr_cluster_build, spgemm_learned_plan + _phase1, "
-                    "spgemm_learned_phase2 storing C into pinned host memory (row pointer copied beside it)"}
+                    "spgemm_learned_phase2 into device memory, D2H of C (row pointer, columns, values) into "
+                    "pinned host memory"}
 
 
 def run_batched_headline(cx: Ctx, args, inputs: dict):
