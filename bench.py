@@ -299,13 +299,22 @@ NUMERIC_KERNEL_SOURCES = ("k_cluster.cuh", "k_lean.cuh", "k_rows.cuh", "k_bins.c
                           "k_phase_sym.cu")
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments, trailing blanks and empty lines (string literals
+    in these sources hold no comment markers)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return "\n".join(ln for ln in lines if ln)
+
+
 def numeric_sources_digest() -> str:
-    """sha256 over the device sources of the numeric phase's kernels and their launches."""
+    """sha256 over the code (comments stripped) of the device sources of the numeric
+    phase's kernels and their launches."""
     import hashlib
     h = hashlib.sha256()
     for f in NUMERIC_KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2507_21253_gb300", "csrc", f), "rb") as fh:
-            h.update(f.encode() + b"\0" + fh.read())
+        with open(os.path.join(ROOT, "paper_2507_21253_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(f.encode() + b"\0" + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,9 +1,10 @@
 // Binning of work before each phase (Sec. 2.2: the symbolic phase sizes C,
 // the numeric phase fills it).  Clusters of two or more rows go to the cluster
 // kernel when their staged footprint fits in shared memory (bins = shared-memory
-// budget classes); otherwise (and for one-row clusters) their rows go to the
-// row-level kernels, binned by hash table size, and rows beyond the table
-// limit go to the heavy-row kernel.
+// budget classes) and, in the numeric phase, their rows' outputs overlap
+// enough (spread_max); otherwise (and for one-row clusters) their rows go to
+// the row-level kernels, binned by hash table size, and rows beyond the table
+// limit go to the heavy-row kernel.  Pushes into the bins are warp-aggregated.
 // Symbolic bins use the flop upper bound ub_l = sum_k nnz(B_k) (capped by
 // ncols(B)); numeric bins use the exact counts the symbolic phase produced.
 #pragma once

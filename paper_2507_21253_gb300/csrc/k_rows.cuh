@@ -1,9 +1,11 @@
 // Row-level SpGEMM kernels: one warp per output row with a shared-memory hash
 // accumulator (Sec. 2.2, Gustavson row-wise; hash accumulator as in the
-// paper's evaluation setup), and one CTA per heavy row with a dense
-// accumulator over column windows.  Rows come either from a CSR matrix (the
-// plain row-wise method) or from a CSR_Cluster matrix (rows of clusters whose
-// staged footprint exceeds the cluster kernel's shared memory).
+// paper's evaluation setup), one CTA per medium row with a CTA-wide hash
+// table, and one CTA per heavy row with a dense accumulator over column
+// windows.  Rows come either from a CSR matrix (the plain row-wise method) or
+// from a CSR_Cluster matrix (one-row clusters, rows of clusters whose staged
+// footprint exceeds the cluster kernel's shared memory, and in the numeric
+// phase rows of clusters whose outputs overlap too little).
 #pragma once
 
 #include "sgc_device.cuh"
@@ -409,10 +411,13 @@ inline size_t row_hash_smem(int warps, int log2T, bool sym, int acc_bytes) {
 
 // ---------------------------------------------------------------------------
 // Heavy rows: one CTA per row, dense accumulator over windows of W columns.
-// The row's entries are gathered in chunks of blockDim into shared memory,
-// then warps take one entry (B row) each and update the window with
-// shared-memory atomics.  The numeric output of a window is emitted in
-// column order by scanning its presence bitmap.
+// The row's entries are gathered in chunks of blockDim into shared memory.
+// Numeric rows of at most HEAVY_CACHE entries keep a cursor per B row there:
+// in each window a thread walks each short B row from its cursor, a warp each
+// long one (32 elements a step); longer rows take their entries again in
+// every window, a warp per entry from a binary search.  Updates are
+// shared-memory atomics; the numeric output of a window is emitted in column
+// order by scanning its presence bitmap.
 // ---------------------------------------------------------------------------
 constexpr int HEAVY_THREADS = 1024;
 constexpr int HEAVY_SYM_WORDS = 16384;  // 64 KB bitmap: 524288 columns per pass
