@@ -153,6 +153,11 @@ def parse():
                     help="numeric cluster kernel: 0 warp groups (default), 1 warp per cluster where it fits")
     ap.add_argument("--max-warps", type=int, default=0, help="warps per cluster group / row CTA (0: default)")
     ap.add_argument("--batch", type=int, default=256, help="products in the batched workload")
+    ap.add_argument("--tune-space", default="full", choices=["full", "picked"],
+                    help="batched: the tuner's full search space, or only the configuration it picks on GB300 "
+                         "(fixed-length 1 clusters, cooperative staging, fill 75%%, 8 warps, hash table)")
+    ap.add_argument("--no-per-product", action="store_true",
+                    help="batched: skip timing one launch sequence per product")
     ap.add_argument("--gen-procs", type=int, default=0, help="input generation processes (0: host cores)")
     return ap.parse_args()
 
@@ -660,7 +665,11 @@ def measure_batched(cx: Ctx, mats, steps: int, warmup: int) -> dict:
     P, row_off, col_off = sgc.csr_batch_pack(dm)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = autotune.tune(P, reps=2)
+    space = None
+    if cx.args.tune_space == "picked":
+        space = {"clustering": ("fixed1",), "staging": (sgc.STAGING_LDG,), "load_pct": (75,), "max_warps": (8,),
+                 "accumulator": (0,)}
+    res = autotune.tune(P, reps=2, space=space)
     t_tune = time.perf_counter() - t0
     best = res["best"]
     perm, cptr = autotune.cluster(P, best["clustering"])
@@ -679,8 +688,8 @@ def measure_batched(cx: Ctx, mats, steps: int, warmup: int) -> dict:
     nnz = g.C.nnz
     default = res["default"]
     # one symbolic + numeric launch sequence per product
-    per = []
-    hcs = [sgc.hcluster_reorder_parallel(d) for d in dm]
+    per = [float("nan")]
+    hcs = [] if cx.args.no_per_product else [sgc.hcluster_reorder_parallel(d) for d in dm]
     cls = [sgc.csr_cluster_build(d, pr, cp) for d, (pr, cp) in zip(dm, hcs)]
     wss = [sgc.Workspace(sgc.spgemm_workspace_size(c, d)) for c, d in zip(cls, dm)]
     outs = []
@@ -688,7 +697,9 @@ def measure_batched(cx: Ctx, mats, steps: int, warmup: int) -> dict:
         rp, nz = sgc.spgemm_symbolic(c, d, w)
         outs.append(sgc.spgemm_numeric(c, d, rp, nz, w))
     torch.cuda.synchronize()
-    for rep in range(2):
+    for rep in range(0 if cx.args.no_per_product else 2):
+        if rep == 0:
+            per = []
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record()
         for c, d, w, C in zip(cls, dm, wss, outs):
@@ -718,10 +729,12 @@ def measure_batched(cx: Ctx, mats, steps: int, warmup: int) -> dict:
                          "space": res.get("space")},
             "default_graph": ({"ms_per_step": default["ms"], "gflops": gf(default["ms"]), "config": default}
                               if default else None),
-            "per_product_launches": {"ms_per_step": round(per_ms, 4), "gflops": gf(per_ms),
-                                     "launch_sequences": len(mats)},
+            "per_product_launches": (None if cx.args.no_per_product else
+                                     {"ms_per_step": round(per_ms, 4), "gflops": gf(per_ms),
+                                      "launch_sequences": len(mats)}),
             "rowwise_packed": {"ms_per_step": round(row_ms, 4), "gflops": gf(row_ms)},
-            "speedup_vs_rowwise": round(row_ms / ms, 4), "speedup_vs_per_product": round(per_ms / ms, 3)}
+            "speedup_vs_rowwise": round(row_ms / ms, 4),
+            "speedup_vs_per_product": None if cx.args.no_per_product else round(per_ms / ms, 3)}
 
 
 def fp64_floor(cx: Ctx, flops: int) -> dict:
