@@ -519,6 +519,13 @@ def measure_product(cx: Ctx, name: str, A, B, train_mats, steps: int, warmup: in
                                         "phases_ms": {"symbolic": round(float(np.mean(dsym[warmup:])), 4),
                                                       "numeric": round(float(np.mean(dnum[warmup:])), 4)},
                                         "accumulator": "dense over output spans of at most 4096 columns"}
+    # the bytes the cluster kernels stage, counted on the device (one untimed numeric call)
+    sgc.workspace_counters(ws, clear=True)
+    opt_count = sgc.options(fused_fma=args.fused_fma, cluster_load_pct=args.cluster_load,
+                            cluster_kernel=args.cluster_kernel, max_warps=args.max_warps, count_staged=1)
+    sgc.spgemm_numeric(Acl, Bd, rp, nnz, ws, opt_count, C=C)
+    col_b, val_b = sgc.workspace_counters(ws, clear=True)
+    sgc.workspace_status(ws)
     del C
     torch.cuda.empty_cache()
 
@@ -616,7 +623,11 @@ def measure_product(cx: Ctx, name: str, A, B, train_mats, steps: int, warmup: in
     res["hbm"] = {"step_GBs": round((num_bytes + sym_bytes) / (step_ms * 1e-3) / 1e9, 2),
                   "compulsory_bytes": int(compulsory),
                   "compulsory_frac": round(compulsory / (head_ms * 1e-3) / (peak * 1e9), 4),
-                  "staged_B_elements": staged, "reuse_R": round(flops / max(staged, 1), 4)}
+                  "staged_B_elements": staged, "reuse_R": round(flops / max(staged, 1), 4),
+                  "staged_measured": {"col_id_bytes_to_shared_memory": col_b, "value_bytes_through_l2": val_b,
+                                      "scope": "device counters of one numeric call (count_staged=1): clusters "
+                                               "run in the warp-group cluster kernel; staged_B_elements above "
+                                               "is every cluster's, one-row and spread clusters included"}}
     res["preprocess"] = {"hcluster_s": round(t_hc, 3), "csr_cluster_build_s": round(t_build, 4),
                          "in_steps": round((t_hc + t_build) / (head_ms * 1e-3), 1)}
     res["csr_cluster_bytes_over_csr"] = memory_overhead(cx, Ad, A, perm, cptr)

@@ -153,7 +153,11 @@ typedef struct sgc_options {
                                accumulators would stay mostly empty) has its rows computed by the row
                                kernels; 0 = default 3; < 0 = never (every cluster that fits shared memory
                                runs in the cluster kernels) */
-  int32_t reserved[5];
+  int32_t count_staged;     /* 1: the warp-group cluster kernels add the bytes they stage to two counters
+                               kept in the workspace (sgc_workspace_counters): B column ids copied into
+                               shared memory (whole 16-byte copy windows) and B values read through L2.
+                               Costs an atomic per cluster; 0 (default) = off */
+  int32_t reserved[4];
 } sgc_options;
 
 #define SGC_DENSE_SPAN_MAX 4096
@@ -181,6 +185,14 @@ int sgc_default_options(sgc_options* opt);
  * instruction) per second / 1e9, timed with CUDA events on `stream`.  sink: a
  * device double the kernel may write.  Synchronises. */
 int sgc_fp64_rate(int32_t op, int32_t iters, double* sink, double* gops_host, void* stream);
+
+/* Reads the staging counters kept in a spgemm or learned workspace (see
+ * sgc_options.count_staged) into counters_host[0] (bytes of B column ids
+ * copied into shared memory) and counters_host[1] (bytes of B values read
+ * through L2), summed over every call since they were last cleared; clear = 1
+ * zeroes them afterwards.  A new workspace's counters are undefined until
+ * cleared.  Synchronises.  SGC_INVALID_ARG on a NULL pointer. */
+int sgc_workspace_counters(void* ws, size_t ws_bytes, uint64_t* counters_host, int32_t clear, void* stream);
 
 /* Reads and clears the device status word kept in a spgemm workspace
  * (a failed device check or timeout in an asynchronous call such as

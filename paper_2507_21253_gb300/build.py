@@ -60,7 +60,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lgomp"], capture_output=True, text=True)
+    r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lgomp", "-ldl"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -48,6 +48,7 @@ ResolvedOptions resolve(const sgc_options* opt) {
   if (opt && opt->wait_polls < 0) r.wait_limit = 0;
   r.dense = (opt && opt->accumulator == 1) ? 1 : 0;
   r.spread_max = !opt || opt->spread_max == 0 ? SPREAD_MAX_DEFAULT : (opt->spread_max < 0 ? 0 : opt->spread_max);
+  r.count_staged = (opt && opt->count_staged == 1) ? 1 : 0;
   return r;
 }
 
@@ -209,6 +210,17 @@ int sgc_default_options(sgc_options* opt) {
   return SGC_OK;
 }
 
+int sgc_workspace_counters(void* ws, size_t ws_bytes, uint64_t* counters_host, int32_t clear, void* stream) {
+  SGC_NVTX("sgc:sgc_workspace_counters");
+  if (!ws || !counters_host || ws_bytes < 2 * sizeof(DevStatus)) SGC_FAIL(SGC_INVALID_ARG, "workspace too small or NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* ctr = (unsigned long long*)((DevStatus*)ws + 1);
+  SGC_CUDA(cudaMemcpyAsync(counters_host, ctr, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  if (clear) SGC_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(uint64_t), s));
+  SGC_CUDA(cudaStreamSynchronize(s));
+  return SGC_OK;
+}
+
 int sgc_workspace_status(void* ws, size_t ws_bytes, void* stream) {
   if (!ws || ws_bytes < sizeof(DevStatus)) SGC_FAIL(SGC_INVALID_ARG, "workspace too small or NULL");
   cudaStream_t s = (cudaStream_t)stream;
@@ -235,6 +247,7 @@ int csr_cluster_build_workspace_size(int64_t nrows, int64_t nclusters, size_t* b
 int csr_cluster_build_count(const sgc_csr* A, const int32_t* perm, const int64_t* cluster_ptr, int64_t nclusters,
                             int32_t layout, int64_t* ucol_ptr, int64_t* val_ptr, int64_t* nucols_host,
                             int64_t* nvals_host, void* ws, size_t ws_bytes, void* stream) {
+  SGC_NVTX("sgc:csr_cluster_build_count");
   int rc = check_csr(A, "A", false);
   if (rc) return rc;
   if (!nucols_host || !nvals_host || !ucol_ptr || !val_ptr) SGC_FAIL(SGC_INVALID_ARG, "NULL output");
@@ -269,6 +282,7 @@ int csr_cluster_build_count(const sgc_csr* A, const int32_t* perm, const int64_t
 }
 
 int csr_cluster_build(const sgc_csr* A, sgc_csr_cluster* out, void* stream) {
+  SGC_NVTX("sgc:csr_cluster_build");
   int rc = check_csr(A, "A", true);
   if (rc) return rc;
   if (!out) SGC_FAIL(SGC_INVALID_ARG, "out is NULL");
@@ -305,6 +319,7 @@ static int check_product(const sgc_csr_cluster* A, const sgc_csr* B, bool numeri
 
 int spgemm_symbolic(const sgc_csr_cluster* A, const sgc_csr* B, int64_t* c_row_ptr, int64_t* c_nnz_host, void* ws,
                     size_t ws_bytes, const sgc_options* opt, void* stream) {
+  SGC_NVTX("sgc:spgemm_symbolic");
   int rc = check_product(A, B, false);
   if (rc) return rc;
   if (!c_row_ptr) SGC_FAIL(SGC_INVALID_ARG, "c_row_ptr is NULL");
@@ -331,6 +346,7 @@ int spgemm_symbolic(const sgc_csr_cluster* A, const sgc_csr* B, int64_t* c_row_p
 
 int spgemm_numeric(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, void* ws, size_t ws_bytes,
                    const sgc_options* opt, void* stream) {
+  SGC_NVTX("sgc:spgemm_numeric");
   int rc = check_product(A, B, true);
   if (rc) return rc;
   rc = check_csr(C, "C", true);
@@ -411,6 +427,7 @@ static int numeric_host_direct(const sgc_csr_cluster* A, const sgc_csr* B, sgc_c
 int spgemm_numeric_to_host(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, int64_t* host_row_ptr,
                            int32_t* host_col, void* host_val, int32_t nchunks, void* ws, size_t ws_bytes,
                            const sgc_options* opt, void* stream, void* copy_stream) {
+  SGC_NVTX("sgc:spgemm_numeric_to_host");
   int rc = check_product(A, B, true);
   if (rc) return rc;
   if (nchunks != 0) {
@@ -516,6 +533,7 @@ static int check_rows_product(const sgc_csr* A, const sgc_csr* B, bool numeric) 
 
 int spgemm_rowwise_symbolic(const sgc_csr* A, const sgc_csr* B, int64_t* c_row_ptr, int64_t* c_nnz_host, void* ws,
                             size_t ws_bytes, const sgc_options* opt, void* stream) {
+  SGC_NVTX("sgc:spgemm_rowwise_symbolic");
   int rc = check_rows_product(A, B, false);
   if (rc) return rc;
   if (!c_row_ptr) SGC_FAIL(SGC_INVALID_ARG, "c_row_ptr is NULL");
@@ -542,6 +560,7 @@ int spgemm_rowwise_symbolic(const sgc_csr* A, const sgc_csr* B, int64_t* c_row_p
 
 int spgemm_rowwise_numeric(const sgc_csr* A, const sgc_csr* B, sgc_csr* C, void* ws, size_t ws_bytes,
                            const sgc_options* opt, void* stream) {
+  SGC_NVTX("sgc:spgemm_rowwise_numeric");
   int rc = check_rows_product(A, B, true);
   if (rc) return rc;
   rc = check_csr(C, "C", true);
@@ -621,6 +640,7 @@ int hcluster_workspace_size(const sgc_csr* A, int32_t max_cluster, size_t* bytes
 
 int hcluster_candidates(const sgc_csr* A, float jacc_th, int32_t topk, int32_t* cand_j, int32_t* cand_inter,
                         int32_t* cand_union, void* ws, size_t ws_bytes, void* stream) {
+  SGC_NVTX("sgc:hcluster_candidates");
   int rc = check_csr(A, "A", false);
   if (rc) return rc;
   if (topk < 1 || topk > 31) SGC_FAIL(SGC_INVALID_ARG, "topk must be in 1..31");
@@ -638,6 +658,7 @@ int hcluster_candidates(const sgc_csr* A, float jacc_th, int32_t topk, int32_t* 
 
 int cluster_fixed_length(int64_t nrows, int32_t K, int32_t* perm, int64_t* cluster_ptr, int64_t* nclusters_host,
                          void* stream) {
+  SGC_NVTX("sgc:cluster_fixed_length");
   if (nrows < 0 || K < 1 || K > 32) SGC_FAIL(SGC_INVALID_ARG, "nrows >= 0 and K in 1..32 required");
   if (!nclusters_host || !cluster_ptr || (nrows > 0 && !perm)) SGC_FAIL(SGC_INVALID_ARG, "NULL output");
   const int64_t ncl = (nrows + K - 1) / K;
@@ -648,6 +669,7 @@ int cluster_fixed_length(int64_t nrows, int32_t K, int32_t* perm, int64_t* clust
 
 int cluster_variable_length(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm,
                             int64_t* cluster_ptr, int64_t* nclusters_host, void* stream) {
+  SGC_NVTX("sgc:cluster_variable_length");
   int rc = check_csr(A, "A", false);
   if (rc) return rc;
   if (max_cluster < 1 || max_cluster > 32) SGC_FAIL(SGC_INVALID_ARG, "max_cluster must be in 1..32");
@@ -672,6 +694,7 @@ int cluster_variable_length(const sgc_csr* A, float jacc_th, int32_t max_cluster
 int hcluster_reorder_parallel(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm,
                               int64_t* cluster_ptr, int64_t* nclusters_host, void* ws, size_t ws_bytes,
                               void* stream) {
+  SGC_NVTX("sgc:hcluster_reorder_parallel");
   int rc = check_csr(A, "A", false);
   if (rc) return rc;
   if (max_cluster < 1 || max_cluster > 32) SGC_FAIL(SGC_INVALID_ARG, "max_cluster must be in 1..32");
@@ -725,6 +748,7 @@ int hcluster_reorder_parallel(const sgc_csr* A, float jacc_th, int32_t max_clust
 
 int hcluster_reorder(const sgc_csr* A, float jacc_th, int32_t max_cluster, int32_t* perm, int64_t* cluster_ptr,
                      int64_t* nclusters_host, void* ws, size_t ws_bytes, void* stream) {
+  SGC_NVTX("sgc:hcluster_reorder");
   int rc = check_csr(A, "A", false);
   if (rc) return rc;
   if (max_cluster < 1 || max_cluster > 32) SGC_FAIL(SGC_INVALID_ARG, "max_cluster must be in 1..32");
@@ -825,6 +849,7 @@ LwWs carve_lw(void* base, size_t cap, int64_t nrows, int64_t ncl) {
 }  // namespace
 
 int cluster_features(const sgc_csr_cluster* A, const sgc_csr* B, float* features, void* stream) {
+  SGC_NVTX("sgc:cluster_features");
   int rc = check_product(A, B, false);
   if (rc) return rc;
   if (A->nclusters > 0 && !features) SGC_FAIL(SGC_INVALID_ARG, "features is NULL");
@@ -835,6 +860,7 @@ int cluster_features(const sgc_csr_cluster* A, const sgc_csr* B, float* features
 
 int nnz_predictor_targets(const sgc_csr_cluster* A, const sgc_csr* B, const void* ws, size_t ws_bytes,
                           const int64_t* c_row_ptr, float* y, float* y_total, void* stream) {
+  SGC_NVTX("sgc:nnz_predictor_targets");
   int rc = check_product(A, B, false);
   if (rc) return rc;
   SpWs w = carve_sp((void*)ws, ws_bytes, A->nrows, A->nclusters);
@@ -845,6 +871,7 @@ int nnz_predictor_targets(const sgc_csr_cluster* A, const sgc_csr* B, const void
 }
 
 int nnz_predictor_infer(const float* params, const float* features, int64_t n, float* yhat, void* stream) {
+  SGC_NVTX("sgc:nnz_predictor_infer");
   if (n < 0 || (n > 0 && (!params || !features || !yhat))) SGC_FAIL(SGC_INVALID_ARG, "bad arguments");
   SGC_CUDA(mlp_infer_run(params, features, n, yhat, num_sms(), (cudaStream_t)stream));
   return SGC_OK;
@@ -859,6 +886,7 @@ int nnz_predictor_train_workspace_size(int32_t batch, size_t* bytes) {
 
 int nnz_predictor_grad(const float* params, const float* features, const float* y, const int32_t* idx,
                        int32_t batch, float* grad, float* loss, void* ws, size_t ws_bytes, void* stream) {
+  SGC_NVTX("sgc:nnz_predictor_grad");
   size_t need = 0;
   int rc = nnz_predictor_train_workspace_size(batch, &need);
   if (rc) return rc;
@@ -872,6 +900,7 @@ int nnz_predictor_grad(const float* params, const float* features, const float* 
 int nnz_predictor_train(const float* features, const float* y, int64_t n, const int32_t* order, int64_t steps,
                         int32_t batch, float lr, const float* init, float* params_out, float* loss_out, void* ws,
                         size_t ws_bytes, void* stream) {
+  SGC_NVTX("sgc:nnz_predictor_train");
   size_t need = 0;
   int rc = nnz_predictor_train_workspace_size(batch, &need);
   if (rc) return rc;
@@ -893,6 +922,7 @@ int spgemm_learned_workspace_size(const sgc_csr_cluster* A, const sgc_csr* B, co
 
 int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_predictor* pred,
                         int64_t* slab_elems_host, void* ws, size_t ws_bytes, const sgc_options* opt, void* stream) {
+  SGC_NVTX("sgc:spgemm_learned_plan");
   int rc = check_product(A, B, false);
   if (rc) return rc;
   if (!pred || !slab_elems_host || (!pred->params && !pred->ncap)) SGC_FAIL(SGC_INVALID_ARG, "bad predictor");
@@ -929,6 +959,7 @@ int spgemm_learned_plan(const sgc_csr_cluster* A, const sgc_csr* B, const sgc_pr
 int spgemm_learned_phase1(const sgc_csr_cluster* A, const sgc_csr* B, int32_t* slab_col, void* slab_val,
                           int64_t* c_row_ptr, int64_t* c_nnz_host, int64_t* n_overflow_host, void* ws,
                           size_t ws_bytes, const sgc_options* opt, void* stream) {
+  SGC_NVTX("sgc:spgemm_learned_phase1");
   int rc = check_product(A, B, true);
   if (rc) return rc;
   if (!c_row_ptr || !c_nnz_host || !n_overflow_host) SGC_FAIL(SGC_INVALID_ARG, "NULL output");
@@ -988,6 +1019,7 @@ static int output_view(void* p, void** out, const char* what) {
 int spgemm_learned_phase2(const sgc_csr_cluster* A, const sgc_csr* B, const int32_t* slab_col,
                           const void* slab_val, sgc_csr* C_in, void* ws, size_t ws_bytes, const sgc_options* opt,
                           void* stream) {
+  SGC_NVTX("sgc:spgemm_learned_phase2");
   int rc = check_product(A, B, true);
   if (rc) return rc;
   rc = check_csr(C_in, "C", true);
@@ -1116,6 +1148,7 @@ int nnz_predictor_load(const char* path, float* params, int32_t max_sets, int32_
 // ---------------------------------------------------------------------------
 int csr_batch_pack(int32_t k, const sgc_csr* mats, sgc_csr* out, int64_t* row_off, int64_t* col_off,
                    void* stream) {
+  SGC_NVTX("sgc:csr_batch_pack");
   if (k < 0 || (k > 0 && !mats) || !out || !row_off || !col_off) SGC_FAIL(SGC_INVALID_ARG, "bad arguments");
   int rc = check_csr(out, "out", true);
   if (rc) return rc;
@@ -1157,6 +1190,7 @@ struct sgc_graph {
 
 int spgemm_graph_create(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, void* ws, size_t ws_bytes,
                         const sgc_options* opt, void* stream, sgc_graph** graph) {
+  SGC_NVTX("sgc:spgemm_graph_create");
   if (!graph || !stream) SGC_FAIL(SGC_INVALID_ARG, "graph output and a created stream are required");
   int rc = check_product(A, B, true);
   if (rc) return rc;
@@ -1190,6 +1224,7 @@ int spgemm_graph_create(const sgc_csr_cluster* A, const sgc_csr* B, sgc_csr* C, 
 }
 
 int spgemm_graph_launch(sgc_graph* graph, void* stream) {
+  SGC_NVTX("sgc:spgemm_graph_launch");
   if (!graph) SGC_FAIL(SGC_INVALID_ARG, "graph is NULL");
   SGC_CUDA(cudaGraphLaunch(graph->exec, (cudaStream_t)stream));
   return SGC_OK;

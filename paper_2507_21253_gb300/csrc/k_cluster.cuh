@@ -304,7 +304,12 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
   int* wmax = (int*)(my + 104);
   uint64_t* red64 = (uint64_t*)(my + 136);
   DevStatus* st = (DevStatus*)status;
-  const bool bulk = mode == 1;
+  const bool bulk = (mode & 1) != 0;
+  // mode bit 1: add the bytes this kernel stages to the workspace counters that
+  // follow the status word (B column ids copied into shared memory, B values
+  // prefetched into L2 and read from there)
+  const bool count_staged = (mode & 2) != 0;
+  unsigned long long* staged_ctr = (unsigned long long*)((DevStatus*)status + 1);
   if (bulk) {
     if (gt == 0) {
       mbar_init(bar, 1);
@@ -348,7 +353,7 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
     const int TH = 1 << LH;
 
     // ---- 1. descriptors and staging ---------------------------------------
-    int64_t run_c = 0, run_a = 0;
+    int64_t run_c = 0, run_a = 0, my_vals = 0;
     if (bulk) fence_proxy_async_smem();  // earlier generic accesses to the region precede async writes
     for (int64_t tb = 0; tb < T; tb += GT) {
       const int64_t i = tb + gt;
@@ -381,6 +386,7 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       const int oc = (int)(ex & 0xffffffffu), oa = (int)(ex >> 32);
       const int tc = (int)(tot & 0xffffffffu), ta = (int)(tot >> 32);
       if (i < T) {
+        my_vals += len;
         if (!SYM) d.bs[i] = s;
         d.off_c[i] = (int32_t)(run_c + oc + shc) | (ldg ? (int32_t)0x80000000 : 0);
         d.len[i] = len;
@@ -393,6 +399,11 @@ __global__ void __launch_bounds__(CL_THREADS, 4) k_cluster_group(AClusterView A,
       }
       run_c += tc;
       run_a += ta;
+    }
+    if (count_staged) {  // (kernel-uniform) column ids staged: the windows, padding included
+      const int64_t vals = warp_sum(my_vals);
+      if (lane == 0 && !SYM && vals) atomicAdd(&staged_ctr[1], (unsigned long long)(vals * (int64_t)sizeof(In)));
+      if (gt == 0 && run_c) atomicAdd(&staged_ctr[0], (unsigned long long)(run_c * 4));
     }
     // the cluster's own value slots (numeric): one window covering [v0, v0 + nva)
     int ashift = 0;

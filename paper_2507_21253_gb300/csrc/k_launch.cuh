@@ -173,8 +173,8 @@ cudaError_t run_cluster_phase(const AClusterView& A, const BView& B, const CView
     const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
     kd<<<grid, threads, smem, L.s>>>(A, B, C, c_rp, bins.dense_items + (int64_t)b * bins.ncl, bins.count + b,
                                       bins.nout_rec, bins.uc_rec, L.o.dense ? bins.span_lo : nullptr,
-                                      L.o.dense ? bins.span_w : nullptr, L.mode, rbytes, gw, L.o.fused, L.o.cl_load,
-                                      LearnedOut{}, L.o.wait_limit, status);
+                                      L.o.dense ? bins.span_w : nullptr, L.mode | (L.o.count_staged ? 2 : 0), rbytes,
+                                      gw, L.o.fused, L.o.cl_load, LearnedOut{}, L.o.wait_limit, status);
     note_launches(1);
   }
   e = cudaGetLastError();
@@ -206,8 +206,8 @@ cudaError_t run_cluster_learned(const AClusterView& A, const BView& B, const Bin
     const unsigned grid = grid_for(A.ncl, groups, L.sms, occ);
     kd<<<grid, threads, smem, L.s>>>(A, B, CView{}, nullptr, lbins.dense_items + (int64_t)b * lbins.ncl,
                                       lbins.count + b, nullptr, lbins.uc_rec, L.o.dense ? lbins.span_lo : nullptr,
-                                      L.o.dense ? lbins.span_w : nullptr, L.mode, rbytes, gw, L.o.fused,
-                                      L.o.cl_load, lo, L.o.wait_limit, status);
+                                      L.o.dense ? lbins.span_w : nullptr, L.mode | (L.o.count_staged ? 2 : 0),
+                                      rbytes, gw, L.o.fused, L.o.cl_load, lo, L.o.wait_limit, status);
     note_launches(1);
   }
   cudaError_t e = cudaGetLastError();

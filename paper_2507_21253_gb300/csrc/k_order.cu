@@ -93,6 +93,7 @@ extern "C" int cluster_order_workspace_size(int64_t nrows, int64_t nclusters, si
 
 extern "C" int cluster_order_bfs(const sgc_csr* A, int32_t* perm, int64_t* cluster_ptr, int64_t nclusters,
                                  int32_t* nlevels_host, void* ws, size_t ws_bytes, void* stream) {
+  SGC_NVTX("sgc:cluster_order_bfs");
   auto fail = [](int code, const std::string& m) {
     set_last_error("cluster_order_bfs: " + m);
     return code;

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_fp64_probe(int32_t iters, dou
 using namespace sgc;
 
 extern "C" int sgc_fp64_rate(int32_t op, int32_t iters, double* sink, double* gops_host, void* stream) {
+  SGC_NVTX("sgc:sgc_fp64_rate");
   if (op < 0 || op > 2 || iters < 1 || !sink || !gops_host) {
     set_last_error("sgc_fp64_rate: op must be 0..2, iters >= 1, sink and gops_host non-NULL");
     return SGC_INVALID_ARG;

@@ -70,6 +70,7 @@ extern "C" int csr_cluster_build_count_noalloc(const sgc_csr* A, const int32_t* 
                                                int64_t nclusters, int32_t layout, int64_t* ucol_ptr,
                                                int64_t* val_ptr, int64_t* nucols_host, int64_t* nvals_host,
                                                void* stream) {
+  SGC_NVTX("sgc:csr_cluster_build_count_noalloc");
   using namespace sgc;
   if (!A || !nucols_host || !nvals_host || !ucol_ptr || !val_ptr) {
     set_last_error("csr_cluster_build_count_noalloc: NULL argument");

@@ -8,7 +8,20 @@
 
 #include "../../include/sgc.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace sgc {
+
+// A named NVTX range over one library call: the calls show up as ranges on
+// profiler timelines (Nsight Systems / Compute); without a tool attached a push
+// and a pop cost a few nanoseconds.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define SGC_NVTX(name) ::sgc::NvtxRange sgc_nvtx_range_(name)
 
 // thread-local last-error message (capi.cu)
 void set_last_error(const std::string& msg);
@@ -70,6 +83,7 @@ struct ResolvedOptions {
   int lean;     // numeric: 1 = warp-per-cluster kernel where it fits
   uint32_t wait_limit;  // mbarrier polls before a bounded wait gives up
   int dense;            // 1: cluster kernels use the dense accumulator where the output span fits
+  int count_staged;     // 1: cluster kernels add the bytes they stage to the workspace counters
   int spread_max;       // numeric binning: union x rows above this many times the rows' outputs -> row kernels
                         // (0: never)
 };

@@ -62,7 +62,8 @@ class Predictor(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("staging", i32), ("validate", i32), ("stage_elems", i32), ("max_warps", i32),
                 ("load_pct", i32), ("fused_fma", i32), ("cluster_load_pct", i32), ("cluster_kernel", i32),
-                ("wait_polls", i32), ("accumulator", i32), ("spread_max", i32), ("reserved", i32 * 5)]
+                ("wait_polls", i32), ("accumulator", i32), ("spread_max", i32), ("count_staged", i32),
+                ("reserved", i32 * 4)]
 
 
 def _sig(name, *args):
@@ -79,6 +80,7 @@ P = ctypes.POINTER
 _c = {
     "sgc_default_options": _sig("sgc_default_options", P(Options)),
     "sgc_workspace_status": _sig("sgc_workspace_status", vp, ctypes.c_size_t, vp),
+    "sgc_workspace_counters": _sig("sgc_workspace_counters", vp, ctypes.c_size_t, P(ctypes.c_uint64), i32, vp),
     "csr_cluster_build_workspace_size": _sig("csr_cluster_build_workspace_size", i64, i64, P(ctypes.c_size_t)),
     "csr_cluster_build_count": _sig("csr_cluster_build_count", P(CsrStruct), vp, vp, i64, i32, vp, vp, P(i64),
                                     P(i64), vp, ctypes.c_size_t, vp),
@@ -161,12 +163,13 @@ def _ptr(t):
 
 
 def options(staging=STAGING_AUTO, validate=0, stage_elems=0, max_warps=0, load_pct=0, fused_fma=0,
-            cluster_load_pct=0, cluster_kernel=0, wait_polls=0, accumulator=0, spread_max=0) -> Options:
+            cluster_load_pct=0, cluster_kernel=0, wait_polls=0, accumulator=0, spread_max=0,
+            count_staged=0) -> Options:
     o = Options()
     _call("sgc_default_options", ctypes.byref(o))
     o.staging, o.validate, o.stage_elems, o.max_warps, o.load_pct = staging, validate, stage_elems, max_warps, load_pct
     o.fused_fma, o.cluster_load_pct, o.cluster_kernel = fused_fma, cluster_load_pct, cluster_kernel
-    o.wait_polls, o.accumulator, o.spread_max = wait_polls, accumulator, spread_max
+    o.wait_polls, o.accumulator, o.spread_max, o.count_staged = wait_polls, accumulator, spread_max, count_staged
     return o
 
 
@@ -388,6 +391,15 @@ def workspace_status(ws: Workspace):
     _call("sgc_workspace_status", ws.ptr, ws.nbytes, _stream())
 
 
+def workspace_counters(ws: Workspace, clear: bool = True) -> tuple[int, int]:
+    """(bytes of B column ids staged into shared memory, bytes of B values read through
+    L2) counted by the cluster kernels of calls made with count_staged=1 since the
+    last clear."""
+    out = (ctypes.c_uint64 * 2)()
+    _call("sgc_workspace_counters", ws.ptr, ws.nbytes, out, int(clear), _stream())
+    return int(out[0]), int(out[1])
+
+
 def spgemm(A: DeviceCsrCluster, B: DeviceCsr, opt: Options | None = None) -> DeviceCsr:
     """Symbolic + numeric cluster-wise product, checked."""
     ws = Workspace(spgemm_workspace_size(A, B, opt), B.row_ptr.device)
@@ -458,6 +470,57 @@ def hcluster_reorder_parallel(A: DeviceCsr, jacc_th: float = JACC_TH, max_cluste
     _call("hcluster_reorder_parallel", ctypes.byref(a), float(jacc_th), max_cluster, _ptr(perm), _ptr(cptr),
           ctypes.byref(ncl), ws.ptr, ws.nbytes, _stream())
     return perm[:A.nrows], cptr[:ncl.value + 1]
+
+
+CLUSTERS_MAGIC = "sgc-clusters-v1"
+
+
+def _structure_fingerprint(row_ptr, col) -> str:
+    """sha256 over a matrix's structure (int64 row pointer, int32 column ids)."""
+    import hashlib
+    import numpy as np
+    to_np = lambda x: x.detach().cpu().numpy() if isinstance(x, torch.Tensor) else np.asarray(x)  # noqa: E731
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(to_np(row_ptr), dtype=np.int64).tobytes())
+    h.update(np.ascontiguousarray(to_np(col), dtype=np.int32).tobytes())
+    return h.hexdigest()
+
+
+def save_clusters(path: str, A, perm, cluster_ptr, meta: str = "") -> None:
+    """Stores a clustering of A (perm, cluster_ptr from any cluster source) with a
+    fingerprint of A's structure, so that a later run on the same matrix can skip the
+    clustering (its cost is amortised over every product with that A, Sec. 4.2).
+    A: DeviceCsr or a host matrix with row_ptr / col arrays."""
+    import numpy as np
+    to_np = lambda x: x.detach().cpu().numpy() if isinstance(x, torch.Tensor) else np.asarray(x)  # noqa: E731
+    nrows, ncols = int(A.nrows), int(A.ncols)
+    p = to_np(perm).astype(np.int32)[:nrows]
+    c = to_np(cluster_ptr).astype(np.int64)
+    if p.size != nrows or c.size < 1 or c[0] != 0 or c[-1] != nrows or np.any(np.diff(c) <= 0):
+        raise ValueError("perm / cluster_ptr are not a clustering of A's rows")
+    with open(path, "wb") as fh:
+        np.savez(fh, magic=np.array(CLUSTERS_MAGIC), nrows=np.int64(nrows), ncols=np.int64(ncols),
+                 nnz=np.int64(int(to_np(A.row_ptr)[-1])),
+                 fingerprint=np.array(_structure_fingerprint(A.row_ptr, A.col)),
+                 perm=p, cluster_ptr=c, meta=np.array(meta))
+
+
+def load_clusters(path: str, A, device=None):
+    """(perm, cluster_ptr) stored by save_clusters for this A's structure, as tensors on
+    `device` (default: A's device, or the CPU for a host matrix); ValueError when the file
+    is not a stored clustering or A's structure differs from the one it was made for."""
+    import numpy as np
+    with np.load(path, allow_pickle=False) as z:
+        if "magic" not in z.files or str(z["magic"]) != CLUSTERS_MAGIC:
+            raise ValueError(f"{path}: not a stored clustering")
+        if int(z["nrows"]) != int(A.nrows) or int(z["ncols"]) != int(A.ncols):
+            raise ValueError(f"{path}: made for a {int(z['nrows'])}x{int(z['ncols'])} matrix")
+        if str(z["fingerprint"]) != _structure_fingerprint(A.row_ptr, A.col):
+            raise ValueError(f"{path}: made for a matrix of another structure")
+        perm, cptr = z["perm"].copy(), z["cluster_ptr"].copy()
+    if device is None:
+        device = A.row_ptr.device if isinstance(A.row_ptr, torch.Tensor) else "cpu"
+    return torch.from_numpy(perm).to(device), torch.from_numpy(cptr).to(device)
 
 
 def cluster_fixed_length(nrows: int, K: int, device="cuda"):

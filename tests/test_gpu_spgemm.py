@@ -326,3 +326,33 @@ def test_dense_accumulator_tall_skinny(sgc):
     Acl = sgc.csr_cluster_build(Ad, perm, cptr)
     C = sgc.spgemm(Acl, Bd, sgc.options(accumulator=1))
     compare(C, G, B, exact_f64=True)
+
+
+@pytest.mark.parametrize("staging", [1, 2], ids=["bulk", "ldg"])
+def test_staged_byte_counters(sgc, staging):
+    """count_staged = 1: the cluster kernels count the bytes they stage.  Clusters of
+    4 neighbouring rows of an unpermuted stencil all run in the warp-group kernel, so
+    the counters equal sums over every cluster's union columns t: values 8 * nnz(B_t);
+    column ids 4 * nnz(B_t) with cooperative loads, 4 * (the B row's 16-byte-aligned
+    copy window) with bulk copies."""
+    from oracle import csr_cluster as occ
+    A = synth.stencil27_3d(12, 11, 10, seed=3, permute=False)
+    perm, cptr = synth.fixed_clusters(A.nrows, 4)
+    Ad = dev(sgc, A)
+    Acl = sgc.csr_cluster_build(Ad, perm, cptr, 1)
+    cc = occ.build(A, perm, cptr)
+    rp = A.row_ptr.astype(np.int64)
+    t = cc["ucol"].astype(np.int64)
+    s, e = rp[t], rp[t + 1]
+    vals = 8 * int(np.sum(e - s))
+    cols = 4 * int(np.sum(e - s)) if staging == 2 else 4 * int(np.sum(((e + 3) & ~3) - (s & ~3)))
+    ws = sgc.Workspace(sgc.spgemm_workspace_size(Acl, Ad))
+    rpc, nnz = sgc.spgemm_symbolic(Acl, Ad, ws, sgc.options(staging=staging, spread_max=-1))
+    sgc.workspace_counters(ws, clear=True)
+    opt = sgc.options(staging=staging, spread_max=-1, count_staged=1)
+    C = sgc.spgemm_numeric(Acl, Ad, rpc, nnz, ws, opt)
+    sgc.workspace_status(ws)
+    assert sgc.workspace_counters(ws, clear=True) == (cols, vals)
+    compare(C, A, A, exact_f64=True)
+    sgc.spgemm_numeric(Acl, Ad, rpc, nnz, ws, sgc.options(staging=staging, spread_max=-1))
+    assert sgc.workspace_counters(ws) == (0, 0)      # off by default
